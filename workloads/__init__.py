@@ -1,0 +1,267 @@
+"""Seeded synthetic graphs and right-hand sides for LAMG tests and benchmarks.
+
+This module holds input generators only -- none of the method's arithmetic --
+so that both the CUDA library's tests/benchmarks and the CPU oracle can be fed
+identical inputs.  Every graph is returned as ``Graph(n, rp, col, w)``: a
+symmetric CSR of the off-diagonal pattern of the Laplacian (Eq. (1.2) of the
+paper), both directions of every edge, columns strictly increasing per row,
+no self loops, int64 row pointers, int32 columns, float64 weights.  Generators
+that can produce several components keep the largest connected component.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Graph:
+    n: int
+    rp: np.ndarray   # int64 [n+1]
+    col: np.ndarray  # int32 [nnz]
+    w: np.ndarray    # float64 [nnz]
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.size)
+
+    @property
+    def m(self) -> int:
+        return self.nnz // 2
+
+    def edges(self):
+        """Undirected edge list (u < v) in CSR order: (eu, ev, w)."""
+        rows = np.repeat(np.arange(self.n, dtype=np.int64), np.diff(self.rp))
+        keep = rows < self.col
+        return rows[keep].astype(np.int32), self.col[keep].astype(np.int32), self.w[keep].copy()
+
+
+def from_edges(n: int, u, v, w, name: str = "") -> Graph:
+    """CSR from an undirected edge list with u != v and no repeated pair."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    assert u.shape == v.shape == w.shape
+    assert not np.any(u == v), "self loops"
+    r = np.concatenate([u, v])
+    c = np.concatenate([v, u])
+    ww = np.concatenate([w, w])
+    order = np.lexsort((c, r))
+    r, c, ww = r[order], c[order], ww[order]
+    if r.size > 1:
+        dup = (r[1:] == r[:-1]) & (c[1:] == c[:-1])
+        assert not np.any(dup), "repeated edge"
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, r + 1, 1)
+    rp = np.cumsum(rp)
+    return Graph(n, rp, c.astype(np.int32), ww, name)
+
+
+def _dedupe(u, v):
+    """Unique undirected pairs (lo, hi) with lo != hi, sorted."""
+    lo = np.minimum(u, v).astype(np.int64)
+    hi = np.maximum(u, v).astype(np.int64)
+    keep = lo != hi
+    key = np.unique(lo[keep] * (1 << 32) + hi[keep])
+    return (key >> 32).astype(np.int64), (key & 0xFFFFFFFF).astype(np.int64)
+
+
+def largest_component(g: Graph) -> Graph:
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    A = sp.csr_matrix((np.ones(g.nnz), g.col, g.rp), shape=(g.n, g.n))
+    nc, lab = connected_components(A, directed=False)
+    if nc == 1:
+        return g
+    big = np.argmax(np.bincount(lab))
+    keep = np.flatnonzero(lab == big)
+    newid = -np.ones(g.n, dtype=np.int64)
+    newid[keep] = np.arange(keep.size)
+    eu, ev, w = g.edges()
+    sel = (newid[eu] >= 0) & (newid[ev] >= 0)
+    return from_edges(keep.size, newid[eu[sel]], newid[ev[sel]], w[sel], g.name)
+
+
+# --------------------------------------------------------------------------- #
+# Small graphs
+# --------------------------------------------------------------------------- #
+
+def five_node() -> Graph:
+    """The paper's 5-node example (Fig. 1.1); nodes renumbered 0..4."""
+    eu = [0, 0, 0, 0, 1, 2]
+    ev = [1, 2, 3, 4, 3, 3]
+    w = [1.0, 1.0, 1.0, 5.0, 1.0, 2.0]
+    return from_edges(5, eu, ev, w, "five_node")
+
+
+def path(n: int, w: float = 1.0) -> Graph:
+    i = np.arange(n - 1)
+    return from_edges(n, i, i + 1, np.full(n - 1, w), f"path{n}")
+
+
+def star(n: int) -> Graph:
+    return from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n), np.ones(n - 1), f"star{n}")
+
+
+def complete(n: int) -> Graph:
+    u, v = np.triu_indices(n, 1)
+    return from_edges(n, u, v, np.ones(u.size), f"complete{n}")
+
+
+def grid2d(nx: int, ny: int, wx: float = 1.0, wy: float = 1.0) -> Graph:
+    """5-point grid Laplacian with free (Neumann) boundary; node id = i + nx*j."""
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    us = [idx[:, :-1].ravel(), idx[:-1, :].ravel()]
+    vs = [idx[:, 1:].ravel(), idx[1:, :].ravel()]
+    ws = [np.full(us[0].size, wx), np.full(us[1].size, wy)]
+    return from_edges(nx * ny, np.concatenate(us), np.concatenate(vs), np.concatenate(ws),
+                      f"grid{nx}x{ny}")
+
+
+def grid3d(nx: int, ny: int, nz: int, wx=1.0, wy=1.0, wz=1.0) -> Graph:
+    """7-point grid Laplacian with free boundary; node id = i + nx*(j + ny*k).
+
+    Built directly as a CSR (no sort) so that 256^3 stays cheap."""
+    n = nx * ny * nz
+    i = np.arange(n, dtype=np.int64)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    # neighbours in increasing id order: -z, -y, -x, +x, +y, +z
+    offs = [(-nx * ny, z > 0, wz), (-nx, y > 0, wy), (-1, x > 0, wx),
+            (1, x < nx - 1, wx), (nx, y < ny - 1, wy), (nx * ny, z < nz - 1, wz)]
+    deg = np.zeros(n, dtype=np.int64)
+    for _, m, _ in offs:
+        deg += m
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=rp[1:])
+    col = np.empty(int(rp[-1]), dtype=np.int32)
+    w = np.empty(int(rp[-1]), dtype=np.float64)
+    pos = rp[:-1].copy()
+    for d, m, wv in offs:
+        sel = np.flatnonzero(m)
+        col[pos[sel]] = (sel + d).astype(np.int32)
+        w[pos[sel]] = wv
+        pos[sel] += 1
+    return Graph(n, rp, col, w, f"grid{nx}x{ny}x{nz}")
+
+
+# --------------------------------------------------------------------------- #
+# Random graphs of the benchmark configurations
+# --------------------------------------------------------------------------- #
+
+def chung_lu(n: int, beta: float = 2.5, mean_deg: float = 10.0, seed: int = 2,
+             wlo: float = 0.5, whi: float = 2.0, i0: float | None = None) -> Graph:
+    """Power-law expected-degree graph, largest component.
+
+    Expected degrees d_i proportional to (i + i0)^(-1/(beta-1)), scaled to the
+    mean; edges are drawn as M ~ Poisson(sum d / 2) independent pairs whose
+    endpoints are chosen proportionally to d (the edge-sampling form of the
+    Chung-Lu model); self loops and repeats are dropped.  Weights are uniform
+    in [wlo, whi], rounded to FP32 (and stored exactly in FP64)."""
+    rng = np.random.default_rng(seed)
+    if i0 is None:
+        i0 = max(1.0, n ** 0.05)
+    d = (np.arange(n) + i0) ** (-1.0 / (beta - 1.0))
+    d *= mean_deg * n / d.sum()
+    M = rng.poisson(d.sum() / 2.0)
+    p = d / d.sum()
+    cdf = np.cumsum(p)
+    cdf[-1] = 1.0
+    u = np.searchsorted(cdf, rng.random(M), side="right")
+    v = np.searchsorted(cdf, rng.random(M), side="right")
+    lo, hi = _dedupe(u, v)
+    perm = rng.permutation(n)               # shuffle ids so degree is not monotone in id
+    lo, hi = perm[lo], perm[hi]
+    w = rng.uniform(wlo, whi, lo.size).astype(np.float32).astype(np.float64)
+    return largest_component(from_edges(n, lo, hi, w, f"chung_lu{n}"))
+
+
+def rgg2d(n: int, mean_deg: float = 12.0, seed: int = 4) -> Graph:
+    """Random geometric graph in the unit square, radius r = sqrt(mean_deg / (pi n)),
+    weights exp(-d^2 / sigma^2) with sigma = r; largest component."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 2))
+    r = np.sqrt(mean_deg / (np.pi * n))
+    pairs = cKDTree(pts).query_pairs(r, output_type="ndarray")
+    u, v = pairs[:, 0].astype(np.int64), pairs[:, 1].astype(np.int64)
+    d2 = np.sum((pts[u] - pts[v]) ** 2, axis=1)
+    w = np.exp(-d2 / (r * r))
+    return largest_component(from_edges(n, u, v, w, f"rgg{n}"))
+
+
+def erdos_renyi(n: int, mean_deg: float = 8.0, seed: int = 5) -> Graph:
+    """G(n, p) with p = mean_deg / (n - 1): M ~ Binomial(n(n-1)/2, p) uniform pairs
+    (repeats dropped), unit weights, largest component."""
+    rng = np.random.default_rng(seed)
+    M = rng.binomial(n * (n - 1) // 2, mean_deg / (n - 1))
+    u = rng.integers(0, n, M)
+    v = rng.integers(0, n, M)
+    lo, hi = _dedupe(u, v)
+    return largest_component(from_edges(n, lo, hi, np.ones(lo.size), f"er{n}"))
+
+
+def knn_gmm(n: int = 500_000, dim: int = 16, k: int = 10, ncomp: int = 10, seed: int = 6,
+            device: str = "cpu", block: int = 4096):
+    """k-nearest-neighbour graph (union-symmetrised) on points from a Gaussian
+    mixture (means ~ N(0, 3^2 I), unit covariance, equal weights); Gaussian edge
+    weights exp(-d^2/sigma^2), sigma = mean k-th neighbour distance, rounded to
+    FP32.  Returns (graph of the largest component, labels, points)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    means = rng.normal(0.0, 3.0, (ncomp, dim))
+    lab = rng.integers(0, ncomp, n)
+    pts = means[lab] + rng.normal(0.0, 1.0, (n, dim))
+    P = torch.tensor(pts, dtype=torch.float32, device=device)
+    sq = (P * P).sum(1)
+    nbr = np.empty((n, k), dtype=np.int64)
+    dist = np.empty((n, k), dtype=np.float64)
+    for s in range(0, n, block):
+        Q = P[s:s + block]
+        d2 = sq[s:s + block, None] + sq[None, :] - 2.0 * (Q @ P.T)
+        d2[torch.arange(Q.shape[0], device=device), torch.arange(s, s + Q.shape[0], device=device)] = float("inf")
+        val, idx = torch.topk(d2, k, dim=1, largest=False)
+        nbr[s:s + block] = idx.cpu().numpy()
+        dist[s:s + block] = val.clamp_min(0).sqrt().cpu().numpy()
+    sigma = float(dist[:, -1].mean())
+    u = np.repeat(np.arange(n), k)
+    v = nbr.ravel()
+    lo, hi = _dedupe(u, v)
+    d2 = np.sum((pts[lo] - pts[hi]) ** 2, axis=1)
+    w = np.exp(-d2 / (sigma * sigma)).astype(np.float32).astype(np.float64)
+    w = np.maximum(w, np.float64(np.finfo(np.float32).tiny))
+    g = from_edges(n, lo, hi, w, f"knn{n}")
+    g2 = largest_component(g)
+    return g2, lab, pts
+
+
+def zero_sum_rhs(n: int, seed: int, count: int | None = None) -> np.ndarray:
+    """Gaussian right-hand side(s) with the mean removed (Sec. 1: b must be zero-sum)."""
+    rng = np.random.default_rng(seed)
+    if count is None:
+        b = rng.normal(size=n)
+        return b - b.mean()
+    B = rng.normal(size=(n, count))
+    return B - B.mean(axis=0, keepdims=True)
+
+
+# --------------------------------------------------------------------------- #
+# The benchmark configurations
+# --------------------------------------------------------------------------- #
+
+def config_graph(name: str) -> Graph:
+    """'grid64': 64x64 5-point grid; 'chung_lu1m': Chung-Lu n=1M, beta 2.5, mean degree 10;
+    'grid256': 256^3 7-point grid, weights 1/1/0.01; 'rgg2m': 2M-node RGG, mean degree 12."""
+    if name == "grid64":
+        return grid2d(64, 64)
+    if name == "chung_lu1m":
+        return chung_lu(1_000_000, 2.5, 10.0, seed=2)
+    if name == "grid256":
+        return grid3d(256, 256, 256, 1.0, 1.0, 0.01)
+    if name == "rgg2m":
+        return rgg2d(2_000_000, 12.0, seed=4)
+    raise KeyError(name)
