@@ -1,0 +1,343 @@
+"""LAMG benchmark: one step = lamg_setup + lamg_solve to relative residual 1e-8
+on a device-resident synthetic graph (default: Chung-Lu, n = 1M, degree
+exponent 2.5, mean degree 10, FP32 weights, FP32 cycles inside FP64 iterative
+refinement), timed with CUDA events.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload chung_lu1m|grid256|grid64] [--precision fp32ir|fp64]
+
+Multi-GPU: the solve does not shard (each relaxation sweep would need a halo
+exchange); N GPUs run N independent replicas of the step, no collective on
+the data path; value = all ranks' units / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (graph, precision default, description)
+    "chung_lu1m": ("chung_lu1m", "fp32ir",
+                   "Chung-Lu n=1M beta=2.5 mean degree 10 (LCC), w~U[0.5,2] FP32; FP32 cycles in FP64 IR to 1e-8"),
+    "grid256": ("grid256", "fp32ir",
+                "256^3 7-point grid, weights 1/1/0.01; FP32 cycles in FP64 IR to 1e-8"),
+    "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
+}
+TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10}
+CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sample_graph(workload):
+    import workloads as W
+    kind, size = CPU_SAMPLE[workload]
+    if kind == "chung_lu":
+        return W.chung_lu(size, 2.5, 10.0, seed=2), f"Chung-Lu n={size} (same family and seed rule)"
+    if kind == "grid3d":
+        return W.grid3d(size, size, size, 1.0, 1.0, 0.01), f"{size}^3 7-point grid, weights 1/1/0.01"
+    return W.grid2d(size, size), f"{size}x{size} 5-point grid"
+
+
+def cpu_oracle_step(g, b, tol, precision_note=""):
+    """The oracle as it stands: FP64 setup + solve on one host core."""
+    import oracle
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    x, hist = h.solve(b, tol=tol, max_cycles=500)
+    t = time.perf_counter() - t0
+    return t, len(hist) - 1
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed on this host, on a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    g, desc = sample_graph(args.workload)
+    b = W.zero_sum_rhs(g.n, 2)
+    tol = TOL[args.workload]
+    for _ in range(min(args.warmup, 1)):
+        cpu_oracle_step(g, b, tol)
+    ts, cyc = [], []
+    for _ in range(args.steps):
+        t, c = cpu_oracle_step(g, b, tol)
+        ts.append(t)
+        cyc.append(c)
+    tmean = sum(ts) / len(ts)
+    value = g.m * (sum(cyc) / len(cyc)) / tmean
+    line = {
+        "impl": "reference", "metric": "edges*cycles/s (LAMG setup + solve to tol)", "value": value,
+        "unit": "edges*cycles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": min(args.warmup, 1),
+        "ms_per_step": tmean * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": desc, "n": g.n, "m": g.m, "tol": tol},
+        "cpu_baseline": {"value": value, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "edges*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu")
+    ap.add_argument("--workload", default="chung_lu1m", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp32ir", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1108_1310_gb300 import build
+    build.build()
+    from paper_1108_1310_gb300 import lamg as L
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    gname, pdef, desc = WORKLOADS[args.workload]
+    prec_name = args.precision or pdef
+    prec = L.LAMG_FP32_IR if prec_name == "fp32ir" else L.LAMG_FP64
+    tol = TOL[args.workload]
+    g = W.config_graph(gname)
+    b_host = W.zero_sum_rhs(g.n, 2)
+    w_dtype = torch.float32 if args.workload == "chung_lu1m" else torch.float64
+    rp = torch.tensor(g.rp, device=dev)
+    col = torch.tensor(g.col, device=dev)
+    w = torch.tensor(g.w, device=dev).to(w_dtype)
+    b = torch.tensor(b_host, device=dev)
+    x = torch.zeros_like(b)
+    opt = L.lamg_default_options(validate=1)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+
+    def step(profile=False):
+        h = L.lamg_setup(g.n, rp, col, w, opt, stream)
+        if profile:
+            L.lamg_profile(h, True)
+        x.zero_()
+        st = L.lamg_solve(h, b, x, tol, prec, stream)
+        prof = L.lamg_profile(h, False) if profile else None
+        L.lamg_free(h)
+        return st, prof
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    # timed region: each step bracketed by CUDA events; L2 flushed between steps
+    evs = []
+    stats = []
+    prof_ms, prof_cnt, prof_bytes = 0.0, 0, 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = L.lamg_launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, prof = step(profile=True)
+            e1.record(stream)
+            evs.append((e0, e1))
+            stats.append(st)
+            prof_ms += prof[0] * prof[1]
+            prof_cnt += prof[1]
+            prof_bytes = prof[2]
+            flush.fill_(1.0)
+        torch.cuda.synchronize()
+    launches = L.lamg_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    times = [a.elapsed_time(bb) for a, bb in evs]
+    ms = sum(times) / len(times)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    cycles = sum(s.cycles for s in stats) / len(stats)
+    value = world * g.m * cycles / (ms / 1e3)
+
+    # plain FP64 on the same workload, same accuracy (context for the IR form)
+    fp64 = None
+    if prec == L.LAMG_FP32_IR:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        h = L.lamg_setup(g.n, rp, col, w, opt, stream)
+        x.zero_()
+        L.lamg_solve(h, b, x, tol, L.LAMG_FP64, stream)  # warm graph
+        x.zero_()
+        flush.fill_(1.0)
+        e0.record(stream)
+        st64 = L.lamg_solve(h, b, x, tol, L.LAMG_FP64, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        x.zero_()
+        flush.fill_(1.0)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        st32 = L.lamg_solve(h, b, x, tol, prec, stream)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"solve_ms_fp64": e0.elapsed_time(e1), "cycles_fp64": st64.cycles,
+                "solve_ms_fp32ir": e2.elapsed_time(e3), "cycles_fp32ir": st32.cycles,
+                "rel_res_fp64": st64.rel_res, "rel_res_fp32ir": st32.rel_res}
+        L.lamg_free(h)
+
+    # end to end through the host-array API: graph + b from pinned host memory, x back
+    e2e = None
+    if not args.no_e2e:
+        rp_h = torch.tensor(g.rp).pin_memory()
+        col_h = torch.tensor(g.col).pin_memory()
+        w_h = torch.tensor(g.w).to(w_dtype).pin_memory()
+        b_h = torch.tensor(b_host).pin_memory()
+        x_h = torch.zeros(g.n, dtype=torch.float64).pin_memory()
+        rp_d, col_d, w_d = torch.empty_like(rp), torch.empty_like(col), torch.empty_like(w)
+        h2d = rp_h.numel() * 8 + col_h.numel() * 4 + w_h.numel() * w_h.element_size() + b_h.numel() * 8
+        d2h = x_h.numel() * 8
+        tt = []
+        for it in range(2):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rp_d.copy_(rp_h, non_blocking=True)
+            col_d.copy_(col_h, non_blocking=True)
+            w_d.copy_(w_h, non_blocking=True)
+            h = L.lamg_setup(g.n, rp_d, col_d, w_d, opt, stream)
+            x_h.zero_()
+            st = L.lamg_solve_host(h, b_h.numpy(), x_h.numpy(), tol, prec, stream)
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t0)
+            L.lamg_free(h)
+        te = min(tt)
+        e2e = {"value": world * g.m * st.cycles / te, "unit": "edges*cycles/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": te * 1e3}
+
+    peak, peak_kind = load_peaks()
+    roof = None
+    if prof_cnt:
+        avg = prof_ms / prof_cnt
+        achieved = prof_bytes / (avg / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "finest-level Gauss-Seidel sweep (all colours)",
+                "bytes_per_launch": prof_bytes, "avg_ms": avg, "launches": prof_cnt,
+                "peak_kind": f"{peak_kind} hbm_gbs"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sg, sdesc = sample_graph(args.workload)
+        sb = W.zero_sum_rhs(sg.n, 2)
+        t, c = cpu_oracle_step(sg, sb, tol)
+        cpu = {"value": sg.m * c / t, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sdesc}, FP64 setup + solve to {tol:g}, {t:.1f} s"}
+
+    s0 = stats[-1]
+    line = {
+        "metric": "edges*cycles/s (LAMG setup + solve to tol)",
+        "value": value, "unit": "edges*cycles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == L.LAMG_FP32_IR else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "tol": tol,
+                   "precision": prec_name, "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
+                   "rel_res": s0.rel_res, "time_to_tol_s": ms / 1e3,
+                   "setup_s_host": s0.t_setup_s, "solve_s_host": s0.t_solve_s,
+                   "model_bytes_per_cycle": s0.bytes_per_cycle32 if prec == L.LAMG_FP32_IR else s0.bytes_per_cycle,
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
+        "fp64_vs_ir": fp64,
+        "e2e": e2e,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * lamg.h -- C-ABI of the GB300 (sm_103a) Lean Algebraic Multigrid library.
+ *
+ * Solves the compatible graph-Laplacian system of Livne & Brandt, "Lean
+ * Algebraic Multigrid (LAMG): Fast Graph Laplacian Linear Solver", arXiv
+ * 1108.1310, Sec. 1, Eq. (1.3):
+ *
+ *     A x = b,   1^T x = 0,
+ *
+ * A the Laplacian of a connected graph with positive weights (Eq. (1.2)),
+ * b zero-sum.  lamg_setup builds the multilevel hierarchy of Sec. 4.1
+ * (test-vector relaxation, affinities Eq. (3.5), energy ratios Eq. (3.12),
+ * caliber-1 aggregation Sec. 3.4, Galerkin operators Eq. (2.5)); lamg_solve
+ * runs the cycles of Sec. 4.2 (Gauss-Seidel Eq. (2.3), restriction and
+ * prolongation Eqs. (2.5)-(2.6), flat energy correction Eq. (3.9) or iterate
+ * recombination Eq. (3.13), dense coarsest solve, mean subtraction).
+ *
+ * Conventions for every entry point:
+ *  - Graph input: the off-diagonal pattern of A as a CSR holding both
+ *    directions of every edge, columns strictly increasing within each row,
+ *    no self loops, w_uv == w_vu bit for bit, w > 0 and finite.  a_uu is
+ *    implied (sum of the row's weights).  Fewer than 2^31 stored entries.
+ *  - "device" pointers must be device-accessible memory of the current CUDA
+ *    device; "host" pointers ordinary host memory.  The caller owns all
+ *    arrays it passes.  lamg_setup copies what it needs; the caller may free
+ *    its inputs when lamg_setup returns.  The handle owns the hierarchy and
+ *    its workspaces until lamg_free.
+ *  - All device work is ordered on the given stream (0 = legacy default).
+ *    Calls that return statistics or convergence decisions synchronise the
+ *    stream before returning; their device outputs are then complete.
+ *  - Every function returns a lamg_status and never aborts; the text of the
+ *    last error of the calling thread is available from lamg_last_error().
+ *  - A handle may be used by one thread at a time.
+ */
+#ifndef LAMG_H
+#define LAMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lamg_ctx *lamg_handle;
+typedef void *lamg_stream;   /* a cudaStream_t */
+
+typedef enum {
+    LAMG_OK = 0,
+    LAMG_ERR_ARG = 1,              /* malformed argument or CSR                      */
+    LAMG_ERR_NOT_SYMMETRIC = 2,    /* w_uv != w_vu or a missing reverse entry        */
+    LAMG_ERR_BAD_WEIGHT = 3,       /* w <= 0, NaN or Inf                              */
+    LAMG_ERR_DISCONNECTED = 4,     /* the graph has more than one component           */
+    LAMG_ERR_RHS_NOT_ZERO_SUM = 5, /* |1^T b| > 1e-10 ||b||_1 (Sec. 1 needs b zero-sum) */
+    LAMG_ERR_OOM = 6,              /* device allocation failed                        */
+    LAMG_ERR_CUDA = 7,             /* a CUDA call failed (message in lamg_last_error) */
+    LAMG_ERR_NOT_CONVERGED = 8,    /* max_cycles reached above tol; x is the iterate  */
+    LAMG_ERR_TIMEOUT = 9           /* a bounded device wait ran out                   */
+} lamg_status;
+
+typedef enum { LAMG_FP64 = 0, LAMG_FP32_IR = 1 } lamg_precision;
+
+/* Parameters of Sec. 4; lamg_default_options fills the paper's values and the
+ * build's readings of the points the paper leaves open. */
+typedef struct {
+    double   gamma;            /* cycle index (Sec. 4.1): 1.5                          */
+    int32_t  k_finest;         /* TVs at the finest level (Sec. 4.1): 4                 */
+    int32_t  k_max;            /* TVs grow up to this at coarse levels: 10 (max 16)     */
+    int32_t  k_step;           /* TV growth per level: 1                                */
+    int32_t  nu_tv;            /* GS sweeps per TV (Sec. 4.1): 3                        */
+    int32_t  nu1, nu2;         /* pre/post relaxations (Eq. (4.1)): 1, 2                */
+    int32_t  n_coarsest;       /* stop coarsening below this many nodes: 150           */
+    double   q_max;            /* energy-ratio acceptance (Sec. 3.4.5): 2.5             */
+    double   hub_factor;       /* hub test (Sec. 3.4.1 footnote): 8                     */
+    double   weak_tol;         /* weak-edge threshold: 1e-8                             */
+    double   alpha_stall;      /* a level whose best coarsening ratio exceeds this is final: 0.95 */
+    double   relax_fast_ratio; /* TV energy ratio per sweep at or below which GS counts as
+                                  fast and the level is final; <= 0 disables (default 0) */
+    int32_t  max_rounds;       /* aggregation stages per level: 8                       */
+    int32_t  max_levels;       /* depth limit: 100                                      */
+    int32_t  dense_max;        /* largest coarsest level solved by the dense inverse: 1024 */
+    int32_t  coarse_sweeps;    /* GS sweeps when the coarsest level is larger: 20      */
+    double   mu_flat;          /* flat energy correction (Eq. (3.10), Q = 2): 4/3      */
+    uint64_t seed;             /* seed of the counter-based generator: 1               */
+    int32_t  adaptive;         /* 1: iterate recombination (Eq. (3.13)); 0: flat mu    */
+    int32_t  max_cycles;       /* solve limit: 200                                     */
+    int32_t  ir_inner;         /* FP32 cycles per FP64 refinement step: 2               */
+    int32_t  validate;         /* 1: check the input graph (symmetry, weights, connectivity) */
+    int32_t  keep_setup_data;  /* 1: keep TVs, affinities, energy ratios for inspection */
+} lamg_options;
+
+typedef struct {
+    int32_t levels;            /* hierarchy depth L                                     */
+    int32_t cycles;            /* cycles run by the last solve (FP32 cycles under IR)   */
+    int32_t outer_steps;       /* FP64 refinement steps (IR) or cycles (FP64)          */
+    int32_t status;            /* status of the last solve                             */
+    double  rel_res;           /* ||b - A x||_2 / ||b||_2 at exit (FP64)                */
+    double  acf;               /* (r_p / r_0)^(1/p), Sec. 5.1                           */
+    double  t_setup_s;         /* wall time of lamg_setup                              */
+    double  t_solve_s;         /* wall time of the last solve                          */
+    int64_t nnz_total;         /* stored off-diagonal entries over all levels          */
+    int64_t bytes_per_cycle;   /* algorithmic bytes of one FP64 cycle (model)          */
+    int64_t bytes_per_cycle32; /* same for one FP32 cycle                              */
+} lamg_stats;
+
+void        lamg_default_options(lamg_options *opt);
+const char *lamg_last_error(void);
+
+/* lamg_setup -- build the hierarchy (Sec. 4.1).
+ *  n        number of nodes, 1 <= n < 2^31
+ *  row_ptr  device, int64[n+1], row_ptr[0] = 0
+ *  col      device, int32[row_ptr[n]]
+ *  w        device, FP64 (w_is_fp32 = 0) or FP32 (w_is_fp32 = 1) [row_ptr[n]]
+ *  opt      host, may be NULL for defaults
+ *  out      host; receives the handle (NULL on error)
+ * Errors: LAMG_ERR_ARG / NOT_SYMMETRIC / BAD_WEIGHT / DISCONNECTED when
+ * opt->validate is set, LAMG_ERR_OOM, LAMG_ERR_CUDA. */
+lamg_status lamg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
+                       int32_t w_is_fp32, const lamg_options *opt, lamg_stream stream,
+                       lamg_handle *out);
+
+/* lamg_solve -- cycles of Sec. 4.2 until ||b - A x||_2 <= tol ||b||_2.
+ *  b  device FP64[n], zero-sum (LAMG_ERR_RHS_NOT_ZERO_SUM otherwise)
+ *  x  device FP64[n]; in: initial guess, out: the zero-mean iterate
+ *  precision  LAMG_FP64: FP64 cycles.  LAMG_FP32_IR: FP32 cycles inside FP64
+ *             iterative refinement (outer residual, mean projection and the
+ *             coarsest solve in FP64).
+ *  st  host, may be NULL.
+ * Returns LAMG_ERR_NOT_CONVERGED (x valid) when max_cycles is reached. */
+lamg_status lamg_solve(lamg_handle h, const double *b, double *x, double tol,
+                       lamg_precision precision, lamg_stream stream, lamg_stats *st);
+
+/* lamg_solve_host -- lamg_solve with host arrays; the host<->device copies
+ * run on the stream inside the call (end-to-end form). */
+lamg_status lamg_solve_host(lamg_handle h, const double *b_host, double *x_host, double tol,
+                            lamg_precision precision, lamg_stream stream, lamg_stats *st);
+
+/* lamg_solve_batched -- nrhs right-hand sides on one hierarchy (the solve is
+ * re-used, Sec. 1: "a smaller cost to re-solve the system for multiple b's").
+ *  B, X  device FP64, row-interleaved: entry (u, j) at [u * ld + j], ld >= nrhs
+ *  Every column of B must be zero-sum.  Each column converges to tol; the
+ *  call returns when all have.  st: host array of nrhs stats, may be NULL. */
+lamg_status lamg_solve_batched(lamg_handle h, int32_t nrhs, const double *B, double *X,
+                               int64_t ld, double tol, lamg_precision precision,
+                               lamg_stream stream, lamg_stats *st);
+
+/* lamg_adjoint -- gradient of a scalar loss L(x) of the solution x = A^+ b.
+ *  Given g = dL/dx (device FP64[n]) it solves A lambda = g - mean(g) with the
+ *  same hierarchy (A is symmetric), so dL/db = lambda, and, for the m edges
+ *  (eu[e], ev[e]) (device int32[m]), dL/dw_e = -(lambda_u - lambda_v)(x_u - x_v),
+ *  from dA/dw_uv = (e_u - e_v)(e_u - e_v)^T (Eq. (1.2)).
+ *  x       device FP64[n], the solution of the forward solve
+ *  lambda  device FP64[n], out
+ *  dw      device, FP64 (dw_is_fp32 = 0) or FP32 [m], out; NULL skips it */
+lamg_status lamg_adjoint(lamg_handle h, const double *x, const double *g, double *lambda,
+                         const int32_t *eu, const int32_t *ev, int64_t m, void *dw,
+                         int32_t dw_is_fp32, double tol, lamg_precision precision,
+                         lamg_stream stream, lamg_stats *st);
+
+/* lamg_free -- release the handle and everything it owns (NULL is a no-op). */
+void lamg_free(lamg_handle h);
+
+/* ---- introspection (tests and benchmarks) ---- */
+
+/* Per-level summary.  info[0..15]: n, nnz, ncolours, K, nc, rounds, sel_round,
+ * coarsest, stop_reason, alpha (FP64 bits), gamma_l (FP64 bits), tv_ratio (FP64
+ * bits), jp_rounds, dense (1 if the coarsest is solved by the dense inverse). */
+lamg_status lamg_level_info(lamg_handle h, int32_t level, int64_t *info_host);
+
+/* Copy one per-level array to host memory.  Fields (natural node order):
+ *  0 row_ptr int64[n+1]   1 col int32[nnz]   2 w FP64[nnz]   3 colour int32[n]
+ *  4 agg int32[n]         5 state int32[n]   6 hub uint8[n]
+ *  7 tv FP64[n*K]         8 affinity FP64[nnz]  9 q FP64[nnz]   10 score FP64[nnz]
+ * Fields 7-9 need keep_setup_data.  Returns LAMG_ERR_ARG for a field that the
+ * level does not have. */
+lamg_status lamg_level_copy(lamg_handle h, int32_t level, int32_t field, void *host_dst,
+                            int64_t bytes);
+
+/* Run exactly one cycle plus the mean subtraction on device x (FP64 cycles). */
+lamg_status lamg_cycle(lamg_handle h, const double *b, double *x, int32_t adaptive,
+                       lamg_stream stream);
+
+/* Average device time, in milliseconds, and count of the finest-level
+ * relaxation sweep launches timed with CUDA events while profiling is on
+ * (enable = 1 resets the counters; 0 stops recording). */
+lamg_status lamg_profile(lamg_handle h, int32_t enable, double *avg_ms, int64_t *count,
+                         int64_t *bytes_per_launch);
+
+/* Number of this library's kernel launches since it was loaded (each kernel
+ * of a launched CUDA graph counts once per graph launch). */
+lamg_status lamg_launch_count(int64_t *count_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

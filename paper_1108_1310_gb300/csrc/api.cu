@@ -1,0 +1,305 @@
+// api.cu -- the extern "C" entry points declared in include/lamg.h.  Each one
+// validates its arguments, runs the device work on the caller's stream and
+// converts every failure into a lamg_status (never aborts).
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "lamg_internal.cuh"
+
+namespace lamg {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+static thread_local int t_capturing = 0;
+static thread_local int64_t t_captured = 0;
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+void note_launch() {
+    if (t_capturing) t_captured++;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void note_graph_launch(int64_t kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
+void begin_capture_count() { t_capturing = 1; t_captured = 0; }
+int64_t end_capture_count() { t_capturing = 0; return t_captured; }
+int64_t launch_count() { return g_launches.load(); }
+
+template <class F>
+static lamg_status guarded(F &&f) {
+    try {
+        f();
+        g_last_error.clear();
+        return LAMG_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return LAMG_ERR_OOM;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return LAMG_ERR_CUDA;
+    }
+}
+
+static int64_t level_bytes(const SolveLevel &V, int wb) {
+    return V.nnz * (4 + wb) + (int64_t)(V.n + 1) * 4 + (int64_t)V.n * wb * 3;
+}
+
+// Two-level steps per level in one cycle, by replaying the schedule of the
+// cycle (the k-th coarse correction of level l runs ceil((k+1) g) - ceil(k g)
+// steps of level l+1, counters reset per cycle).
+static void count_steps(lamg_ctx *h, int l, int theta, std::vector<int32_t> &visits,
+                        std::vector<double> &steps) {
+    for (int i = 0; i < theta; i++) {
+        steps[l] += 1.0;
+        if (l + 1 < h->L - 1) {
+            const int32_t k = visits[l]++;
+            const double g = h->sl[l].gamma_l;
+            int th = (int)(std::ceil((double)(k + 1) * g) - std::ceil((double)k * g));
+            th = th < 1 ? 1 : (th > 2 ? 2 : th);
+            count_steps(h, l + 1, th, visits, steps);
+        } else {
+            steps[l + 1] += 1.0;  // one coarsest solve per step of level L-2
+        }
+    }
+}
+
+// Algorithmic bytes of one cycle: per two-level step at level l, (nu1 + nu2)
+// sweeps, a residual (sweep bytes + r write), restriction (r read + member
+// index + b^c, x^c writes), the prolongation (agg + x read/write + x^c
+// gather); plus the coarsest solves (dense inverse read, or its sweeps).
+static int64_t cycle_bytes(lamg_ctx *h, int wb) {
+    const int L = h->L;
+    if (L == 1) {
+        const SolveLevel &C = h->lv[0];
+        return C.dense ? (int64_t)C.n * C.n * 8 : h->opt.coarse_sweeps * level_bytes(C, wb);
+    }
+    std::vector<int32_t> visits(L, 0);
+    std::vector<double> steps(L, 0.0);
+    count_steps(h, 0, 1, visits, steps);
+    double total = 0.0;
+    for (int l = 0; l + 1 < L; l++) {
+        const SolveLevel &V = h->lv[l];
+        const double sw = (double)level_bytes(V, wb);
+        const double res = sw + (double)V.n * wb;
+        const double rst = (double)V.n * (wb + 4) + (double)h->lv[l + 1].n * 2 * wb;
+        const double pro = (double)V.n * (4 + 2 * wb);
+        total += steps[l] * ((h->opt.nu1 + h->opt.nu2) * sw + res + rst + pro);
+    }
+    const SolveLevel &C = h->lv[L - 1];
+    total += steps[L - 1] * (C.dense ? (double)C.n * C.n * 8 : h->opt.coarse_sweeps * (double)level_bytes(C, wb));
+    return (int64_t)total;
+}
+
+}  // namespace lamg
+
+using namespace lamg;
+
+extern "C" {
+
+void lamg_default_options(lamg_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->gamma = 1.5;
+    o->k_finest = 4;
+    o->k_max = 10;
+    o->k_step = 1;
+    o->nu_tv = 3;
+    o->nu1 = 1;
+    o->nu2 = 2;
+    o->n_coarsest = 150;
+    o->q_max = 2.5;
+    o->hub_factor = 8.0;
+    o->weak_tol = 1e-8;
+    o->alpha_stall = 0.95;
+    o->relax_fast_ratio = 0.0;
+    o->max_rounds = 8;
+    o->max_levels = 100;
+    o->dense_max = 1024;
+    o->coarse_sweeps = 20;
+    o->mu_flat = 4.0 / 3.0;
+    o->seed = 1;
+    o->adaptive = 1;
+    o->max_cycles = 200;
+    o->ir_inner = 2;
+    o->validate = 1;
+    o->keep_setup_data = 0;
+}
+
+const char *lamg_last_error(void) { return g_last_error.c_str(); }
+
+lamg_status lamg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
+                       int32_t w_is_fp32, const lamg_options *opt, lamg_stream stream, lamg_handle *out) {
+    if (out) *out = nullptr;
+    lamg_ctx *h = nullptr;
+    lamg_status st = guarded([&] {
+        LAMG_REQUIRE(out != nullptr, LAMG_ERR_ARG, "out is NULL");
+        LAMG_REQUIRE(n >= 1 && n < ((int64_t)1 << 31), LAMG_ERR_ARG, "n must be in [1, 2^31)");
+        LAMG_REQUIRE(row_ptr != nullptr, LAMG_ERR_ARG, "NULL row_ptr");
+        auto t0 = std::chrono::steady_clock::now();
+        h = new lamg_ctx();
+        if (opt) h->opt = *opt; else lamg_default_options(&h->opt);
+        LAMG_REQUIRE(h->opt.gamma >= 1.0 && h->opt.nu_tv >= 0 && h->opt.nu1 >= 0 && h->opt.nu2 >= 0 &&
+                         h->opt.k_finest >= 1 && h->opt.max_rounds >= 1 && h->opt.max_levels >= 1 &&
+                         h->opt.dense_max >= 1,
+                     LAMG_ERR_ARG, "invalid options");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (h->opt.validate) validate_graph(n, row_ptr, col, w, w_is_fp32, s);
+        build_hierarchy(h, n, row_ptr, col, w, w_is_fp32, s);
+        build_solve_layout(h, s);
+        h->n = n;
+        auto t1 = std::chrono::steady_clock::now();
+        h->t_setup_s = std::chrono::duration<double>(t1 - t0).count();
+        int64_t tot = 0;
+        for (auto &V : h->lv) tot += V.nnz;
+        h->last.levels = h->L;
+        h->last.t_setup_s = h->t_setup_s;
+        h->last.nnz_total = tot;
+        h->last.bytes_per_cycle = cycle_bytes(h, 8);
+        h->last.bytes_per_cycle32 = cycle_bytes(h, 4);
+    });
+    if (st != LAMG_OK) {
+        if (h) { release_solve(h); delete h; }
+        return st;
+    }
+    *out = h;
+    return LAMG_OK;
+}
+
+lamg_status lamg_solve(lamg_handle h, const double *b, double *x, double tol, lamg_precision p,
+                       lamg_stream stream, lamg_stats *st) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && b && x, LAMG_ERR_ARG, "NULL argument");
+        LAMG_REQUIRE(p == LAMG_FP64 || p == LAMG_FP32_IR, LAMG_ERR_ARG, "unknown precision");
+        LAMG_REQUIRE(tol >= 0.0, LAMG_ERR_ARG, "tol must be >= 0");
+        solve_device(h, b, x, tol, p, (cudaStream_t)stream, st);
+    });
+}
+
+lamg_status lamg_solve_host(lamg_handle h, const double *b_host, double *x_host, double tol,
+                            lamg_precision p, lamg_stream stream, lamg_stats *st) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && b_host && x_host, LAMG_ERR_ARG, "NULL argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t bytes = sizeof(double) * (size_t)h->n;
+        if (!h->bnat.get()) { h->bnat.alloc(h->n); h->xnat.alloc(h->n); }
+        LAMG_CUDA(cudaMemcpyAsync(h->bnat.get(), b_host, bytes, cudaMemcpyHostToDevice, s));
+        LAMG_CUDA(cudaMemcpyAsync(h->xnat.get(), x_host, bytes, cudaMemcpyHostToDevice, s));
+        lamg_status inner = LAMG_OK;
+        try {
+            solve_device(h, h->bnat.get(), h->xnat.get(), tol, p, s, st);
+        } catch (const Error &e) {
+            if (e.status != LAMG_ERR_NOT_CONVERGED) throw;
+            inner = e.status;
+        }
+        LAMG_CUDA(cudaMemcpyAsync(x_host, h->xnat.get(), bytes, cudaMemcpyDeviceToHost, s));
+        LAMG_CUDA(cudaStreamSynchronize(s));
+        if (inner != LAMG_OK) throw Error{inner, "max_cycles reached before tol"};
+    });
+}
+
+lamg_status lamg_solve_batched(lamg_handle h, int32_t nrhs, const double *B, double *X, int64_t ld,
+                               double tol, lamg_precision p, lamg_stream stream, lamg_stats *st) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && B && X && nrhs >= 1 && ld >= nrhs, LAMG_ERR_ARG, "bad batched arguments");
+        solve_batched_device(h, nrhs, B, X, ld, tol, p, (cudaStream_t)stream, st);
+    });
+}
+
+lamg_status lamg_adjoint(lamg_handle h, const double *x, const double *g, double *lambda,
+                         const int32_t *eu, const int32_t *ev, int64_t m, void *dw, int32_t dw_is_fp32,
+                         double tol, lamg_precision p, lamg_stream stream, lamg_stats *st) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && x && g && lambda, LAMG_ERR_ARG, "NULL argument");
+        LAMG_REQUIRE(!dw || (eu && ev && m >= 0), LAMG_ERR_ARG, "edge arrays required for dw");
+        adjoint_device(h, x, g, lambda, eu, ev, m, dw, dw_is_fp32, tol, p, (cudaStream_t)stream, st);
+    });
+}
+
+void lamg_free(lamg_handle h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    release_solve(h);
+    delete h;
+}
+
+lamg_status lamg_level_info(lamg_handle h, int32_t level, int64_t *info) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && info && level >= 0 && level < h->L, LAMG_ERR_ARG, "bad level");
+        const SetupLevel &S = h->sl[level];
+        std::memset(info, 0, sizeof(int64_t) * 16);
+        info[0] = S.n; info[1] = S.nnz; info[2] = S.ncolours; info[3] = S.K; info[4] = S.nc;
+        info[5] = S.rounds; info[6] = S.sel_round; info[7] = S.coarsest; info[8] = S.stop_reason;
+        std::memcpy(&info[9], &S.alpha, 8);
+        std::memcpy(&info[10], &S.gamma_l, 8);
+        std::memcpy(&info[11], &S.tv_ratio, 8);
+        info[12] = S.jp_rounds;
+        info[13] = h->lv.empty() ? 0 : h->lv[level].dense;
+    });
+}
+
+lamg_status lamg_level_copy(lamg_handle h, int32_t level, int32_t field, void *dst, int64_t bytes) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && dst && level >= 0 && level < h->L, LAMG_ERR_ARG, "bad level");
+        const SetupLevel &S = h->sl[level];
+        const void *src = nullptr;
+        size_t need = 0;
+        std::vector<int64_t> rp64;
+        switch (field) {
+            case 0: {
+                std::vector<int32_t> rp32(S.n + 1);
+                LAMG_CUDA(cudaMemcpy(rp32.data(), S.rp.get(), sizeof(int32_t) * (S.n + 1), cudaMemcpyDeviceToHost));
+                rp64.assign(rp32.begin(), rp32.end());
+                need = sizeof(int64_t) * (S.n + 1);
+                LAMG_REQUIRE(bytes == (int64_t)need, LAMG_ERR_ARG, "size mismatch");
+                std::memcpy(dst, rp64.data(), need);
+                return;
+            }
+            case 1: src = S.col.get(); need = S.col.bytes(); break;
+            case 2: src = S.w.get(); need = S.w.bytes(); break;
+            case 3: src = S.colour.get(); need = S.colour.bytes(); break;
+            case 4: src = S.agg.get(); need = S.agg.bytes(); break;
+            case 5: src = S.state.get(); need = S.state.bytes(); break;
+            case 6: src = S.hub.get(); need = S.hub.bytes(); break;
+            case 7: src = S.tv.get(); need = S.tv.bytes(); break;
+            case 8: src = S.aff.get(); need = S.aff.bytes(); break;
+            case 9: src = S.q.get(); need = S.q.bytes(); break;
+            case 10: src = S.score.get(); need = S.score.bytes(); break;
+            default: break;
+        }
+        const bool empty_ok = (field == 1 || field == 2) && S.nnz == 0;
+        LAMG_REQUIRE(src != nullptr || empty_ok, LAMG_ERR_ARG, "field not available on this level");
+        LAMG_REQUIRE(bytes == (int64_t)need, LAMG_ERR_ARG, "size mismatch");
+        if (need) LAMG_CUDA(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
+    });
+}
+
+lamg_status lamg_cycle(lamg_handle h, const double *b, double *x, int32_t adaptive, lamg_stream stream) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && b && x, LAMG_ERR_ARG, "NULL argument");
+        cycle_device(h, b, x, adaptive, (cudaStream_t)stream);
+    });
+}
+
+lamg_status lamg_profile(lamg_handle h, int32_t enable, double *avg_ms, int64_t *count, int64_t *bytes) {
+    return guarded([&] {
+        LAMG_REQUIRE(h, LAMG_ERR_ARG, "NULL handle");
+        if (avg_ms) *avg_ms = h->prof_count ? h->prof_ms / (double)h->prof_count : 0.0;
+        if (count) *count = h->prof_count;
+        if (bytes) *bytes = h->prof_bytes;
+        if (enable) { h->prof_ms = 0.0; h->prof_count = 0; }
+        h->prof_on = enable ? 1 : 0;
+    });
+}
+
+lamg_status lamg_launch_count(int64_t *count) {
+    return guarded([&] {
+        LAMG_REQUIRE(count, LAMG_ERR_ARG, "NULL argument");
+        *count = launch_count();
+    });
+}
+
+}  // extern "C"

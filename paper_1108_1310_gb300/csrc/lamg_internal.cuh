@@ -1,0 +1,230 @@
+// lamg_internal.cuh -- internal data structures and helpers of the GB300 LAMG
+// library (Livne & Brandt, arXiv 1108.1310).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lamg.h"
+
+namespace lamg {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+
+struct Error {
+    lamg_status status;
+    std::string msg;
+};
+
+void set_last_error(const std::string &msg);
+
+#define LAMG_CUDA(expr)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            throw ::lamg::Error{e_ == cudaErrorMemoryAllocation ? LAMG_ERR_OOM : LAMG_ERR_CUDA, \
+                                std::string(#expr) + ": " + cudaGetErrorString(e_) +     \
+                                    " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"}; \
+        }                                                                                \
+    } while (0)
+
+// Every kernel launch is followed by LAMG_CHECK_LAUNCH(), which also counts
+// it (launches issued while a graph is being captured are counted per graph
+// and added each time the graph is launched).
+void note_launch();
+void note_graph_launch(int64_t kernels);
+void begin_capture_count();
+int64_t end_capture_count();
+int64_t launch_count();
+
+#define LAMG_CHECK_LAUNCH()                  \
+    do {                                     \
+        ::lamg::note_launch();               \
+        LAMG_CUDA(cudaGetLastError());       \
+    } while (0)
+
+#define LAMG_REQUIRE(cond, status, text)                                                 \
+    do {                                                                                 \
+        if (!(cond)) throw ::lamg::Error{(status), std::string(text)};                   \
+    } while (0)
+
+// Rows longer than this are processed by a whole warp (canonical sum switches
+// from left-to-right to 32 lane partials + halving tree at the same length).
+constexpr int kLongRow = 32;
+
+// ---------------------------------------------------------------------------
+// Device buffers (owned, freed with the handle)
+// ---------------------------------------------------------------------------
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) LAMG_CUDA(cudaMalloc((void **)&p, sizeof(T) * count));
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    T *get() const { return p; }
+    size_t bytes() const { return sizeof(T) * n; }
+};
+
+// ---------------------------------------------------------------------------
+// Hierarchy
+// ---------------------------------------------------------------------------
+
+// Setup-phase view of one level, natural node order (Sec. 4.1).
+struct SetupLevel {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    DBuf<int32_t> rp, col;         // CSR, int32 row pointers (nnz < 2^31)
+    DBuf<double> w;                // FP64 weights
+    DBuf<int32_t> colour;          // Jones-Plassmann colour
+    int32_t ncolours = 0, jp_rounds = 0;
+    DBuf<int32_t> corder;          // nodes sorted by (colour, id)
+    std::vector<int32_t> cstart;   // colour ranges in corder (ncolours + 1)
+    DBuf<int32_t> agg, state;      // aggregation result (non-coarsest levels)
+    DBuf<uint8_t> hub;
+    DBuf<double> tv, aff, q, score;  // kept only with keep_setup_data
+    int32_t K = 0, nc = 0, rounds = 0, sel_round = 0;
+    int32_t coarsest = 0, stop_reason = 0;
+    double alpha = 0.0, gamma_l = 0.0, tv_ratio = 0.0;
+};
+
+// Solve-phase layout of one level: rows permuted so that each colour is a
+// contiguous range, short rows (<= kLongRow entries) before long rows within
+// each colour; vectors live in this order.
+struct SolveLevel {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    DBuf<int32_t> rp, col;         // permuted CSR (columns in permuted ids)
+    DBuf<double> w64;
+    DBuf<float> w32;
+    DBuf<int32_t> perm;            // perm[i] = natural id of permuted row i
+    std::vector<int32_t> cs;       // colour c rows: [cs[c], cs[c+1])
+    std::vector<int32_t> cl;       // long rows of colour c: [cl[c], cs[c+1])
+    DBuf<int32_t> longrows;        // all long rows (permuted ids)
+    int32_t nlong = 0;
+    // transfer to the next coarser level (absent on the coarsest level)
+    DBuf<int32_t> pagg;            // permuted fine row -> permuted coarse id
+    DBuf<int32_t> mptr, mlist;     // members of each coarse id (permuted fine ids)
+    DBuf<int32_t> longagg;         // coarse ids with > kLongRow members
+    int32_t nlongagg = 0;
+    // coarsest level
+    int32_t dense = 0;
+    DBuf<double> minv;             // (A + 11^T/n)^-1, n x n, if dense
+};
+
+// Per-level vectors of one precision.
+template <class T>
+struct LevelVecs {
+    DBuf<T> x, b, r, xs0, xs1, rs0, rs1;
+};
+
+struct Hierarchy;
+
+}  // namespace lamg
+
+struct lamg_ctx {
+    lamg_options opt;
+    std::vector<lamg::SetupLevel> sl;
+    std::vector<lamg::SolveLevel> lv;
+    int32_t L = 0;
+    int64_t n = 0;
+    double t_setup_s = 0.0;
+    // solve workspaces
+    std::vector<lamg::LevelVecs<double>> v64;
+    std::vector<lamg::LevelVecs<float>> v32;
+    lamg::DBuf<double> scratch;     // reductions, recombination coefficients
+    lamg::DBuf<double> xnat, bnat;  // level-1 vectors for host-array solves
+    lamg::DBuf<double> r64;         // FP64 outer residual (permuted)
+    double *host_pinned = nullptr;  // pinned readback slots
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t g64 = nullptr, g32 = nullptr;   // captured cycles
+    int32_t g64_adaptive = -1, g32_adaptive = -1;
+    int64_t g64_kernels = 0, g32_kernels = 0, g64p_kernels = 0, g32p_kernels = 0;
+    // profiling of the finest-level sweeps
+    int32_t prof_on = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    double prof_ms = 0.0;
+    int64_t prof_count = 0;
+    int64_t prof_bytes = 0;
+    cudaGraphExec_t g64p = nullptr, g32p = nullptr;  // profiled variants
+    int32_t g64p_adaptive = -1, g32p_adaptive = -1;
+    lamg_stats last{};
+};
+
+namespace lamg {
+
+// setup.cu
+void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                     const void *w, int32_t w_is_fp32, cudaStream_t s);
+void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
+                    int32_t w_is_fp32, cudaStream_t s);
+
+// solve.cu
+void build_solve_layout(lamg_ctx *h, cudaStream_t s);
+void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_precision p,
+                  cudaStream_t s, lamg_stats *st);
+void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X, int64_t ld,
+                          double tol, lamg_precision p, cudaStream_t s, lamg_stats *st);
+void cycle_device(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s);
+void adjoint_device(lamg_ctx *h, const double *x, const double *g, double *lambda,
+                    const int32_t *eu, const int32_t *ev, int64_t m, void *dw, int32_t dw32,
+                    double tol, lamg_precision p, cudaStream_t s, lamg_stats *st);
+void release_solve(lamg_ctx *h);
+
+// prims.cu
+void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+template <class K, class V>
+void radix_sort_pairs(K *keys, V *vals, K *ktmp, V *vtmp, int64_t n, int nbits, cudaStream_t s);
+int64_t compact_indices(const uint8_t *flags, int32_t *out_idx, int64_t n, cudaStream_t s);
+int32_t reduce_max_i32(const int32_t *a, int64_t n, cudaStream_t s);
+int64_t count_equal_i32(const int32_t *a, int64_t n, int32_t value, cudaStream_t s);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Temporary device memory from the stream-ordered pool, freed at scope exit.
+template <class T>
+struct Tmp {
+    T *p = nullptr;
+    cudaStream_t s;
+    Tmp(size_t count, cudaStream_t st) : s(st) {
+        if (count) LAMG_CUDA(cudaMallocAsync((void **)&p, sizeof(T) * count, st));
+    }
+    ~Tmp() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    Tmp(const Tmp &) = delete;
+    Tmp &operator=(const Tmp &) = delete;
+    T *get() const { return p; }
+};
+
+template <class T>
+inline T read_scalar(const T *dptr, cudaStream_t s) {
+    T v;
+    LAMG_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
+    LAMG_CUDA(cudaStreamSynchronize(s));
+    return v;
+}
+
+}  // namespace lamg

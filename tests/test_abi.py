@@ -1,0 +1,81 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol that
+include/lamg.h declares, and the Python binding's structs match the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lamg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1108_1310_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lamg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_five_entry_points():
+    names = _declared()
+    for n in ("lamg_setup", "lamg_solve", "lamg_solve_batched", "lamg_adjoint", "lamg_free"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layout_matches_header(tmp_path):
+    from paper_1108_1310_gb300 import lamg as L
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "lamg.h"\n'
+        "int main(void){\n"
+        'printf("%zu %zu\\n", sizeof(lamg_options), sizeof(lamg_stats));\n'
+        + "".join(f'printf("%zu\\n", offsetof(lamg_options, {f}));\n' for f, _ in L.lamg_options._fields_)
+        + "".join(f'printf("%zu\\n", offsetof(lamg_stats, {f}));\n' for f, _ in L.lamg_stats._fields_)
+        + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    out = [int(t) for t in subprocess.check_output([str(exe)]).split()]
+    assert out[0] == ctypes.sizeof(L.lamg_options)
+    assert out[1] == ctypes.sizeof(L.lamg_stats)
+    offs = [getattr(L.lamg_options, f).offset for f, _ in L.lamg_options._fields_] + \
+           [getattr(L.lamg_stats, f).offset for f, _ in L.lamg_stats._fields_]
+    assert out[2:] == offs
+
+
+def test_default_options_are_the_papers(lib):
+    from paper_1108_1310_gb300 import lamg as L
+    o = L.lamg_default_options()
+    assert (o.gamma, o.k_finest, o.k_max, o.nu_tv, o.nu1, o.nu2, o.n_coarsest) == (1.5, 4, 10, 3, 1, 2, 150)
+    assert (o.q_max, o.hub_factor, o.mu_flat) == (2.5, 8.0, 4.0 / 3.0)
+    assert o.adaptive == 1
+
+
+def test_default_options_match_the_oracle(lib):
+    import oracle
+    from paper_1108_1310_gb300 import lamg as L
+    a, b = L.lamg_default_options(), oracle.default_opts()
+    for f, _ in oracle.Opts._fields_:
+        assert getattr(a, f) == getattr(b, f), f
+
+
+def test_errors_without_gpu_are_status_codes(lib):
+    from paper_1108_1310_gb300 import lamg as L
+    h = ctypes.c_void_p()
+    # n = 0 is rejected before any device work
+    st = L._lib.lamg_setup(0, None, None, None, 0, None, None, ctypes.byref(h))
+    assert st == L.LAMG_ERR_ARG and not h.value
+    assert b"n must be" in L._lib.lamg_last_error()
+    L._lib.lamg_free(None)  # no-op
