@@ -189,7 +189,7 @@ def main():
     w = torch.tensor(g.w, device=dev).to(w_dtype)
     b = torch.tensor(b_host, device=dev)
     x = torch.zeros_like(b)
-    opt = L.lamg_default_options(validate=1)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
     def step(profile=False):

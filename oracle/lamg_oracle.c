@@ -69,10 +69,20 @@ static double tv_uniform(uint64_t z) {
 /* ------------------------------------------------------------------------- */
 /* Canonical summation order (build reading; every setup float that feeds an   */
 /* integer decision is summed this way on both sides).                         */
-/*   len <= 32 : left to right from +0.0.                                      */
-/*   len  > 32 : 32 partial sums p_j = t_j + t_{j+32} + ... (left to right),   */
-/*               then p_j += p_{j+h} for h = 16, 8, 4, 2, 1 (j < h); p_0.      */
+/*   len <= 32   : left to right from +0.0.                                    */
+/*   len <= 512  : 32 partial sums p_j = t_j + t_{j+32} + ... (left to right), */
+/*                 then the halving tree p_j += p_{j+h}, h = 16, 8, 4, 2, 1;   */
+/*                 the result is p_0.                                          */
+/*   len  > 512  : 1024 partial sums p_j = t_j + t_{j+1024} + ...; each group  */
+/*                 of 32 consecutive p_j is reduced by the halving tree, and   */
+/*                 the 32 group results by the halving tree again.             */
 /* ------------------------------------------------------------------------- */
+
+static double tree32(double *p) {
+    for (int h = 16; h >= 1; h /= 2)
+        for (int j = 0; j < h; j++) p[j] = p[j] + p[j + h];
+    return p[0];
+}
 
 double orc_canon_sum(const double *t, int64_t len) {
     if (len <= 32) {
@@ -80,20 +90,27 @@ double orc_canon_sum(const double *t, int64_t len) {
         for (int64_t i = 0; i < len; i++) s = s + t[i];
         return s;
     }
-    double p[32];
-    for (int j = 0; j < 32; j++) {
-        p[j] = 0.0;
-        for (int64_t i = j; i < len; i += 32) p[j] = p[j] + t[i];
+    if (len <= 512) {
+        double p[32];
+        for (int j = 0; j < 32; j++) {
+            p[j] = 0.0;
+            for (int64_t i = j; i < len; i += 32) p[j] = p[j] + t[i];
+        }
+        return tree32(p);
     }
-    for (int h = 16; h >= 1; h /= 2)
-        for (int j = 0; j < h; j++) p[j] = p[j] + p[j + h];
-    return p[0];
+    double p[1024], q[32];
+    for (int j = 0; j < 1024; j++) {
+        p[j] = 0.0;
+        for (int64_t i = j; i < len; i += 1024) p[j] = p[j] + t[i];
+    }
+    for (int g = 0; g < 32; g++) q[g] = tree32(p + 32 * g);
+    return tree32(q);
 }
 
-/* Long vectors: chunks of 4096 terms, each summed canonically; the chunk sums
+/* Long vectors: chunks of 512 terms, each summed canonically; the chunk sums
  * are summed the same way, recursively. */
 double orc_canon_sum_global(const double *t, int64_t len) {
-    const int64_t C = 4096;
+    const int64_t C = 512;
     if (len <= C) return orc_canon_sum(t, len);
     int64_t nch = (len + C - 1) / C;
     double *part = (double *)malloc(sizeof(double) * (size_t)nch);
@@ -172,13 +189,15 @@ static void diag_canon(int64_t n, const int64_t *rp, const double *w, double *di
 
 /* ------------------------------------------------------------------------- */
 /* Colouring (build reading of the relaxation order; the paper's GS of         */
-/* Eq. (2.3) is lexicographic).  Jones-Plassmann: priority splitmix64(key+u),  */
-/* ties to the lower index; each round, every uncoloured node that beats all   */
-/* its uncoloured neighbours takes the smallest colour unused by its           */
+/* Eq. (2.3) is lexicographic).  Jones-Plassmann, largest degree first: node u */
+/* beats v iff (deg u, h u) > (deg v, h v) lexicographically, h = splitmix64(  */
+/* key + u), ties to the lower index; each round, every uncoloured node that   */
+/* beats all its uncoloured neighbours takes the smallest colour unused by its */
 /* neighbours.  Returns the number of colours; *rounds if requested.           */
 /* ------------------------------------------------------------------------- */
 
-static int beats(uint64_t pu, int64_t u, uint64_t pv, int64_t v) {
+static int beats(int64_t du, uint64_t pu, int64_t u, int64_t dv, uint64_t pv, int64_t v) {
+    if (du != dv) return du > dv;
     return pu > pv || (pu == pv && u < v);
 }
 
@@ -198,7 +217,10 @@ static int32_t colour_impl(int64_t n, const int64_t *rp, const int32_t *col, uin
             int is_max = 1;
             for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
                 int32_t v = col[e];
-                if (colour[v] < 0 && beats(pri[v], v, pri[u], u)) { is_max = 0; break; }
+                if (colour[v] < 0 && beats(rp[v + 1] - rp[v], pri[v], v, rp[u + 1] - rp[u], pri[u], u)) {
+                    is_max = 0;
+                    break;
+                }
             }
             if (is_max) sel[ns++] = (int32_t)u;
         }

@@ -53,9 +53,14 @@ int64_t launch_count();
         if (!(cond)) throw ::lamg::Error{(status), std::string(text)};                   \
     } while (0)
 
-// Rows longer than this are processed by a whole warp (canonical sum switches
-// from left-to-right to 32 lane partials + halving tree at the same length).
+// Row tiers.  Setup: rows of <= kLongRow terms are handled by one thread,
+// up to kHugeRow by one warp, longer ones by a block of kBlk threads; the
+// canonical summation order (left to right / 32-lane tree / 1024-lane tree)
+// switches at the same lengths.  The solve uses kHugeSolve for its block tier.
 constexpr int kLongRow = 32;
+constexpr int kHugeRow = 512;
+constexpr int kHugeSolve = 512;
+constexpr int kBlk = 1024;
 
 // ---------------------------------------------------------------------------
 // Device buffers (owned, freed with the handle)
@@ -100,8 +105,9 @@ struct SetupLevel {
     DBuf<double> w;                // FP64 weights
     DBuf<int32_t> colour;          // Jones-Plassmann colour
     int32_t ncolours = 0, jp_rounds = 0;
-    DBuf<int32_t> corder;          // nodes sorted by (colour, id)
-    std::vector<int32_t> cstart;   // colour ranges in corder (ncolours + 1)
+    DBuf<int32_t> sorder;          // nodes sorted by (colour, row tier, id)
+    std::vector<int32_t> cb;       // colour c, tier t: sorder[cb[4c+t], cb[4c+t+1]); cb[4c+3] = end
+    DBuf<int32_t> cb_dev;          // same on the device
     DBuf<int32_t> agg, state;      // aggregation result (non-coarsest levels)
     DBuf<uint8_t> hub;
     DBuf<double> tv, aff, q, score;  // kept only with keep_setup_data
@@ -120,15 +126,18 @@ struct SolveLevel {
     DBuf<double> w64;
     DBuf<float> w32;
     DBuf<int32_t> perm;            // perm[i] = natural id of permuted row i
-    std::vector<int32_t> cs;       // colour c rows: [cs[c], cs[c+1])
-    std::vector<int32_t> cl;       // long rows of colour c: [cl[c], cs[c+1])
-    DBuf<int32_t> longrows;        // all long rows (permuted ids)
-    int32_t nlong = 0;
+    std::vector<int32_t> cb;       // colour c, tier t rows: [cb[4c+t], cb[4c+t+1]); cb[4c+3] = end
+    DBuf<int32_t> cb_dev;
+    // sweep plan per precision (0 = FP64, 1 = FP32): segments (c0, c1, single);
+    // single = 1: colours c0..c1-1 in one single-block launch, else colour c0 alone
+    std::vector<int32_t> seg[2];
+    DBuf<int32_t> wrows, brows;    // all warp-tier / block-tier rows (permuted ids)
+    int32_t nw = 0, nb = 0;
     // transfer to the next coarser level (absent on the coarsest level)
     DBuf<int32_t> pagg;            // permuted fine row -> permuted coarse id
     DBuf<int32_t> mptr, mlist;     // members of each coarse id (permuted fine ids)
-    DBuf<int32_t> longagg;         // coarse ids with > kLongRow members
-    int32_t nlongagg = 0;
+    DBuf<int32_t> wagg, bagg;      // coarse ids whose member lists are warp / block tier
+    int32_t nwagg = 0, nbagg = 0;
     // coarsest level
     int32_t dense = 0;
     DBuf<double> minv;             // (A + 11^T/n)^-1, n x n, if dense

@@ -5,21 +5,51 @@
 //
 // Every floating-point value that feeds an integer decision is computed in
 // FP64 with a fixed operation order (this translation unit is compiled with
-// -fmad=false, so no multiply-add is contracted):
-//  * row sums of up to kLongRow terms: one thread, left to right from +0.0;
-//  * longer sums: one warp, lane j sums terms j, j+32, ... left to right, then
-//    p_j += p_{j+h} for h = 16, 8, 4, 2, 1 (shfl_down); the result is lane 0's.
-// Rows are therefore processed by a thread-per-row kernel (short rows) and a
-// warp-per-row kernel (the list of long rows).
+// -fmad=false, so no multiply-add is contracted).  A row (or segment) of
+// `len` terms is summed
+//  * len <= 32   by one thread, left to right from +0.0;
+//  * len <= 512  by one warp: lane j sums terms j, j+32, ... left to right,
+//    then p_j += p_{j+h} for h = 16, 8, 4, 2, 1 (shfl_down); lane 0's value;
+//  * len  > 512  by a 1024-thread block: thread j sums j, j+1024, ...; each
+//    warp reduces its 32 partials by the same halving tree, then warp 0
+//    reduces the 32 warp results by it again.
+// Kernels are therefore templated on the row tier M (thread / warp / block).
+#include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "lamg_internal.cuh"
 
 namespace lamg {
 
+// Phase timer for development: with LAMG_TIMING=1 in the environment every
+// phase of the setup synchronises the stream and prints its wall time.
+struct PhaseTimer {
+    bool on;
+    cudaStream_t s;
+    int level = 0;
+    std::chrono::steady_clock::time_point t;
+    explicit PhaseTimer(cudaStream_t st) : s(st) {
+        const char *e = std::getenv("LAMG_TIMING");
+        on = e && e[0] == '1';
+        t = std::chrono::steady_clock::now();
+    }
+    void mark(const char *what) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "lamg-timing level %d %-10s %9.3f ms\n", level, what,
+                     std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
+
 constexpr unsigned kFull = 0xffffffffu;
 enum { ST_U = 0, ST_S = 1, ST_A = 2, ST_D = 3 };
+enum { M_THR = 0, M_WARP = 1, M_BLK = 2 };
+constexpr int kJPBatch = 4;          // JP rounds issued between host checks
+constexpr int kJPFinish = 65536;     // remaining nodes at or below which JP finishes on the induced graph
 
 // ---------------------------------------------------------------------------
 // splitmix64 (Steele, Lea & Flood 2014): first output of the generator seeded
@@ -40,52 +70,173 @@ static uint64_t tv_key(uint64_t seed, int level) {
     return splitmix64(splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 2)));
 }
 
+// ---------------------------------------------------------------------------
+// Tier helpers
+// ---------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ int row_tier(int64_t len) {
+    return len <= kLongRow ? 0 : (len <= kHugeRow ? 1 : 2);
+}
+
+template <int M> __device__ __forceinline__ int tlane() {
+    return M == M_THR ? 0 : (M == M_WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x);
+}
+template <int M> __device__ __forceinline__ int tstride() { return M == M_THR ? 1 : (M == M_WARP ? 32 : kBlk); }
+
 __device__ __forceinline__ double warp_tree(double p) {
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) p = p + __shfl_down_sync(kFull, p, h);
     return __shfl_sync(kFull, p, 0);
 }
 
-// Row addressing: thread variant covers rows [0, n) and skips long rows;
-// warp variant takes its rows from the long-row list.
-template <bool WARP>
+// Canonical reduction of the tier's partial sums; result in every thread.
+template <int M>
+__device__ __forceinline__ double canon_reduce(double p) {
+    if (M == M_THR) return p;
+    p = warp_tree(p);
+    if (M == M_WARP) return p;
+    __shared__ double red[33];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = warp_tree(red[threadIdx.x]);
+        if (threadIdx.x == 0) red[32] = v;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <int M>
+__device__ __forceinline__ double reduce_max(double v) {
+    if (M == M_THR) return v;
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    if (M == M_WARP) return v;
+    __shared__ double red[33];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = red[threadIdx.x];
+        for (int o = 16; o; o >>= 1) t = fmax(t, __shfl_xor_sync(kFull, t, o));
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <int M>
+__device__ __forceinline__ bool reduce_any(bool v) {
+    if (M == M_THR) return v;
+    if (M == M_WARP) return __any_sync(kFull, v);
+    return __syncthreads_or(v) != 0;
+}
+
+template <int M>
+__device__ __forceinline__ bool reduce_all(bool v) {
+    if (M == M_THR) return v;
+    if (M == M_WARP) return __all_sync(kFull, v);
+    return __syncthreads_and(v) != 0;
+}
+
+template <int M>
+__device__ __forceinline__ unsigned long long reduce_or64(unsigned long long v) {
+    if (M == M_THR) return v;
+    for (int o = 16; o; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
+    if (M == M_WARP) return v;
+    __shared__ unsigned long long red[33];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long t = red[threadIdx.x];
+        for (int o = 16; o; o >>= 1) t |= __shfl_xor_sync(kFull, t, o);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// best = largest score, ties -> smaller neighbour; v < 0 means none
+__device__ __forceinline__ void best_merge(double &bs, int32_t &bv, double os, int32_t ov) {
+    if (ov >= 0 && (bv < 0 || os > bs || (os == bs && ov < bv))) { bs = os; bv = ov; }
+}
+
+template <int M>
+__device__ __forceinline__ int32_t reduce_best(double bs, int32_t bv) {
+    if (M == M_THR) return bv;
+    for (int o = 16; o; o >>= 1) {
+        const double os = __shfl_xor_sync(kFull, bs, o);
+        const int32_t ov = __shfl_xor_sync(kFull, bv, o);
+        best_merge(bs, bv, os, ov);
+    }
+    if (M == M_WARP) return bv;
+    __shared__ double rs[32];
+    __shared__ int32_t rv[33];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { rs[threadIdx.x >> 5] = bs; rv[threadIdx.x >> 5] = bv; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = rs[threadIdx.x];
+        int32_t v = rv[threadIdx.x];
+        for (int o = 16; o; o >>= 1) {
+            const double os = __shfl_xor_sync(kFull, s, o);
+            const int32_t ov = __shfl_xor_sync(kFull, v, o);
+            best_merge(s, v, os, ov);
+        }
+        if (threadIdx.x == 0) rv[32] = v;
+    }
+    __syncthreads();
+    return rv[32];
+}
+
+// Row addressing.  THR: thread i takes list[i] (or i when list is NULL) of n
+// rows; kernels skip rows above the thread tier.  WARP / BLK: one warp /
+// block per list entry.
+template <int M>
 __device__ __forceinline__ bool get_row(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
-                                        int32_t &row, int &lane) {
-    if (!WARP) {
-        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                        int32_t &row) {
+    if (M == M_THR) {
+        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= n) return false;
-        row = (int32_t)i;
-        lane = 0;
+        row = list ? list[i] : (int32_t)i;
         return true;
     }
-    int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wg >= nlist) return false;
-    row = list[wg];
-    lane = threadIdx.x & 31;
+    if (M == M_WARP) {
+        const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (w >= nlist) return false;
+        row = list[w];
+        return true;
+    }
+    if (blockIdx.x >= nlist) return false;
+    row = list[blockIdx.x];
     return true;
 }
 
-template <bool WARP>
-static void grid_for(int64_t count, int &blocks, int &threads) {
-    threads = 256;
-    int64_t t = WARP ? count * 32 : count;
-    blocks = (int)std::max<int64_t>(1, (t + threads - 1) / threads);
-}
-
-#define LAUNCH_ROWS(KERNEL, N, LIST, NLIST, S, ...)                                       \
-    do {                                                                                  \
-        int b_, t_;                                                                       \
-        if ((N) > 0) {                                                                    \
-            grid_for<false>((N), b_, t_);                                                 \
-            KERNEL<false><<<b_, t_, 0, (S)>>>((N), (LIST), (NLIST), __VA_ARGS__);         \
-            LAMG_CHECK_LAUNCH();                                                          \
-        }                                                                                 \
-        if ((NLIST) > 0) {                                                                \
-            grid_for<true>((NLIST), b_, t_);                                              \
-            KERNEL<true><<<b_, t_, 0, (S)>>>((N), (LIST), (NLIST), __VA_ARGS__);          \
-            LAMG_CHECK_LAUNCH();                                                          \
-        }                                                                                 \
+// Launch the three tiers of a per-row kernel: THR over all n rows (or a
+// list), WARP over the warp-tier list, BLK over the block-tier list.
+#define LAUNCH3(KERNEL, N, TLIST, WL, NW, BL, NB, S, ...)                                  \
+    do {                                                                                    \
+        if ((N) > 0) {                                                                      \
+            KERNEL<M_THR><<<ceil_div((N), 256), 256, 0, (S)>>>((N), (TLIST), 0, __VA_ARGS__); \
+            LAMG_CHECK_LAUNCH();                                                            \
+        }                                                                                   \
+        if ((NW) > 0) {                                                                     \
+            KERNEL<M_WARP><<<ceil_div((int64_t)(NW) * 32, 256), 256, 0, (S)>>>(0, (WL), (NW), __VA_ARGS__); \
+            LAMG_CHECK_LAUNCH();                                                            \
+        }                                                                                   \
+        if ((NB) > 0) {                                                                     \
+            KERNEL<M_BLK><<<(NB), kBlk, 0, (S)>>>(0, (BL), (NB), __VA_ARGS__);             \
+            LAMG_CHECK_LAUNCH();                                                            \
+        }                                                                                   \
     } while (0)
+
+// Rows of one level split by tier.
+struct Tiers {
+    Tmp<int32_t> w, b;
+    int32_t nw = 0, nb = 0;
+    Tiers(int32_t n, cudaStream_t s) : w(n, s), b(n, s) {}
+};
 
 // ---------------------------------------------------------------------------
 // Input conversion and validation (Eq. (1.2), Sec. 1)
@@ -122,25 +273,32 @@ __global__ void k_validate_rows(int64_t n, const int64_t *__restrict__ rp,
     if (f) atomicOr(flags, f);
 }
 
-__global__ void k_validate_sym(int64_t n, const int64_t *__restrict__ rp,
+// row of entry i: the last u with rp[u] <= i (binary search)
+__device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ rp, int64_t n, int64_t i) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// entry-parallel symmetry check
+__global__ void k_validate_sym(int64_t n, int64_t nnz, const int64_t *__restrict__ rp,
                                const int32_t *__restrict__ col, const double *__restrict__ w,
                                int32_t *flags) {
-    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    for (int64_t i = rp[u]; i < rp[u + 1]; i++) {
-        int32_t v = col[i];
-        int64_t lo = rp[v], hi = rp[v + 1] - 1, f = -1;
-        while (lo <= hi) {
-            int64_t mid = (lo + hi) >> 1;
-            int32_t c = col[mid];
-            if (c == u) { f = mid; break; }
-            if (c < u) lo = mid + 1; else hi = mid - 1;
-        }
-        if (f < 0 || __double_as_longlong(w[f]) != __double_as_longlong(w[i])) {
-            atomicOr(flags, VF_SYM);
-            return;
-        }
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnz) return;
+    const int64_t u = row_of(rp, n, i);
+    const int32_t v = col[i];
+    int64_t a = rp[v], b = rp[v + 1] - 1, f = -1;
+    while (a <= b) {
+        int64_t mid = (a + b) >> 1;
+        int32_t c = col[mid];
+        if (c == u) { f = mid; break; }
+        if (c < u) a = mid + 1; else b = mid - 1;
     }
+    if (f < 0 || __double_as_longlong(w[f]) != __double_as_longlong(w[i])) atomicOr(flags, VF_SYM);
 }
 
 __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
@@ -159,22 +317,20 @@ __global__ void k_uf_init(int32_t *parent, int64_t n) {
     if (i < n) parent[i] = (int32_t)i;
 }
 
-__global__ void k_uf_union(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           int32_t *parent) {
-    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    for (int64_t i = rp[u]; i < rp[u + 1]; i++) {
-        int32_t v = col[i];
-        if (v <= u) continue;
-        int32_t a = (int32_t)u, b = v;
-        // hook the larger root under the smaller; retry until both share a root
-        for (int it = 0; it < (1 << 20); it++) {
-            int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
-            if (ra == rb) break;
-            int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
-            if (atomicCAS(&parent[hi], hi, lo) == hi) break;
-            a = ra; b = rb;
-        }
+// entry-parallel union of the endpoints of every entry (u < v)
+__global__ void k_uf_union(int64_t n, int64_t nnz, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, int32_t *parent) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnz) return;
+    int32_t a = (int32_t)row_of(rp, n, i), b = col[i];
+    if (b <= a) return;
+    // hook the larger root under the smaller; retry until both share a root
+    for (int it = 0; it < (1 << 20); it++) {
+        int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+        if (ra == rb) break;
+        int32_t hi2 = ra > rb ? ra : rb, lo2 = ra > rb ? rb : ra;
+        if (atomicCAS(&parent[hi2], hi2, lo2) == hi2) break;
+        a = ra; b = rb;
     }
 }
 
@@ -209,8 +365,10 @@ void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const
     LAMG_REQUIRE(!(f & VF_ARG), LAMG_ERR_ARG,
                  "malformed CSR: columns must be in range, strictly increasing, no self loops");
     LAMG_REQUIRE(!(f & VF_WEIGHT), LAMG_ERR_BAD_WEIGHT, "weights must be positive and finite");
-    k_validate_sym<<<ceil_div(n, 256), 256, 0, s>>>(n, row_ptr, col, w64.get(), flags.get());
-    LAMG_CHECK_LAUNCH();
+    if (nnz) {
+        k_validate_sym<<<ceil_div(nnz, 256), 256, 0, s>>>(n, nnz, row_ptr, col, w64.get(), flags.get());
+        LAMG_CHECK_LAUNCH();
+    }
     f = read_scalar(flags.get(), s);
     LAMG_REQUIRE(!(f & VF_SYM), LAMG_ERR_NOT_SYMMETRIC, "CSR is not symmetric (w_uv != w_vu)");
     Tmp<int32_t> parent(n, s);
@@ -218,8 +376,10 @@ void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const
     LAMG_CUDA(cudaMemsetAsync(roots.get(), 0, sizeof(unsigned long long), s));
     k_uf_init<<<ceil_div(n, 256), 256, 0, s>>>(parent.get(), n);
     LAMG_CHECK_LAUNCH();
-    k_uf_union<<<ceil_div(n, 256), 256, 0, s>>>(n, row_ptr, col, parent.get());
-    LAMG_CHECK_LAUNCH();
+    if (nnz) {
+        k_uf_union<<<ceil_div(nnz, 256), 256, 0, s>>>(n, nnz, row_ptr, col, parent.get());
+        LAMG_CHECK_LAUNCH();
+    }
     k_uf_roots<<<ceil_div(n, 256), 256, 0, s>>>(parent.get(), n, roots.get());
     LAMG_CHECK_LAUNCH();
     unsigned long long r = read_scalar(roots.get(), s);
@@ -230,18 +390,18 @@ void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const
 // Per-node statistics: a_uu, max|w|, hub test (Sec. 3.4.1 footnote)
 // ---------------------------------------------------------------------------
 
-template <bool WARP>
-__global__ void k_node_stats(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_stats(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                              const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                              const double *__restrict__ w, double hub_factor,
                              double *__restrict__ diag, double *__restrict__ maxw,
                              uint8_t *__restrict__ hub) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
     const int32_t s = rp[u], e = rp[u + 1], deg = e - s;
-    if (!WARP && deg > kLongRow) return;
+    if (M == M_THR && deg > kLongRow) return;
     double d = 0.0, m = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int32_t i = s + lane; i < e; i += (WARP ? 32 : 1)) {
+    for (int32_t i = s + tlane<M>(); i < e; i += tstride<M>()) {
         const double wi = w[i];
         const int32_t v = col[i];
         const double a = fabs(wi);
@@ -250,13 +410,11 @@ __global__ void k_node_stats(int32_t n, const int32_t *__restrict__ list, int32_
         s1 = s1 + a;
         s2 = s2 + a * (double)(rp[v + 1] - rp[v]);
     }
-    if (WARP) {
-        d = warp_tree(d);
-        s1 = warp_tree(s1);
-        s2 = warp_tree(s2);
-        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
-        if (lane) return;
-    }
+    d = canon_reduce<M>(d);
+    s1 = canon_reduce<M>(s1);
+    s2 = canon_reduce<M>(s2);
+    m = reduce_max<M>(m);
+    if (tlane<M>() != 0) return;
     diag[u] = d;
     maxw[u] = m;
     const double lhs = (double)deg * s1;
@@ -266,26 +424,24 @@ __global__ void k_node_stats(int32_t n, const int32_t *__restrict__ list, int32_
 
 // Initial aggregation state (Sec. 3.4.2): nodes without strong edges form the
 // dummy aggregate (D), hubs are seeds (S), the rest undecided (U).
-template <bool WARP>
-__global__ void k_node_state(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_state(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                              const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                              const double *__restrict__ w, const double *__restrict__ maxw,
                              double weak_tol, const uint8_t *__restrict__ hub,
                              int32_t *__restrict__ state) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
     const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
+    if (M == M_THR && e - s > kLongRow) return;
     bool strong = false;
     const double mu = maxw[u];
-    for (int32_t i = s + lane; i < e; i += (WARP ? 32 : 1)) {
+    for (int32_t i = s + tlane<M>(); i < e; i += tstride<M>()) {
         const double mw = fmax(mu, maxw[col[i]]);
         if (fabs(w[i]) >= weak_tol * mw) strong = true;
     }
-    if (WARP) {
-        strong = __any_sync(kFull, strong);
-        if (lane) return;
-    }
+    strong = reduce_any<M>(strong);
+    if (tlane<M>() != 0) return;
     state[u] = !strong ? ST_D : (hub[u] ? ST_S : ST_U);
 }
 
@@ -293,63 +449,215 @@ __global__ void k_node_state(int32_t n, const int32_t *__restrict__ list, int32_
 // Jones-Plassmann colouring
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool beats(uint64_t pu, int32_t u, uint64_t pv, int32_t v) {
+// Priority: largest degree first, then the hash, ties to the lower index.
+__device__ __forceinline__ bool beats(int32_t du, uint64_t pu, int32_t u, int32_t dv, uint64_t pv, int32_t v) {
+    if (du != dv) return du > dv;
     return pu > pv || (pu == pv && u < v);
 }
 
-template <bool WARP>
-__global__ void k_jp_select(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
-                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            const int32_t *__restrict__ colour, uint64_t key,
-                            uint8_t *__restrict__ sel) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
-    const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
-    if (colour[u] >= 0) {
-        if (lane == 0) sel[u] = 0;
-        return;
-    }
+// u is selected in this round iff it is uncoloured and beats every uncoloured neighbour
+template <int M>
+__device__ __forceinline__ bool jp_is_max(int32_t u, const int32_t *__restrict__ rp,
+                                          const int32_t *__restrict__ col,
+                                          const int32_t *__restrict__ colour, uint64_t key) {
+    if (colour[u] >= 0) return false;  // same value in every thread of the tier
     const uint64_t pu = splitmix64(key + (uint64_t)u);
+    const int32_t du = rp[u + 1] - rp[u];
     bool is_max = true;
-    for (int32_t i = s + lane; i < e; i += (WARP ? 32 : 1)) {
+    for (int32_t i = rp[u] + tlane<M>(); i < rp[u + 1]; i += tstride<M>()) {
         const int32_t v = col[i];
-        if (colour[v] < 0 && beats(splitmix64(key + (uint64_t)v), v, pu, u)) { is_max = false; break; }
+        if (colour[v] < 0 && beats(rp[v + 1] - rp[v], splitmix64(key + (uint64_t)v), v, du, pu, u)) {
+            is_max = false;
+            break;
+        }
     }
-    if (WARP) {
-        is_max = __all_sync(kFull, is_max);
-        if (lane) return;
-    }
-    sel[u] = is_max ? 1 : 0;
+    return reduce_all<M>(is_max);
 }
 
-template <bool WARP>
-__global__ void k_jp_assign(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
-                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            const uint8_t *__restrict__ sel, int32_t *__restrict__ colour,
-                            int32_t *__restrict__ remaining) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
-    const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
-    if (!sel[u]) return;
-    // smallest colour not used by a neighbour, searched in windows of 64
+// smallest colour not used by any neighbour, searched in windows of 64
+template <int M>
+__device__ __forceinline__ int32_t jp_free_colour(int32_t u, const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ col,
+                                                  const int32_t *__restrict__ colour) {
     for (int32_t base = 0;; base += 64) {
         unsigned long long mask = 0ull;
-        for (int32_t i = s + lane; i < e; i += (WARP ? 32 : 1)) {
+        for (int32_t i = rp[u] + tlane<M>(); i < rp[u + 1]; i += tstride<M>()) {
             const int32_t c = colour[col[i]];
             if (c >= base && c < base + 64) mask |= 1ull << (c - base);
         }
-        if (WARP)
-            for (int o = 16; o; o >>= 1) mask |= __shfl_xor_sync(kFull, mask, o);
-        if (mask != ~0ull) {
-            if (lane == 0) {
-                colour[u] = base + __ffsll((long long)~mask) - 1;
-                atomicSub(remaining, 1);
+        mask = reduce_or64<M>(mask);
+        if (mask != ~0ull) return base + __ffsll((long long)~mask) - 1;
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_jp_select(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const int32_t *__restrict__ colour, uint64_t key,
+                            uint8_t *__restrict__ sel, const int32_t *__restrict__ remaining,
+                            int32_t *__restrict__ rounds) {
+    if (M == M_THR && blockIdx.x == 0 && threadIdx.x == 0 && *remaining > 0) atomicAdd(rounds, 1);
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
+    if (M == M_THR && rp[u + 1] - rp[u] > kLongRow) return;
+    const bool r = jp_is_max<M>(u, rp, col, colour, key);
+    if (tlane<M>() == 0) sel[u] = r ? 1 : 0;
+}
+
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_jp_assign(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const uint8_t *__restrict__ sel, int32_t *__restrict__ colour,
+                            int32_t *__restrict__ remaining) {
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
+    if (M == M_THR && rp[u + 1] - rp[u] > kLongRow) return;
+    if (!sel[u]) return;
+    const int32_t c = jp_free_colour<M>(u, rp, col, colour);
+    if (tlane<M>() == 0) {
+        colour[u] = c;
+        atomicSub(remaining, 1);
+    }
+}
+
+// ---- Last rounds on the subgraph induced by the r <= kJPFinish remaining nodes.
+// R = remaining nodes (increasing id), pos[u] = index of u in R or -1.
+// Keys for the exact priority order of the remaining nodes (LSD passes: the
+// list is already in increasing id; a stable sort by ~hash then by ~degree
+// yields decreasing (degree, hash), ties by increasing id).
+__global__ void k_jp_hashkey(const int32_t *__restrict__ R, const int32_t *__restrict__ idx, int32_t r,
+                             uint64_t key, uint64_t *__restrict__ k) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < r) k[i] = ~splitmix64(key + (uint64_t)R[idx[i]]);
+}
+
+__global__ void k_jp_degkey(const int32_t *__restrict__ R, const int32_t *__restrict__ idx, int32_t r,
+                            const int32_t *__restrict__ rp, uint64_t *__restrict__ k) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < r) {
+        const int32_t u = R[idx[i]];
+        k[i] = (uint64_t)(0x7fffffff - (rp[u + 1] - rp[u]));
+    }
+}
+
+__global__ void k_jp_rank_from_order(const int32_t *__restrict__ idx, int32_t r, int32_t *__restrict__ rank) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < r) rank[idx[i]] = i;
+}
+
+// one warp per remaining node: count its remaining neighbours (fill = 0) or
+// write (key = i * r + rank of the neighbour, value = neighbour index) and
+// set the forbidden bits of its already coloured neighbours (fill = 1).
+__global__ void k_jp_induced(const int32_t *__restrict__ R, int32_t r, const int32_t *__restrict__ rp,
+                             const int32_t *__restrict__ col, const int32_t *__restrict__ pos,
+                             const int32_t *__restrict__ rank, const int32_t *__restrict__ colour, int fill,
+                             int32_t *__restrict__ cnt, const int32_t *__restrict__ iptr,
+                             uint64_t *__restrict__ ikey, int32_t *__restrict__ ival,
+                             unsigned long long *__restrict__ forb, int32_t W) {
+    const int32_t i = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= r) return;
+    const int32_t u = R[i];
+    int32_t run = 0;
+    for (int32_t base = rp[u]; base < rp[u + 1]; base += 32) {
+        const int32_t e = base + lane;
+        int32_t j = -1;
+        if (e < rp[u + 1]) {
+            const int32_t v = col[e];
+            j = pos[v];
+            if (fill && j < 0) {
+                const int32_t c = colour[v];
+                if (c >= 0) atomicOr(&forb[(int64_t)i * W + (c >> 6)], 1ull << (c & 63));
             }
+        }
+        const unsigned m = __ballot_sync(kFull, j >= 0);
+        if (fill && j >= 0) {
+            const int32_t o = iptr[i] + run + __popc(m & ((1u << lane) - 1u));
+            ikey[o] = (uint64_t)i * (uint64_t)r + (uint64_t)rank[j];
+            ival[o] = j;
+        }
+        run += __popc(m);
+    }
+    if (!fill && lane == 0) cnt[i] = run;
+}
+
+// JP rounds on the induced graph in one block.  A node is selected iff the
+// first uncoloured entry of its neighbour list (sorted by decreasing priority)
+// has lower priority than itself, which is exactly "beats every uncoloured
+// neighbour".  The pointer into the list only moves forward.  Colours come
+// from the forbidden masks (coloured neighbours, set as they get coloured).
+// The active list is compacted every round (its order does not affect any
+// decision: selection, colour choice and mask updates are order-free).
+__global__ void __launch_bounds__(kBlk) k_jp_finish(const int32_t *__restrict__ R, int32_t r,
+                                                   const int32_t *__restrict__ rank, const int32_t *__restrict__ iptr,
+                                                   const int32_t *__restrict__ inb, int32_t *__restrict__ ptr,
+                                                   int32_t *__restrict__ icol, uint8_t *__restrict__ sel,
+                                                   int32_t *__restrict__ act0, int32_t *__restrict__ act1,
+                                                   unsigned long long *__restrict__ forb, int32_t W,
+                                                   int32_t *__restrict__ colour, int32_t *__restrict__ rounds_out) {
+    __shared__ int32_t na, nn;
+    for (int32_t i = threadIdx.x; i < r; i += kBlk) { ptr[i] = iptr[i]; icol[i] = -1; act0[i] = i; }
+    if (threadIdx.x == 0) na = r;
+    __syncthreads();
+    int32_t *act = act0, *nxt = act1;
+    for (int32_t round = 0; round <= r; round++) {
+        const int32_t m = na;
+        if (m == 0) {
+            if (threadIdx.x == 0) *rounds_out = round;
             return;
         }
+        for (int32_t t = threadIdx.x; t < m; t += kBlk) {
+            const int32_t i = act[t];
+            int32_t p = ptr[i];
+            while (p < iptr[i + 1] && icol[inb[p]] >= 0) p++;
+            ptr[i] = p;
+            sel[i] = (p == iptr[i + 1] || rank[inb[p]] > rank[i]) ? 1 : 0;
+        }
+        if (threadIdx.x == 0) nn = 0;
+        __syncthreads();
+        for (int32_t t = threadIdx.x; t < m; t += kBlk) {
+            const int32_t i = act[t];
+            if (!sel[i]) continue;
+            int32_t c = -1;
+            for (int32_t wd = 0; wd < W && c < 0; wd++) {
+                const unsigned long long mk = forb[(int64_t)i * W + wd];
+                if (mk != ~0ull) c = wd * 64 + __ffsll((long long)~mk) - 1;
+            }
+            icol[i] = c;
+            colour[R[i]] = c;
+        }
+        __syncthreads();
+        for (int32_t t = threadIdx.x; t < m; t += kBlk) {
+            const int32_t i = act[t];
+            if (!sel[i]) {
+                nxt[atomicAdd(&nn, 1)] = i;
+                continue;
+            }
+            const int32_t c = icol[i];
+            for (int32_t q = iptr[i]; q < iptr[i + 1]; q++)
+                atomicOr(&forb[(int64_t)inb[q] * W + (c >> 6)], 1ull << (c & 63));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) na = nn;
+        int32_t *tp = act; act = nxt; nxt = tp;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *rounds_out = -1;  // not reached: every round colours a node
+}
+
+__global__ void k_iota32(int32_t *__restrict__ a, int32_t n) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+
+__global__ void k_uncoloured(const int32_t *__restrict__ colour, int32_t n, uint8_t *__restrict__ f) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) f[u] = colour[u] < 0 ? 1 : 0;
+}
+
+__global__ void k_pos_scatter(const int32_t *__restrict__ R, int32_t r, int32_t *__restrict__ pos) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < r) pos[R[i]] = i;
 }
 
 __global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
@@ -357,39 +665,43 @@ __global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
     if (i < n) a[i] = v;
 }
 
-__global__ void k_iota(int32_t *a, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = (int32_t)i;
-}
-
-__global__ void k_to_u32(const int32_t *__restrict__ a, uint32_t *__restrict__ o, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) o[i] = (uint32_t)a[i];
-}
-
-__global__ void k_hist_i32(const int32_t *__restrict__ a, int64_t n, int32_t *__restrict__ cnt) {
+__global__ void k_hist_u32(const uint32_t *__restrict__ a, int64_t n, int32_t *__restrict__ cnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(&cnt[a[i]], 1);
 }
 
-__global__ void k_long_flags(const int32_t *__restrict__ rp, const int32_t *__restrict__ order,
-                             int64_t n, uint8_t *__restrict__ f) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t u = order ? order[i] : (int32_t)i;
-    f[i] = (rp[u + 1] - rp[u]) > kLongRow ? 1 : 0;
+// flag rows of one tier (only uncoloured ones when `colour` is given)
+__global__ void k_tier_flags(const int32_t *__restrict__ rp, int64_t n, int tier,
+                             const int32_t *__restrict__ colour, uint8_t *__restrict__ f) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const bool ok = colour ? colour[u] < 0 : true;
+    f[u] = (ok && row_tier(rp[u + 1] - rp[u]) == tier) ? 1 : 0;
 }
 
-__global__ void k_gather_i32(const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
-                             int32_t *__restrict__ dst, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[idx[i]];
+// key = colour * 3 + tier, value = node
+__global__ void k_order_keys(const int32_t *__restrict__ rp, const int32_t *__restrict__ colour, int32_t n,
+                             uint32_t *__restrict__ key, int32_t *__restrict__ val) {
+    int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    key[u] = (uint32_t)colour[u] * 3u + (uint32_t)row_tier(rp[u + 1] - rp[u]);
+    val[u] = u;
 }
 
 static int bits_for(uint64_t maxval) {
     int b = 0;
     while (b < 64 && (maxval >> b) != 0) b++;
     return b;
+}
+
+// Rows of tier `tier` (only uncoloured ones when colour != NULL), increasing id.
+static int32_t tier_list(const int32_t *rp, int64_t n, int tier, const int32_t *colour, int32_t *out,
+                         cudaStream_t s) {
+    if (n <= 0) return 0;
+    Tmp<uint8_t> f(n, s);
+    k_tier_flags<<<ceil_div(n, 256), 256, 0, s>>>(rp, n, tier, colour, f.get());
+    LAMG_CHECK_LAUNCH();
+    return (int32_t)compact_indices(f.get(), out, n, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -404,56 +716,88 @@ __global__ void k_tv_init(double *__restrict__ X, int64_t count, uint64_t key) {
     X[i] = 2.0 * t - 1.0;
 }
 
-// One colour of a TV sweep: rows order[lo..hi) (thread variant skips long rows;
-// warp variant takes the colour's long rows from `list`).
-template <bool WARP>
-__global__ void k_tv_sweep(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+// x_uk = (canonical sum of w_uv x_vk) / a_uu for every TV k (b = 0); one pass
+// over the row with K accumulators, each summed in its canonical order.
+template <int M>
+__device__ __forceinline__ void tv_update(int32_t u, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                          const double *__restrict__ w, const double *__restrict__ diag, int32_t K,
+                                          double *__restrict__ X) {
+    const int32_t s = rp[u], e = rp[u + 1];
+    double acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc[k] = 0.0;
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
+        const double wj = w[j];
+        const double *xv = X + (int64_t)col[j] * K;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (k < K) acc[k] = acc[k] + wj * xv[k];
+    }
+    const double du = diag[u];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        if (k < K) {
+            const double t = canon_reduce<M>(acc[k]);
+            if (tlane<M>() == 0) X[(int64_t)u * K + k] = t / du;
+        }
+    }
+    if (M == M_WARP) __syncwarp();
+    if (M == M_BLK) __syncthreads();
+}
+
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_tv_sweep(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                            const double *__restrict__ w, const double *__restrict__ diag,
                            int32_t K, double *__restrict__ X) {
-    int32_t i; int lane;
-    if (!get_row<WARP>(n, list, nlist, i, lane)) return;
-    const int32_t u = WARP ? i : list[i];  // thread variant: list = colour order slice
-    const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
-    const double du = diag[u];
-    for (int k = 0; k < K; k++) {
-        double acc = 0.0;
-        for (int32_t j = s + lane; j < e; j += (WARP ? 32 : 1))
-            acc = acc + w[j] * X[(int64_t)col[j] * K + k];
-        if (WARP) acc = warp_tree(acc);
-        if (lane == 0) X[(int64_t)u * K + k] = acc / du;
-        if (WARP) __syncwarp();
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
+    tv_update<M>(u, rp, col, w, diag, K, X);
+}
+
+// Colours c0 .. c1-1 of a TV sweep in one block (colour/tier ranges in cb).
+__global__ void __launch_bounds__(kBlk) k_tv_sweep_tail(int32_t c0, int32_t c1, const int32_t *__restrict__ cb,
+                                                       const int32_t *__restrict__ order,
+                                                       const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                       const double *__restrict__ w, const double *__restrict__ diag,
+                                                       int32_t K, double *__restrict__ X) {
+    const int warp = threadIdx.x >> 5;
+    for (int32_t c = c0; c < c1; c++) {
+        const int32_t t0 = cb[4 * c], t1 = cb[4 * c + 1], t2 = cb[4 * c + 2], t3 = cb[4 * c + 3];
+        for (int32_t i = t0 + threadIdx.x; i < t1; i += kBlk) tv_update<M_THR>(order[i], rp, col, w, diag, K, X);
+        for (int32_t i = t1 + warp; i < t2; i += kBlk / 32) tv_update<M_WARP>(order[i], rp, col, w, diag, K, X);
+        for (int32_t i = t2; i < t3; i++) tv_update<M_BLK>(order[i], rp, col, w, diag, K, X);
+        __syncthreads();
     }
 }
 
 // Nodal energy E_u = 1/2 sum_v w_uv (x_u - x_v)^2 of TV k (Eq. (3.11a)).
-template <bool WARP>
-__global__ void k_tv_energy(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_tv_energy(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                             const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                             const double *__restrict__ w, int32_t K, int32_t k,
                             const double *__restrict__ X, double *__restrict__ eu) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
     const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
+    if (M == M_THR && e - s > kLongRow) return;
     const double xu = X[(int64_t)u * K + k];
     double acc = 0.0;
-    for (int32_t j = s + lane; j < e; j += (WARP ? 32 : 1)) {
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
         const double d = xu - X[(int64_t)col[j] * K + k];
         acc = acc + w[j] * (d * d);
     }
-    if (WARP) acc = warp_tree(acc);
-    if (lane == 0) eu[u] = 0.5 * acc;
+    acc = canon_reduce<M>(acc);
+    if (tlane<M>() == 0) eu[u] = 0.5 * acc;
 }
 
-// Canonical sum of chunks of 4096 terms, one warp per chunk.
+// Canonical sum of chunks of 512 terms, one warp per chunk.
 __global__ void k_canon_chunks(const double *__restrict__ t, int64_t len, double *__restrict__ out) {
     const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t lo = c * 4096;
+    const int64_t lo = c * 512;
     if (lo >= len) return;
-    const int64_t cnt = (len - lo) < 4096 ? (len - lo) : 4096;
+    const int64_t cnt = (len - lo) < 512 ? (len - lo) : 512;
     if (cnt <= 32) {
         if (lane == 0) {
             double s = 0.0;
@@ -469,16 +813,16 @@ __global__ void k_canon_chunks(const double *__restrict__ t, int64_t len, double
 }
 
 static double canon_sum_global(const double *t, int64_t len, cudaStream_t s) {
-    Tmp<double> a((size_t)std::max<int64_t>(1, (len + 4095) / 4096), s);
-    Tmp<double> b((size_t)std::max<int64_t>(1, (len + 4095) / 4096), s);
+    Tmp<double> a((size_t)std::max<int64_t>(1, (len + 511) / 512), s);
+    Tmp<double> b((size_t)std::max<int64_t>(1, (len + 511) / 512), s);
     const double *src = t;
     double *dst = a.get(), *other = b.get();
     while (true) {
-        int64_t nch = (len + 4095) / 4096;
+        int64_t nch = (len + 511) / 512;
         if (nch < 1) nch = 1;
         k_canon_chunks<<<ceil_div(nch * 32, 256), 256, 0, s>>>(src, len, dst);
         LAMG_CHECK_LAUNCH();
-        if (len <= 4096) break;
+        if (len <= 512) break;
         len = nch;
         src = dst;
         std::swap(dst, other);
@@ -487,20 +831,22 @@ static double canon_sum_global(const double *t, int64_t len, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Affinity and energy ratio (Eqs. (3.5), (3.12)); see the oracle for the
-// reading of Eq. (3.12): q_us = max_k E_u(x^k; x^k_s) / min_y E_u(x^k; y).
+// Affinity and energy ratio (Eqs. (3.5), (3.12)); the reading of Eq. (3.12):
+// q_us = max_k E_u(x^k; x^k_s) / min_y E_u(x^k; y), with
+// Emin = 1/2 sum_v w_uv (y* - x_v)^2 and E_s = Emin + a_uu (x_s - y*)^2 / 2.
 // ---------------------------------------------------------------------------
 
-template <bool WARP>
-__global__ void k_node_pre(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_pre(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                            const double *__restrict__ w, const double *__restrict__ diag,
                            int32_t K, const double *__restrict__ X, double *__restrict__ XX,
                            double *__restrict__ ystar, double *__restrict__ emin) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
     const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
+    if (M == M_THR && e - s > kLongRow) return;
+    const int lane = tlane<M>();
     if (lane == 0) {
         double xx = 0.0;
         for (int k = 0; k < K; k++) {
@@ -510,33 +856,52 @@ __global__ void k_node_pre(int32_t n, const int32_t *__restrict__ list, int32_t 
         XX[u] = xx;
     }
     const double du = diag[u];
-    for (int k = 0; k < K; k++) {
-        double B = 0.0;
-        for (int32_t j = s + lane; j < e; j += (WARP ? 32 : 1))
-            B = B + w[j] * X[(int64_t)col[j] * K + k];
-        if (WARP) B = warp_tree(B);
-        const double y = B / du;
-        double E = 0.0;
-        for (int32_t j = s + lane; j < e; j += (WARP ? 32 : 1)) {
-            const double d = y - X[(int64_t)col[j] * K + k];
-            E = E + w[j] * (d * d);
-        }
-        if (WARP) E = warp_tree(E);
-        if (lane == 0) {
-            ystar[(int64_t)u * K + k] = y;
-            emin[(int64_t)u * K + k] = 0.5 * E;
+    double acc[16], y[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc[k] = 0.0;
+    for (int32_t j = s + lane; j < e; j += tstride<M>()) {
+        const double wj = w[j];
+        const double *xv = X + (int64_t)col[j] * K;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (k < K) acc[k] = acc[k] + wj * xv[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        y[k] = 0.0;
+        if (k < K) y[k] = canon_reduce<M>(acc[k]) / du;
+        acc[k] = 0.0;
+    }
+    for (int32_t j = s + lane; j < e; j += tstride<M>()) {
+        const double wj = w[j];
+        const double *xv = X + (int64_t)col[j] * K;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (k < K) {
+                const double d = y[k] - xv[k];
+                acc[k] = acc[k] + wj * (d * d);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        if (k < K) {
+            const double E = canon_reduce<M>(acc[k]);
+            if (lane == 0) {
+                ystar[(int64_t)u * K + k] = y[k];
+                emin[(int64_t)u * K + k] = 0.5 * E;
+            }
         }
     }
 }
 
-template <bool WARP>
-__global__ void k_entry_rows(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_entry_rows(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                              const int32_t *__restrict__ rp, int32_t *__restrict__ erow) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
     const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
-    for (int32_t j = s + lane; j < e; j += (WARP ? 32 : 1)) erow[j] = u;
+    if (M == M_THR && e - s > kLongRow) return;
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) erow[j] = u;
 }
 
 __global__ void k_scores(int64_t nnz, const int32_t *__restrict__ erow, const int32_t *__restrict__ col,
@@ -574,36 +939,29 @@ __global__ void k_scores(int64_t nnz, const int32_t *__restrict__ erow, const in
 // Aggregation stages (Sec. 3.4.2, build reading; see the oracle)
 // ---------------------------------------------------------------------------
 
-template <bool WARP>
-__global__ void k_best(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_best(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                        const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                        const double *__restrict__ score, const int32_t *__restrict__ state,
                        int32_t *__restrict__ best) {
-    int32_t u; int lane;
-    if (!get_row<WARP>(n, list, nlist, u, lane)) return;
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
     const int32_t s = rp[u], e = rp[u + 1];
-    if (!WARP && e - s > kLongRow) return;
+    if (M == M_THR && e - s > kLongRow) return;
     if (state[u] != ST_U) {
-        if (lane == 0) best[u] = -1;
+        if (tlane<M>() == 0) best[u] = -1;
         return;
     }
     double bs = -1.0;
     int32_t bv = -1;
-    for (int32_t j = s + lane; j < e; j += (WARP ? 32 : 1)) {
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
         const int32_t v = col[j];
         const double sc = score[j];
         if (sc < 0.0 || state[v] == ST_A) continue;
-        if (sc > bs || (sc == bs && v < bv)) { bs = sc; bv = v; }
+        best_merge(bs, bv, sc, v);
     }
-    if (WARP) {
-        for (int o = 16; o; o >>= 1) {
-            const double os = __shfl_xor_sync(kFull, bs, o);
-            const int32_t ov = __shfl_xor_sync(kFull, bv, o);
-            if (ov >= 0 && (os > bs || (os == bs && (bv < 0 || ov < bv)))) { bs = os; bv = ov; }
-        }
-        if (lane) return;
-    }
-    best[u] = bv;
+    bv = reduce_best<M>(bs, bv);
+    if (tlane<M>() == 0) best[u] = bv;
 }
 
 __global__ void k_resolve(int32_t n, const int32_t *__restrict__ state, const int32_t *__restrict__ best,
@@ -681,27 +1039,24 @@ __global__ void k_seg_heads(int64_t M, const uint64_t *__restrict__ key, uint8_t
     if (i < M) f[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
 }
 
-__global__ void k_seg_long(int64_t P, const int32_t *__restrict__ start, int64_t M,
-                           uint8_t *__restrict__ f) {
+// segment p covers [start[p], start[p+1]) (the last one ends at M): an rp-like array
+__global__ void k_seg_ptr(int64_t P, const int32_t *__restrict__ start, int64_t M, int32_t *__restrict__ sp) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int64_t e = (p + 1 < P) ? start[p + 1] : M;
-    f[p] = (e - start[p]) > kLongRow ? 1 : 0;
+    if (p < P) sp[p] = start[p];
+    if (p == P) sp[P] = (int32_t)M;
 }
 
-// Segment sums: thread variant for short segments, warp variant for the long list.
-template <bool WARP>
-__global__ void k_seg_sum(int32_t P, const int32_t *__restrict__ list, int32_t nlist,
-                          const int32_t *__restrict__ start, int64_t M,
-                          const double *__restrict__ val, double *__restrict__ W) {
-    int32_t p; int lane;
-    if (!get_row<WARP>(P, list, nlist, p, lane)) return;
-    const int64_t s = start[p], e = (p + 1 < P) ? start[p + 1] : M;
-    if (!WARP && e - s > kLongRow) return;
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_seg_sum(int32_t P, const int32_t *__restrict__ list, int32_t nlist,
+                          const int32_t *__restrict__ sp, const double *__restrict__ val, double *__restrict__ W) {
+    int32_t p;
+    if (!get_row<M>(P, list, nlist, p)) return;
+    const int32_t s = sp[p], e = sp[p + 1];
+    if (M == M_THR && e - s > kLongRow) return;
     double acc = 0.0;
-    for (int64_t j = s + lane; j < e; j += (WARP ? 32 : 1)) acc = acc + val[j];
-    if (WARP) acc = warp_tree(acc);
-    if (lane == 0) W[p] = acc;
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) acc = acc + val[j];
+    acc = canon_reduce<M>(acc);
+    if (tlane<M>() == 0) W[p] = acc;
 }
 
 __global__ void k_gal_dir(int64_t P, const int32_t *__restrict__ start, const uint64_t *__restrict__ key,
@@ -732,117 +1087,181 @@ __global__ void k_gal_csr(int64_t E, const uint64_t *__restrict__ key2, const do
 // Driver
 // ---------------------------------------------------------------------------
 
-struct LongList {
-    int32_t n = 0;
-    Tmp<int32_t> *buf = nullptr;
-};
-
-static int32_t build_long_rows(const int32_t *rp, int32_t n, Tmp<int32_t> &out, cudaStream_t s) {
-    Tmp<uint8_t> f(n, s);
-    k_long_flags<<<ceil_div(n, 256), 256, 0, s>>>(rp, nullptr, n, f.get());
-    LAMG_CHECK_LAUNCH();
-    return (int32_t)compact_indices(f.get(), out.get(), n, s);
+static void build_tiers(const int32_t *rp, int32_t n, Tiers &t, cudaStream_t s) {
+    t.nw = tier_list(rp, n, 1, nullptr, t.w.get(), s);
+    t.nb = tier_list(rp, n, 2, nullptr, t.b.get(), s);
 }
 
-static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const int32_t *longrows,
-                         int32_t nlong, cudaStream_t s) {
+static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s) {
     const int32_t n = L.n;
     L.colour.alloc(n);
     Tmp<uint8_t> sel(n, s);
-    Tmp<int32_t> remaining(1, s);
+    Tmp<int32_t> ctr(2, s);  // remaining, rounds
     k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, -1);
     LAMG_CHECK_LAUNCH();
-    LAMG_CUDA(cudaMemcpyAsync(remaining.get(), &n, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const int32_t init[2] = {n, 0};
+    LAMG_CUDA(cudaMemcpyAsync(ctr.get(), init, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     const uint64_t key = colour_key(h->opt.seed, level);
-    int rounds = 0;
-    for (int32_t left = n; left > 0; rounds++) {
-        LAMG_REQUIRE(rounds < 100000, LAMG_ERR_CUDA, "colouring did not terminate");
-        LAUNCH_ROWS(k_jp_select, n, longrows, nlong, s, L.rp.get(), L.col.get(), L.colour.get(), key,
-                    sel.get());
-        LAUNCH_ROWS(k_jp_assign, n, longrows, nlong, s, L.rp.get(), L.col.get(), sel.get(),
-                    L.colour.get(), remaining.get());
-        left = read_scalar(remaining.get(), s);
+    int32_t *remaining = ctr.get(), *rounds = ctr.get() + 1;
+    int32_t left = n;
+    for (int batch = 0; left > kJPFinish; batch++) {
+        LAMG_REQUIRE(batch < 1000000, LAMG_ERR_CUDA, "colouring did not terminate");
+        for (int r = 0; r < kJPBatch; r++) {
+            LAUNCH3(k_jp_select, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                    L.col.get(), L.colour.get(), key, sel.get(), remaining, rounds);
+            LAUNCH3(k_jp_assign, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                    L.col.get(), sel.get(), L.colour.get(), remaining);
+        }
+        left = read_scalar(remaining, s);
     }
-    L.jp_rounds = rounds;
+    const int32_t batch_rounds = read_scalar(rounds, s);
+    int32_t fin_rounds = 0;
+    if (left > 0) {
+        const int32_t r = left;
+        Tmp<int32_t> R(n, s), pos(n, s), rank(r, s), cnt(r + 1, s), iptr(r + 1, s), ptr(r, s), icol(r, s);
+        Tmp<uint8_t> uncol(n, s), fsel(r, s);
+        k_uncoloured<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, uncol.get());
+        LAMG_CHECK_LAUNCH();
+        const int32_t rr = (int32_t)compact_indices(uncol.get(), R.get(), n, s);
+        LAMG_REQUIRE(rr == r, LAMG_ERR_CUDA, "colouring: remaining count mismatch");
+        const int32_t maxc = reduce_max_i32(L.colour.get(), n, s);
+        const int32_t W = (maxc + 1 + r + 63) / 64 + 1;
+        Tmp<unsigned long long> forb((size_t)r * W, s);
+        LAMG_CUDA(cudaMemsetAsync(forb.get(), 0, sizeof(unsigned long long) * (size_t)r * W, s));
+        k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(pos.get(), n, -1);
+        LAMG_CHECK_LAUNCH();
+        k_pos_scatter<<<ceil_div(r, 256), 256, 0, s>>>(R.get(), r, pos.get());
+        LAMG_CHECK_LAUNCH();
+        {
+            // exact priority order of the remaining nodes by two stable passes
+            Tmp<uint64_t> pk(r, s), pkt(r, s);
+            Tmp<int32_t> idx(r, s), idt(r, s);
+            k_iota32<<<ceil_div(r, 256), 256, 0, s>>>(idx.get(), r);
+            LAMG_CHECK_LAUNCH();
+            k_jp_hashkey<<<ceil_div(r, 256), 256, 0, s>>>(R.get(), idx.get(), r, key, pk.get());
+            LAMG_CHECK_LAUNCH();
+            radix_sort_pairs<uint64_t, int32_t>(pk.get(), idx.get(), pkt.get(), idt.get(), r, 64, s);
+            k_jp_degkey<<<ceil_div(r, 256), 256, 0, s>>>(R.get(), idx.get(), r, L.rp.get(), pk.get());
+            LAMG_CHECK_LAUNCH();
+            radix_sort_pairs<uint64_t, int32_t>(pk.get(), idx.get(), pkt.get(), idt.get(), r, 31, s);
+            k_jp_rank_from_order<<<ceil_div(r, 256), 256, 0, s>>>(idx.get(), r, rank.get());
+            LAMG_CHECK_LAUNCH();
+        }
+        k_jp_induced<<<ceil_div((int64_t)r * 32, 256), 256, 0, s>>>(R.get(), r, L.rp.get(), L.col.get(), pos.get(),
+                                                                   rank.get(), L.colour.get(), 0, cnt.get(), nullptr,
+                                                                   nullptr, nullptr, forb.get(), W);
+        LAMG_CHECK_LAUNCH();
+        LAMG_CUDA(cudaMemsetAsync(cnt.get() + r, 0, sizeof(int32_t), s));
+        exclusive_scan_i32(cnt.get(), iptr.get(), r + 1, s);
+        const int32_t ne = read_scalar(iptr.get() + r, s);
+        Tmp<uint64_t> ikey(ne, s), iktmp(ne, s);
+        Tmp<int32_t> inb(ne, s), ivtmp(ne, s), act0(r, s), act1(r, s);
+        k_jp_induced<<<ceil_div((int64_t)r * 32, 256), 256, 0, s>>>(R.get(), r, L.rp.get(), L.col.get(), pos.get(),
+                                                                   rank.get(), L.colour.get(), 1, nullptr, iptr.get(),
+                                                                   ikey.get(), inb.get(), forb.get(), W);
+        LAMG_CHECK_LAUNCH();
+        radix_sort_pairs<uint64_t, int32_t>(ikey.get(), inb.get(), iktmp.get(), ivtmp.get(), ne,
+                                            bits_for((uint64_t)r * (uint64_t)r - 1), s);
+        k_jp_finish<<<1, kBlk, 0, s>>>(R.get(), r, rank.get(), iptr.get(), inb.get(), ptr.get(), icol.get(),
+                                       fsel.get(), act0.get(), act1.get(), forb.get(), W, L.colour.get(), rounds);
+        LAMG_CHECK_LAUNCH();
+        fin_rounds = read_scalar(rounds, s);
+        LAMG_REQUIRE(fin_rounds >= 0, LAMG_ERR_CUDA, "colouring: finish kernel failed");
+    }
+    L.jp_rounds = batch_rounds + fin_rounds;
     L.ncolours = reduce_max_i32(L.colour.get(), n, s) + 1;
-    // nodes sorted by (colour, id) and the colour ranges
-    L.corder.alloc(n);
+    // nodes sorted by (colour, tier, id) and the ranges of each (colour, tier)
+    const int nbins = 3 * L.ncolours;
+    L.sorder.alloc(n);
     Tmp<uint32_t> keys(n, s), ktmp(n, s);
-    Tmp<int32_t> vtmp(n, s), cnt(L.ncolours + 1, s), cst(L.ncolours + 1, s);
-    k_to_u32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), keys.get(), n);
+    Tmp<int32_t> vtmp(n, s), cnt(nbins + 1, s), off(nbins + 1, s);
+    k_order_keys<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), L.colour.get(), n, keys.get(), L.sorder.get());
     LAMG_CHECK_LAUNCH();
-    k_iota<<<ceil_div(n, 256), 256, 0, s>>>(L.corder.get(), n);
+    radix_sort_pairs<uint32_t, int32_t>(keys.get(), L.sorder.get(), ktmp.get(), vtmp.get(), n,
+                                        bits_for((uint64_t)nbins - 1), s);
+    LAMG_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (nbins + 1), s));
+    k_hist_u32<<<ceil_div(n, 256), 256, 0, s>>>(keys.get(), n, cnt.get());
     LAMG_CHECK_LAUNCH();
-    radix_sort_pairs<uint32_t, int32_t>(keys.get(), L.corder.get(), ktmp.get(), vtmp.get(), n,
-                                        bits_for((uint64_t)L.ncolours - 1), s);
-    LAMG_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (L.ncolours + 1), s));
-    k_hist_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, cnt.get());
-    LAMG_CHECK_LAUNCH();
-    exclusive_scan_i32(cnt.get(), cst.get(), L.ncolours + 1, s);
-    L.cstart.resize(L.ncolours + 1);
-    LAMG_CUDA(cudaMemcpyAsync(L.cstart.data(), cst.get(), sizeof(int32_t) * (L.ncolours + 1),
-                              cudaMemcpyDeviceToHost, s));
+    exclusive_scan_i32(cnt.get(), off.get(), nbins + 1, s);
+    std::vector<int32_t> hoff(nbins + 1);
+    LAMG_CUDA(cudaMemcpyAsync(hoff.data(), off.get(), sizeof(int32_t) * (nbins + 1), cudaMemcpyDeviceToHost, s));
     LAMG_CUDA(cudaStreamSynchronize(s));
+    L.cb.assign(4 * L.ncolours, 0);
+    for (int c = 0; c < L.ncolours; c++)
+        for (int t = 0; t < 4; t++) L.cb[4 * c + t] = hoff[3 * c + t];
+    L.cb_dev.alloc(L.cb.size());
+    LAMG_CUDA(cudaMemcpyAsync(L.cb_dev.get(), L.cb.data(), sizeof(int32_t) * L.cb.size(), cudaMemcpyHostToDevice, s));
+}
+
+// Colours whose sweep is cheap enough for one block: no block-tier rows and
+// (entries of the colour) * K <= kTailWork.  Consecutive such colours are
+// swept by one single-block launch; the others by their own launches.
+constexpr int64_t kTailWork = 16384;
+
+__global__ void k_colour_entries(const int32_t *__restrict__ rp, const int32_t *__restrict__ colour, int32_t n,
+                                 int32_t *__restrict__ ent) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) atomicAdd(&ent[colour[u]], rp[u + 1] - rp[u]);
 }
 
 // TVs and their sweeps; returns the largest per-TV energy ratio of the last
 // sweep when the relaxation-speed test is enabled (else +inf).
-static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const double *diag, double *X,
+static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, const double *diag, double *X,
                         cudaStream_t s) {
     const int32_t n = L.n, K = L.K;
     const lamg_options &o = h->opt;
     k_tv_init<<<ceil_div((int64_t)n * K, 256), 256, 0, s>>>(X, (int64_t)n * K, tv_key(o.seed, level));
     LAMG_CHECK_LAUNCH();
-    // long rows in colour order, with per-colour ranges
-    Tmp<uint8_t> f(n, s);
-    Tmp<int32_t> pos(n, s), lorder(n, s);
-    k_long_flags<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), L.corder.get(), n, f.get());
-    LAMG_CHECK_LAUNCH();
-    int32_t nl = (int32_t)compact_indices(f.get(), pos.get(), n, s);
-    std::vector<int32_t> lstart(L.ncolours + 1, 0);
-    if (nl > 0) {
-        k_gather_i32<<<ceil_div(nl, 256), 256, 0, s>>>(pos.get(), L.corder.get(), lorder.get(), nl);
-        LAMG_CHECK_LAUNCH();
-        std::vector<int32_t> hpos(nl);
-        LAMG_CUDA(cudaMemcpyAsync(hpos.data(), pos.get(), sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
-        LAMG_CUDA(cudaStreamSynchronize(s));
-        // positions in corder are sorted; colour c covers corder [cstart[c], cstart[c+1])
-        int32_t j = 0;
-        for (int c = 0; c <= L.ncolours; c++) {
-            while (j < nl && hpos[j] < L.cstart[c]) j++;
-            lstart[c] = j;
-        }
-        lstart[L.ncolours] = nl;
-    }
+    const int32_t *ord = L.sorder.get();
     const bool test = o.relax_fast_ratio > 0.0 && o.nu_tv >= 2;
     Tmp<double> eu(test ? n : 0, s);
-    Tmp<int32_t> noneL(0, s);
     double eprev[16], ecur[16];
+    // per-colour entry counts -> which colours the single-block sweep takes
+    std::vector<int32_t> ent(L.ncolours);
+    {
+        Tmp<int32_t> de(L.ncolours, s);
+        LAMG_CUDA(cudaMemsetAsync(de.get(), 0, sizeof(int32_t) * L.ncolours, s));
+        k_colour_entries<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), L.colour.get(), n, de.get());
+        LAMG_CHECK_LAUNCH();
+        LAMG_CUDA(cudaMemcpyAsync(ent.data(), de.get(), sizeof(int32_t) * L.ncolours, cudaMemcpyDeviceToHost, s));
+        LAMG_CUDA(cudaStreamSynchronize(s));
+    }
+    auto small = [&](int c) {
+        return L.cb[4 * c + 3] == L.cb[4 * c + 2] && (int64_t)ent[c] * K <= kTailWork;
+    };
     for (int sw = 1; sw <= o.nu_tv; sw++) {
-        for (int c = 0; c < L.ncolours; c++) {
-            const int32_t c0 = L.cstart[c], c1 = L.cstart[c + 1];
-            if (c1 > c0) {
-                int b, t;
-                grid_for<false>(c1 - c0, b, t);
-                k_tv_sweep<false><<<b, t, 0, s>>>(c1 - c0, L.corder.get() + c0, 0, L.rp.get(),
-                                                 L.col.get(), L.w.get(), diag, K, X);
+        for (int c = 0; c < L.ncolours;) {
+            if (small(c)) {
+                int c1 = c;
+                while (c1 < L.ncolours && small(c1)) c1++;
+                k_tv_sweep_tail<<<1, kBlk, 0, s>>>(c, c1, L.cb_dev.get(), ord, L.rp.get(), L.col.get(), L.w.get(),
+                                                   diag, K, X);
+                LAMG_CHECK_LAUNCH();
+                c = c1;
+                continue;
+            }
+            const int32_t t0 = L.cb[4 * c], t1 = L.cb[4 * c + 1], t2 = L.cb[4 * c + 2], t3 = L.cb[4 * c + 3];
+            if (t1 > t0) {
+                k_tv_sweep<M_THR><<<ceil_div(t1 - t0, 256), 256, 0, s>>>(t1 - t0, ord + t0, 0, L.rp.get(),
+                                                                        L.col.get(), L.w.get(), diag, K, X);
                 LAMG_CHECK_LAUNCH();
             }
-            const int32_t l0 = lstart[c], l1 = lstart[c + 1];
-            if (l1 > l0) {
-                int b, t;
-                grid_for<true>(l1 - l0, b, t);
-                k_tv_sweep<true><<<b, t, 0, s>>>(0, lorder.get() + l0, l1 - l0, L.rp.get(),
-                                                L.col.get(), L.w.get(), diag, K, X);
+            if (t2 > t1) {
+                k_tv_sweep<M_WARP><<<ceil_div((int64_t)(t2 - t1) * 32, 256), 256, 0, s>>>(
+                    0, ord + t1, t2 - t1, L.rp.get(), L.col.get(), L.w.get(), diag, K, X);
                 LAMG_CHECK_LAUNCH();
             }
+            if (t3 > t2) {
+                k_tv_sweep<M_BLK><<<t3 - t2, kBlk, 0, s>>>(0, ord + t2, t3 - t2, L.rp.get(), L.col.get(),
+                                                          L.w.get(), diag, K, X);
+                LAMG_CHECK_LAUNCH();
+            }
+            c++;
         }
         if (test && sw >= o.nu_tv - 1) {
-            Tmp<int32_t> lr(n, s);
-            int32_t nlr = build_long_rows(L.rp.get(), n, lr, s);
             for (int k = 0; k < K; k++) {
-                LAUNCH_ROWS(k_tv_energy, n, lr.get(), nlr, s, L.rp.get(), L.col.get(), L.w.get(), K, k,
-                            X, eu.get());
+                LAUNCH3(k_tv_energy, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                        L.col.get(), L.w.get(), K, k, X, eu.get());
                 double E = canon_sum_global(eu.get(), n, s);
                 if (sw == o.nu_tv - 1) eprev[k] = E; else ecur[k] = E;
             }
@@ -858,15 +1277,15 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const double *dia
 }
 
 // Aggregation of one level; fills L.agg, L.state, L.nc, L.alpha, L.rounds, L.sel_round.
-static void aggregate_level(lamg_ctx *h, SetupLevel &L, const int32_t *longrows, int32_t nlong,
-                            const double *score, const double *maxw, cudaStream_t s) {
+static void aggregate_level(lamg_ctx *h, SetupLevel &L, const Tiers &T, const double *score, const double *maxw,
+                            cudaStream_t s) {
     const int32_t n = L.n;
     const lamg_options &o = h->opt;
     Tmp<int32_t> state(n, s), seed(n, s), best(n, s), nstate(n, s), nseed(n, s), bseed(n, s);
     L.state.alloc(n);
     L.agg.alloc(n);
-    LAUNCH_ROWS(k_node_state, n, longrows, nlong, s, L.rp.get(), L.col.get(), L.w.get(), maxw,
-                o.weak_tol, L.hub.get(), state.get());
+    LAUNCH3(k_node_state, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
+            L.w.get(), maxw, o.weak_tol, L.hub.get(), state.get());
     LAMG_CUDA(cudaMemsetAsync(seed.get(), 0xFF, sizeof(int32_t) * n, s));
     const int64_t nd = count_equal_i32(state.get(), n, ST_D, s);
     const double amax = 0.7 / o.gamma;
@@ -875,7 +1294,8 @@ static void aggregate_level(lamg_ctx *h, SetupLevel &L, const int32_t *longrows,
     Tmp<int32_t> changed(1, s);
     Tmp<unsigned long long> cnt(1, s);
     for (r = 1; r <= o.max_rounds; r++) {
-        LAUNCH_ROWS(k_best, n, longrows, nlong, s, L.rp.get(), L.col.get(), score, state.get(), best.get());
+        LAUNCH3(k_best, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
+                score, state.get(), best.get());
         LAMG_CUDA(cudaMemcpyAsync(nstate.get(), state.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
         LAMG_CUDA(cudaMemcpyAsync(nseed.get(), seed.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
         LAMG_CUDA(cudaMemsetAsync(changed.get(), 0, sizeof(int32_t), s));
@@ -887,8 +1307,11 @@ static void aggregate_level(lamg_ctx *h, SetupLevel &L, const int32_t *longrows,
         LAMG_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(unsigned long long), s));
         k_count_su<<<ceil_div(n, 256), 256, 0, s>>>(state.get(), n, cnt.get());
         LAMG_CHECK_LAUNCH();
-        const int32_t ch = read_scalar(changed.get(), s);
-        const unsigned long long su = read_scalar(cnt.get(), s);
+        int32_t ch;
+        unsigned long long su;
+        LAMG_CUDA(cudaMemcpyAsync(&ch, changed.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LAMG_CUDA(cudaMemcpyAsync(&su, cnt.get(), sizeof(su), cudaMemcpyDeviceToHost, s));
+        LAMG_CUDA(cudaStreamSynchronize(s));
         const int64_t nc = (int64_t)su + (nd > 0 ? 1 : 0);
         const double alpha = (double)nc / (double)n;
         if (fabs(alpha - amax) < fabs(best_alpha - amax)) {
@@ -943,15 +1366,15 @@ static void galerkin_level(SetupLevel &F, SetupLevel &C, const int32_t *erow, cu
         LAMG_CHECK_LAUNCH();
     }
     const int64_t P = compact_indices(hf.get(), start.get(), M, s);
-    Tmp<uint8_t> lf(P, s);
-    Tmp<int32_t> lsegs(P, s);
     Tmp<double> W(P, s);
-    int64_t nls = 0;
     if (P) {
-        k_seg_long<<<ceil_div(P, 256), 256, 0, s>>>(P, start.get(), M, lf.get());
+        Tmp<int32_t> sp(P + 1, s);
+        k_seg_ptr<<<ceil_div(P + 1, 256), 256, 0, s>>>(P, start.get(), M, sp.get());
         LAMG_CHECK_LAUNCH();
-        nls = compact_indices(lf.get(), lsegs.get(), P, s);
-        LAUNCH_ROWS(k_seg_sum, (int32_t)P, lsegs.get(), (int32_t)nls, s, start.get(), M, val.get(), W.get());
+        Tiers ST((int32_t)P, s);
+        build_tiers(sp.get(), (int32_t)P, ST, s);
+        LAUNCH3(k_seg_sum, (int32_t)P, (const int32_t *)nullptr, ST.w.get(), ST.nw, ST.b.get(), ST.nb, s, sp.get(),
+                val.get(), W.get());
     }
     const int64_t E = 2 * P;
     Tmp<uint64_t> key2(E, s), k2tmp(E, s);
@@ -1018,17 +1441,22 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         }
     }
     const int maxl = std::min(o.max_levels, 128);
+    PhaseTimer pt(s);
+    pt.mark("ingest");
     for (int l = 0;; l++) {
         SetupLevel &L = h->sl[l];
         const int32_t nl = L.n;
         h->L = l + 1;
-        Tmp<int32_t> longrows(nl, s);
-        const int32_t nlong = build_long_rows(L.rp.get(), nl, longrows, s);
+        pt.level = l;
+        Tiers T(nl, s);
+        build_tiers(L.rp.get(), nl, T, s);
         Tmp<double> diag(nl, s), maxw(nl, s);
         L.hub.alloc(nl);
-        LAUNCH_ROWS(k_node_stats, nl, longrows.get(), nlong, s, L.rp.get(), L.col.get(), L.w.get(),
-                    o.hub_factor, diag.get(), maxw.get(), L.hub.get());
-        colour_level(h, L, l, longrows.get(), nlong, s);
+        LAUNCH3(k_node_stats, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                L.col.get(), L.w.get(), o.hub_factor, diag.get(), maxw.get(), L.hub.get());
+        pt.mark("stats");
+        colour_level(h, L, l, T, s);
+        pt.mark("colour");
         if (nl < o.n_coarsest || l + 1 >= maxl) {
             L.coarsest = 1;
             L.stop_reason = nl < o.n_coarsest ? 1 : 4;
@@ -1040,7 +1468,8 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         if (K < 1) K = 1;
         L.K = K;
         Tmp<double> X((size_t)nl * K, s);
-        L.tv_ratio = relax_tvs(h, L, l, diag.get(), X.get(), s);
+        L.tv_ratio = relax_tvs(h, L, l, T, diag.get(), X.get(), s);
+        pt.mark("tv");
         if (o.keep_setup_data) {
             L.tv.alloc((size_t)nl * K);
             LAMG_CUDA(cudaMemcpyAsync(L.tv.get(), X.get(), sizeof(double) * nl * K, cudaMemcpyDeviceToDevice, s));
@@ -1052,10 +1481,11 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         }
         // per-node TV quantities, then per-entry affinity / energy ratio / score
         Tmp<double> XX(nl, s), ystar((size_t)nl * K, s), emin((size_t)nl * K, s);
-        LAUNCH_ROWS(k_node_pre, nl, longrows.get(), nlong, s, L.rp.get(), L.col.get(), L.w.get(),
-                    diag.get(), K, X.get(), XX.get(), ystar.get(), emin.get());
+        LAUNCH3(k_node_pre, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                L.col.get(), L.w.get(), diag.get(), K, X.get(), XX.get(), ystar.get(), emin.get());
         Tmp<int32_t> erow(L.nnz, s);
-        LAUNCH_ROWS(k_entry_rows, nl, longrows.get(), nlong, s, L.rp.get(), erow.get());
+        LAUNCH3(k_entry_rows, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                erow.get());
         Tmp<double> score(L.nnz, s);
         if (o.keep_setup_data) {
             L.aff.alloc(L.nnz);
@@ -1072,7 +1502,9 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
                 LAMG_CUDA(cudaMemcpyAsync(L.score.get(), score.get(), sizeof(double) * L.nnz,
                                           cudaMemcpyDeviceToDevice, s));
         }
-        aggregate_level(h, L, longrows.get(), nlong, score.get(), maxw.get(), s);
+        pt.mark("scores");
+        aggregate_level(h, L, T, score.get(), maxw.get(), s);
+        pt.mark("aggregate");
         if (L.alpha > o.alpha_stall) {
             L.coarsest = 1;
             L.stop_reason = 3;
@@ -1080,6 +1512,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         }
         h->sl.emplace_back();
         galerkin_level(h->sl[l], h->sl[l + 1], erow.get(), s);
+        pt.mark("galerkin");
     }
     cycle_indices(h);
     LAMG_CUDA(cudaStreamSynchronize(s));

@@ -21,6 +21,8 @@ namespace lamg {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRedBlocks = 608;     // 152 SMs x 4 blocks for reductions
 constexpr int kRedThreads = 256;
+constexpr int64_t kTailWork32 = 65536;  // entries of a colour run the single-block sweep takes (FP32)
+constexpr int64_t kTailWork64 = 8192;   // same for FP64
 
 // scratch layout (doubles)
 enum {
@@ -34,11 +36,16 @@ enum {
 // Layout construction
 // ---------------------------------------------------------------------------
 
+// solve row tiers: one thread (<= kLongRow entries), one warp (<= kHugeSolve), one block
+__host__ __device__ __forceinline__ int solve_tier(int64_t len) {
+    return len <= kLongRow ? 0 : (len <= kHugeSolve ? 1 : 2);
+}
+
 __global__ void k_perm_keys(const int32_t *__restrict__ rp, const int32_t *__restrict__ colour,
                             int32_t n, uint32_t *__restrict__ key, int32_t *__restrict__ val) {
     int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n) return;
-    key[u] = (uint32_t)colour[u] * 2u + ((rp[u + 1] - rp[u]) > kLongRow ? 1u : 0u);
+    key[u] = (uint32_t)colour[u] * 3u + (uint32_t)solve_tier(rp[u + 1] - rp[u]);
     val[u] = u;
 }
 
@@ -79,9 +86,9 @@ __global__ void k_permute_entries(int32_t n, const int32_t *__restrict__ rp, con
     }
 }
 
-__global__ void k_long_flag_rows(const int32_t *__restrict__ prp, int32_t n, uint8_t *__restrict__ f) {
+__global__ void k_tier_rows(const int32_t *__restrict__ ptr, int32_t n, int tier, uint8_t *__restrict__ f) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) f[i] = (prp[i + 1] - prp[i]) > kLongRow ? 1 : 0;
+    if (i < n) f[i] = solve_tier(ptr[i + 1] - ptr[i]) == tier ? 1 : 0;
 }
 
 __global__ void k_pagg(const int32_t *__restrict__ perm, const int32_t *__restrict__ agg,
@@ -95,62 +102,56 @@ __global__ void k_pagg(const int32_t *__restrict__ perm, const int32_t *__restri
     val[i] = i;
 }
 
-__global__ void k_long_members(const int32_t *__restrict__ mptr, int32_t nc, uint8_t *__restrict__ f) {
-    int32_t J = blockIdx.x * blockDim.x + threadIdx.x;
-    if (J < nc) f[J] = (mptr[J + 1] - mptr[J]) > kLongRow ? 1 : 0;
+// Dense coarsest operator: M = A + (1/n) 1 1^T (SPD for a connected
+// Laplacian; its inverse maps a zero-sum b to the zero-mean solution).  The
+// inverse is formed by Gauss-Jordan elimination of [M | I] without pivoting
+// (valid for SPD M), one all-SM launch per pivot, double-buffered so that
+// every launch reads the previous step only.
+__global__ void k_dense_assemble(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const double *__restrict__ w, double *__restrict__ G) {
+    // G is n x 2n, row-major: [M | I]
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * 2 * n) return;
+    const int32_t i = (int32_t)(q / (2 * n)), j = (int32_t)(q % (2 * n));
+    double v;
+    if (j >= n) {
+        v = (j - n == i) ? 1.0 : 0.0;
+    } else {
+        v = 1.0 / (double)n;
+        if (i == j) {
+            double d = 0.0;
+            for (int32_t e = rp[i]; e < rp[i + 1]; e++) d += w[e];
+            v += d;
+        } else {
+            for (int32_t e = rp[i]; e < rp[i + 1]; e++)
+                if (col[e] == j) v -= w[e];
+        }
+    }
+    G[q] = v;
 }
 
-// Dense coarsest operator: M = A + (1/n) 1 1^T (SPD for a connected
-// Laplacian), Cholesky M = L L^T, inverse M^-1 = L^-T L^-1.  One block.
-__global__ void k_dense_inverse(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                const double *__restrict__ w, double *__restrict__ M,
-                                double *__restrict__ Y, double *__restrict__ Minv, int32_t *err) {
-    const int t = threadIdx.x, T = blockDim.x;
-    const double inv_n = 1.0 / (double)n;
-    for (int64_t k = t; k < (int64_t)n * n; k += T) M[k] = inv_n;
-    __syncthreads();
-    for (int32_t i = t; i < n; i += T) {
-        double d = 0.0;
-        for (int32_t j = rp[i]; j < rp[i + 1]; j++) {
-            M[(int64_t)i * n + col[j]] += -w[j];
-            d += w[j];
-        }
-        M[(int64_t)i * n + i] += d;
+__global__ void k_gauss_jordan_step(int32_t n, int32_t k, const double *__restrict__ G, double *__restrict__ H,
+                                    int32_t *err) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t W = 2 * (int64_t)n;
+    if (q >= (int64_t)n * W) return;
+    const int32_t i = (int32_t)(q / W);
+    const int64_t j = q % W;
+    const double piv = G[(int64_t)k * W + k];
+    if (!(piv > 0.0)) {
+        if (q == 0) *err = 1;
+        H[q] = G[q];
+        return;
     }
-    __syncthreads();
-    __shared__ double piv;
-    for (int32_t j = 0; j < n; j++) {
-        if (t == 0) {
-            double a = M[(int64_t)j * n + j];
-            if (!(a > 0.0)) { *err = 1; a = 1.0; }
-            piv = sqrt(a);
-            M[(int64_t)j * n + j] = piv;
-        }
-        __syncthreads();
-        for (int32_t i = j + 1 + t; i < n; i += T) M[(int64_t)i * n + j] /= piv;
-        __syncthreads();
-        const int64_t m = n - j - 1;
-        for (int64_t q = t; q < m * m; q += T) {
-            const int32_t i = j + 1 + (int32_t)(q / m), k = j + 1 + (int32_t)(q % m);
-            if (k <= i) M[(int64_t)i * n + k] -= M[(int64_t)i * n + j] * M[(int64_t)k * n + j];
-        }
-        __syncthreads();
-    }
-    // Y = L^-1, column c by forward substitution (one thread per column)
-    for (int32_t c = t; c < n; c += T) {
-        for (int32_t i = 0; i < n; i++) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int32_t k = c; k < i; k++) s -= M[(int64_t)i * n + k] * Y[(int64_t)k * n + c];
-            Y[(int64_t)i * n + c] = (i < c) ? 0.0 : s / M[(int64_t)i * n + i];
-        }
-    }
-    __syncthreads();
-    for (int64_t q = t; q < (int64_t)n * n; q += T) {
-        const int32_t i = (int32_t)(q / n), j = (int32_t)(q % n);
-        double s = 0.0;
-        for (int32_t k = max(i, j); k < n; k++) s += Y[(int64_t)k * n + i] * Y[(int64_t)k * n + j];
-        Minv[q] = s;
-    }
+    const double pk = G[(int64_t)k * W + j] / piv;
+    H[q] = (i == k) ? pk : G[q] - G[(int64_t)i * W + k] * pk;
+}
+
+__global__ void k_dense_extract(int32_t n, const double *__restrict__ G, double *__restrict__ Minv) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * n) return;
+    const int32_t i = (int32_t)(q / n), j = (int32_t)(q % n);
+    Minv[q] = G[(int64_t)i * 2 * n + n + j];
 }
 
 void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
@@ -166,7 +167,7 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         V.nnz = S.nnz;
         V.perm.alloc(n);
         iperm[l].alloc(n);
-        const int nbins = 2 * S.ncolours;
+        const int nbins = 3 * S.ncolours;
         Tmp<uint32_t> key(n, s), ktmp(n, s);
         Tmp<int32_t> vtmp(n, s), cnt(nbins + 1, s), off(nbins + 1, s);
         k_perm_keys<<<ceil_div(n, 256), 256, 0, s>>>(S.rp.get(), S.colour.get(), n, key.get(), V.perm.get());
@@ -183,10 +184,11 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         std::vector<int32_t> hoff(nbins + 1);
         LAMG_CUDA(cudaMemcpyAsync(hoff.data(), off.get(), sizeof(int32_t) * (nbins + 1), cudaMemcpyDeviceToHost, s));
         LAMG_CUDA(cudaStreamSynchronize(s));
-        V.cs.resize(S.ncolours + 1);
-        V.cl.resize(S.ncolours);
-        for (int c = 0; c < S.ncolours; c++) { V.cs[c] = hoff[2 * c]; V.cl[c] = hoff[2 * c + 1]; }
-        V.cs[S.ncolours] = n;
+        V.cb.assign(4 * S.ncolours, 0);
+        for (int c = 0; c < S.ncolours; c++)
+            for (int t = 0; t < 4; t++) V.cb[4 * c + t] = hoff[3 * c + t];
+        V.cb_dev.alloc(V.cb.size());
+        LAMG_CUDA(cudaMemcpyAsync(V.cb_dev.get(), V.cb.data(), sizeof(int32_t) * V.cb.size(), cudaMemcpyHostToDevice, s));
         // permuted CSR
         Tmp<int32_t> deg(n + 1, s);
         V.rp.alloc(n + 1);
@@ -202,11 +204,41 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
                 V.w64.get(), V.w32.get());
             LAMG_CHECK_LAUNCH();
         }
+        // sweep plan: runs of colours without block-tier rows and few entries go
+        // to one single-block launch (limits differ: FP64 throughput per SM is low)
+        {
+            std::vector<int32_t> hrp(n + 1);
+            LAMG_CUDA(cudaMemcpyAsync(hrp.data(), V.rp.get(), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+            LAMG_CUDA(cudaStreamSynchronize(s));
+            for (int p = 0; p < 2; p++) {
+                const int64_t lim = p == 0 ? kTailWork64 : kTailWork32;
+                auto small = [&](int c) {
+                    return V.cb[4 * c + 3] == V.cb[4 * c + 2] &&
+                           (int64_t)hrp[V.cb[4 * c + 3]] - hrp[V.cb[4 * c]] <= lim;
+                };
+                V.seg[p].clear();
+                for (int c = 0; c < S.ncolours;) {
+                    if (small(c)) {
+                        int c1 = c;
+                        while (c1 < S.ncolours && small(c1)) c1++;
+                        V.seg[p].insert(V.seg[p].end(), {c, c1, 1});
+                        c = c1;
+                    } else {
+                        V.seg[p].insert(V.seg[p].end(), {c, c + 1, 0});
+                        c++;
+                    }
+                }
+            }
+        }
         Tmp<uint8_t> f(n, s);
-        k_long_flag_rows<<<ceil_div(n, 256), 256, 0, s>>>(V.rp.get(), n, f.get());
+        V.wrows.alloc(n);
+        V.brows.alloc(n);
+        k_tier_rows<<<ceil_div(n, 256), 256, 0, s>>>(V.rp.get(), n, 1, f.get());
         LAMG_CHECK_LAUNCH();
-        V.longrows.alloc(n);
-        V.nlong = (int32_t)compact_indices(f.get(), V.longrows.get(), n, s);
+        V.nw = (int32_t)compact_indices(f.get(), V.wrows.get(), n, s);
+        k_tier_rows<<<ceil_div(n, 256), 256, 0, s>>>(V.rp.get(), n, 2, f.get());
+        LAMG_CHECK_LAUNCH();
+        V.nb = (int32_t)compact_indices(f.get(), V.brows.get(), n, s);
     }
     for (int l = 0; l + 1 < L; l++) {
         SetupLevel &S = h->sl[l];
@@ -228,10 +260,14 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         LAMG_CHECK_LAUNCH();
         exclusive_scan_i32(cnt.get(), V.mptr.get(), nc + 1, s);
         Tmp<uint8_t> f(nc, s);
-        k_long_members<<<ceil_div(nc, 256), 256, 0, s>>>(V.mptr.get(), nc, f.get());
+        V.wagg.alloc(nc);
+        V.bagg.alloc(nc);
+        k_tier_rows<<<ceil_div(nc, 256), 256, 0, s>>>(V.mptr.get(), nc, 1, f.get());
         LAMG_CHECK_LAUNCH();
-        V.longagg.alloc(nc);
-        V.nlongagg = (int32_t)compact_indices(f.get(), V.longagg.get(), nc, s);
+        V.nwagg = (int32_t)compact_indices(f.get(), V.wagg.get(), nc, s);
+        k_tier_rows<<<ceil_div(nc, 256), 256, 0, s>>>(V.mptr.get(), nc, 2, f.get());
+        LAMG_CHECK_LAUNCH();
+        V.nbagg = (int32_t)compact_indices(f.get(), V.bagg.get(), nc, s);
     }
     // coarsest level: dense inverse when small enough
     SolveLevel &C = h->lv[L - 1];
@@ -239,11 +275,19 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         const int32_t n = C.n;
         C.dense = 1;
         C.minv.alloc((size_t)n * n);
-        Tmp<double> M((size_t)n * n, s), Y((size_t)n * n, s);
+        Tmp<double> G((size_t)n * 2 * n, s), H((size_t)n * 2 * n, s);
         Tmp<int32_t> err(1, s);
         LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
-        k_dense_inverse<<<1, 1024, 0, s>>>(n, C.rp.get(), C.col.get(), C.w64.get(), M.get(), Y.get(),
-                                           C.minv.get(), err.get());
+        const int64_t tot = (int64_t)n * 2 * n;
+        k_dense_assemble<<<ceil_div(tot, 256), 256, 0, s>>>(n, C.rp.get(), C.col.get(), C.w64.get(), G.get());
+        LAMG_CHECK_LAUNCH();
+        double *a = G.get(), *bb = H.get();
+        for (int32_t k = 0; k < n; k++) {
+            k_gauss_jordan_step<<<ceil_div(tot, 256), 256, 0, s>>>(n, k, a, bb, err.get());
+            LAMG_CHECK_LAUNCH();
+            std::swap(a, bb);
+        }
+        k_dense_extract<<<ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, a, C.minv.get());
         LAMG_CHECK_LAUNCH();
         LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_ARG,
                      "coarsest operator is not positive definite (disconnected graph?)");
@@ -255,106 +299,148 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
 // Cycle kernels (T = double or float)
 // ---------------------------------------------------------------------------
 
-// Gauss-Seidel update of one colour (Eq. (2.3)): x_i = (b_i + sum w x_v) / sum w.
-template <class T>
-__global__ void __launch_bounds__(256) k_sweep_thr(int32_t row0, int32_t nrows, const int32_t *__restrict__ rp,
-                                                   const int32_t *__restrict__ col, const T *__restrict__ w,
-                                                   const T *__restrict__ b, T *__restrict__ x) {
-    const int32_t i = row0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= row0 + nrows) return;
-    const int32_t s = rp[i], e = rp[i + 1];
-    T acc = b[i], d = T(0);
-    for (int32_t j = s; j < e; j++) {
-        const T wj = w[j];
-        acc += wj * x[col[j]];
-        d += wj;
-    }
-    x[i] = acc / d;
+// Tier helpers of the solve (any summation order is allowed here).
+enum { M_THR = 0, M_WARP = 1, M_BLK = 2 };
+template <int M> __device__ __forceinline__ int slane() {
+    return M == M_THR ? 0 : (M == M_WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x);
 }
+template <int M> __device__ __forceinline__ int sstride() { return M == M_THR ? 1 : (M == M_WARP ? 32 : kBlk); }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_sweep_warp(int32_t row0, int32_t nrows, const int32_t *__restrict__ rp,
-                                                    const int32_t *__restrict__ col, const T *__restrict__ w,
-                                                    const T *__restrict__ b, T *__restrict__ x) {
-    const int32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wg >= nrows) return;
-    const int32_t i = row0 + wg;
+__device__ __forceinline__ T warp_allsum(T v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// block sum of two values, result in every thread (blockDim = kBlk)
+template <class T>
+__device__ __forceinline__ void block_allsum2(T &a, T &b) {
+    __shared__ T sa[32], sb[32];
+    a = warp_allsum(a);
+    b = warp_allsum(b);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = a; sb[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    a = T(0);
+    b = T(0);
+#pragma unroll 8
+    for (int k = 0; k < kBlk / 32; k++) { a += sa[k]; b += sb[k]; }
+}
+
+template <int M, class T>
+__device__ __forceinline__ void reduce2(T &a, T &b) {
+    if (M == M_WARP) { a = warp_allsum(a); b = warp_allsum(b); }
+    if (M == M_BLK) block_allsum2(a, b);
+}
+
+// Gauss-Seidel update of row i (Eq. (2.3)): x_i = (b_i + sum w x_v) / sum w.
+template <int M, class T>
+__device__ __forceinline__ void gs_row(int32_t i, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                       const T *__restrict__ w, const T *__restrict__ b, T *__restrict__ x) {
     const int32_t s = rp[i], e = rp[i + 1];
     T acc = T(0), d = T(0);
-    for (int32_t j = s + lane; j < e; j += 32) {
+    for (int32_t j = s + slane<M>(); j < e; j += sstride<M>()) {
         const T wj = w[j];
         acc += wj * x[col[j]];
         d += wj;
     }
-    for (int o = 16; o; o >>= 1) {
-        acc += __shfl_xor_sync(kFull, acc, o);
-        d += __shfl_xor_sync(kFull, d, o);
-    }
-    if (lane == 0) x[i] = (b[i] + acc) / d;
+    reduce2<M>(acc, d);
+    if (slane<M>() == 0) x[i] = (b[i] + acc) / d;
+    if (M == M_BLK) __syncthreads();
 }
 
-// r = b - A x = b + sum_v w (x_v - x_i)
-template <class T>
-__global__ void __launch_bounds__(256) k_resid_thr(int32_t n, const int32_t *__restrict__ rp,
-                                                   const int32_t *__restrict__ col, const T *__restrict__ w,
-                                                   const T *__restrict__ b, const T *__restrict__ x,
-                                                   T *__restrict__ r) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// r_i = b_i - (A x)_i = b_i + sum_v w (x_v - x_i)
+template <int M, class T>
+__device__ __forceinline__ void resid_row(int32_t i, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                          const T *__restrict__ w, const T *__restrict__ b, const T *__restrict__ x,
+                                          T *__restrict__ r) {
     const int32_t s = rp[i], e = rp[i + 1];
-    if (e - s > kLongRow) return;
     const T xi = x[i];
-    T acc = b[i];
-    for (int32_t j = s; j < e; j++) acc += w[j] * (x[col[j]] - xi);
-    r[i] = acc;
+    T acc = T(0), dummy = T(0);
+    for (int32_t j = s + slane<M>(); j < e; j += sstride<M>()) acc += w[j] * (x[col[j]] - xi);
+    reduce2<M>(acc, dummy);
+    if (slane<M>() == 0) r[i] = b[i] + acc;
+    if (M == M_BLK) __syncthreads();
 }
 
+// one colour's rows of a tier: THR/WARP/BLK over the contiguous range [row0, row0 + nrows)
+template <int M, class T>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256)
+k_sweep(int32_t row0, int32_t nrows, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+        const T *__restrict__ w, const T *__restrict__ b, T *__restrict__ x) {
+    int64_t k;
+    if (M == M_THR) k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    else if (M == M_WARP) k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    else k = blockIdx.x;
+    if (k >= nrows) return;
+    gs_row<M, T>(row0 + (int32_t)k, rp, col, w, b, x);
+}
+
+// Colours c0 .. c1-1 of one sweep in a single block, colour by colour.
 template <class T>
-__global__ void __launch_bounds__(256) k_resid_warp(const int32_t *__restrict__ list, int32_t nlist,
+__global__ void __launch_bounds__(kBlk) k_sweep_tail(int32_t c0, int32_t c1, const int32_t *__restrict__ cb,
                                                     const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                                     const T *__restrict__ w, const T *__restrict__ b,
-                                                    const T *__restrict__ x, T *__restrict__ r) {
-    const int32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wg >= nlist) return;
-    const int32_t i = list[wg];
-    const int32_t s = rp[i], e = rp[i + 1];
-    const T xi = x[i];
-    T acc = T(0);
-    for (int32_t j = s + lane; j < e; j += 32) acc += w[j] * (x[col[j]] - xi);
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (lane == 0) r[i] = b[i] + acc;
+                                                    T *__restrict__ x) {
+    const int warp = threadIdx.x >> 5;
+    for (int32_t c = c0; c < c1; c++) {
+        const int32_t t0 = cb[4 * c], t1 = cb[4 * c + 1], t2 = cb[4 * c + 2], t3 = cb[4 * c + 3];
+        for (int32_t i = t0 + threadIdx.x; i < t1; i += kBlk) gs_row<M_THR, T>(i, rp, col, w, b, x);
+        for (int32_t i = t1 + warp; i < t2; i += kBlk / 32) gs_row<M_WARP, T>(i, rp, col, w, b, x);
+        for (int32_t i = t2; i < t3; i++) gs_row<M_BLK, T>(i, rp, col, w, b, x);
+        __syncthreads();
+    }
+}
+
+// residual: THR over all rows (skips the warp/block tiers), WARP/BLK over row lists
+template <int M, class T>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256)
+k_resid(int32_t n, const int32_t *__restrict__ list, int32_t nlist, const int32_t *__restrict__ rp,
+        const int32_t *__restrict__ col, const T *__restrict__ w, const T *__restrict__ b, const T *__restrict__ x,
+        T *__restrict__ r) {
+    int32_t i;
+    if (M == M_THR) {
+        const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (k >= n) return;
+        i = (int32_t)k;
+        if (rp[i + 1] - rp[i] > kLongRow) return;
+    } else if (M == M_WARP) {
+        const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (k >= nlist) return;
+        i = list[k];
+    } else {
+        if (blockIdx.x >= nlist) return;
+        i = list[blockIdx.x];
+    }
+    resid_row<M, T>(i, rp, col, w, b, x, r);
 }
 
 // b^c_J = mu * sum_{i in T_J} r_i ; x^c_J = 0   (Eq. (3.9))
-template <class T>
-__global__ void __launch_bounds__(256) k_restrict_thr(int32_t nc, const int32_t *__restrict__ mptr,
-                                                      const int32_t *__restrict__ mlist, const T *__restrict__ r,
-                                                      T mu, T *__restrict__ bc, T *__restrict__ xc) {
-    const int32_t J = blockIdx.x * blockDim.x + threadIdx.x;
-    if (J >= nc) return;
-    const int32_t s = mptr[J], e = mptr[J + 1];
-    xc[J] = T(0);
-    if (e - s > kLongRow) return;
-    T acc = T(0);
-    for (int32_t j = s; j < e; j++) acc += r[mlist[j]];
-    bc[J] = mu * acc;
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_restrict_warp(const int32_t *__restrict__ list, int32_t nlist,
-                                                       const int32_t *__restrict__ mptr,
-                                                       const int32_t *__restrict__ mlist, const T *__restrict__ r,
-                                                       T mu, T *__restrict__ bc) {
-    const int32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wg >= nlist) return;
-    const int32_t J = list[wg];
-    T acc = T(0);
-    for (int32_t j = mptr[J] + lane; j < mptr[J + 1]; j += 32) acc += r[mlist[j]];
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (lane == 0) bc[J] = mu * acc;
+template <int M, class T>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256)
+k_restrict(int32_t nc, const int32_t *__restrict__ list, int32_t nlist, const int32_t *__restrict__ mptr,
+           const int32_t *__restrict__ mlist, const T *__restrict__ r, T mu, T *__restrict__ bc,
+           T *__restrict__ xc) {
+    int32_t J;
+    if (M == M_THR) {
+        const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (k >= nc) return;
+        J = (int32_t)k;
+        xc[J] = T(0);
+        if (mptr[J + 1] - mptr[J] > kLongRow) return;
+    } else if (M == M_WARP) {
+        const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (k >= nlist) return;
+        J = list[k];
+    } else {
+        if (blockIdx.x >= nlist) return;
+        J = list[blockIdx.x];
+    }
+    T acc = T(0), dummy = T(0);
+    for (int32_t j = mptr[J] + slane<M>(); j < mptr[J + 1]; j += sstride<M>()) acc += r[mlist[j]];
+    reduce2<M>(acc, dummy);
+    if (slane<M>() == 0) bc[J] = mu * acc;
 }
 
 // x_i += x^c_{agg(i)}   (Eq. (2.6))
@@ -579,18 +665,28 @@ template <class T>
 static void sweep(IssueCtx &c, int l, const T *b, T *x) {
     const SolveLevel &V = c.h->lv[l];
     const T *w = Prec<T>::w(V);
-    const int nc = (int)V.cs.size() - 1;
     const bool prof = c.profile && l == 0;
     if (prof) LAMG_CUDA(cudaEventRecordWithFlags(c.h->prof_ev[2 * c.prof_idx], c.s, cudaEventRecordExternal));
-    for (int k = 0; k < nc; k++) {
-        const int32_t a = V.cs[k], m = V.cl[k], e = V.cs[k + 1];
-        if (m > a) {
-            k_sweep_thr<T><<<ceil_div(m - a, 256), 256, 0, c.s>>>(a, m - a, V.rp.get(), V.col.get(), w, b, x);
+    const std::vector<int32_t> &seg = V.seg[sizeof(T) == 8 ? 0 : 1];
+    for (size_t q = 0; q < seg.size(); q += 3) {
+        const int k = seg[q];
+        if (seg[q + 2]) {
+            k_sweep_tail<T><<<1, kBlk, 0, c.s>>>(seg[q], seg[q + 1], V.cb_dev.get(), V.rp.get(), V.col.get(), w, b, x);
+            LAMG_CHECK_LAUNCH();
+            continue;
+        }
+        const int32_t t0 = V.cb[4 * k], t1 = V.cb[4 * k + 1], t2 = V.cb[4 * k + 2], t3 = V.cb[4 * k + 3];
+        if (t1 > t0) {
+            k_sweep<M_THR, T><<<ceil_div(t1 - t0, 256), 256, 0, c.s>>>(t0, t1 - t0, V.rp.get(), V.col.get(), w, b, x);
             LAMG_CHECK_LAUNCH();
         }
-        if (e > m) {
-            k_sweep_warp<T><<<ceil_div((int64_t)(e - m) * 32, 256), 256, 0, c.s>>>(m, e - m, V.rp.get(),
-                                                                                   V.col.get(), w, b, x);
+        if (t2 > t1) {
+            k_sweep<M_WARP, T><<<ceil_div((int64_t)(t2 - t1) * 32, 256), 256, 0, c.s>>>(t1, t2 - t1, V.rp.get(),
+                                                                                       V.col.get(), w, b, x);
+            LAMG_CHECK_LAUNCH();
+        }
+        if (t3 > t2) {
+            k_sweep<M_BLK, T><<<t3 - t2, kBlk, 0, c.s>>>(t2, t3 - t2, V.rp.get(), V.col.get(), w, b, x);
             LAMG_CHECK_LAUNCH();
         }
     }
@@ -604,11 +700,35 @@ template <class T>
 static void residual(IssueCtx &c, int l, const T *b, const T *x, T *r) {
     const SolveLevel &V = c.h->lv[l];
     const T *w = Prec<T>::w(V);
-    k_resid_thr<T><<<ceil_div(V.n, 256), 256, 0, c.s>>>(V.n, V.rp.get(), V.col.get(), w, b, x, r);
+    k_resid<M_THR, T><<<ceil_div(V.n, 256), 256, 0, c.s>>>(V.n, nullptr, 0, V.rp.get(), V.col.get(), w, b, x, r);
     LAMG_CHECK_LAUNCH();
-    if (V.nlong) {
-        k_resid_warp<T><<<ceil_div((int64_t)V.nlong * 32, 256), 256, 0, c.s>>>(V.longrows.get(), V.nlong, V.rp.get(),
+    if (V.nw) {
+        k_resid<M_WARP, T><<<ceil_div((int64_t)V.nw * 32, 256), 256, 0, c.s>>>(0, V.wrows.get(), V.nw, V.rp.get(),
                                                                               V.col.get(), w, b, x, r);
+        LAMG_CHECK_LAUNCH();
+    }
+    if (V.nb) {
+        k_resid<M_BLK, T><<<V.nb, kBlk, 0, c.s>>>(0, V.brows.get(), V.nb, V.rp.get(), V.col.get(), w, b, x, r);
+        LAMG_CHECK_LAUNCH();
+    }
+}
+
+template <class T>
+static void restrict_to(IssueCtx &c, int l, const T *r, T *bc, T *xc) {
+    const SolveLevel &F = c.h->lv[l];
+    const int32_t nc = c.h->lv[l + 1].n;
+    const T mu = (T)c.mu;
+    k_restrict<M_THR, T><<<ceil_div(nc, 256), 256, 0, c.s>>>(nc, nullptr, 0, F.mptr.get(), F.mlist.get(), r, mu, bc,
+                                                            xc);
+    LAMG_CHECK_LAUNCH();
+    if (F.nwagg) {
+        k_restrict<M_WARP, T><<<ceil_div((int64_t)F.nwagg * 32, 256), 256, 0, c.s>>>(
+            0, F.wagg.get(), F.nwagg, F.mptr.get(), F.mlist.get(), r, mu, bc, xc);
+        LAMG_CHECK_LAUNCH();
+    }
+    if (F.nbagg) {
+        k_restrict<M_BLK, T><<<F.nbagg, kBlk, 0, c.s>>>(0, F.bagg.get(), F.nbagg, F.mptr.get(), F.mlist.get(), r, mu,
+                                                        bc, xc);
         LAMG_CHECK_LAUNCH();
     }
 }
@@ -646,14 +766,7 @@ static void visit(IssueCtx &c, int l, int theta) {
             k_copy2<T><<<ceil_div(F.n, 256), 256, 0, c.s>>>(F.n, vf.x.get(), xs, vf.r.get(), rs);
             LAMG_CHECK_LAUNCH();
         }
-        k_restrict_thr<T><<<ceil_div(C.n, 256), 256, 0, c.s>>>(C.n, F.mptr.get(), F.mlist.get(), vf.r.get(),
-                                                             (T)c.mu, vc.b.get(), vc.x.get());
-        LAMG_CHECK_LAUNCH();
-        if (F.nlongagg) {
-            k_restrict_warp<T><<<ceil_div((int64_t)F.nlongagg * 32, 256), 256, 0, c.s>>>(
-                F.longagg.get(), F.nlongagg, F.mptr.get(), F.mlist.get(), vf.r.get(), (T)c.mu, vc.b.get());
-            LAMG_CHECK_LAUNCH();
-        }
+        restrict_to<T>(c, l, vf.r.get(), vc.b.get(), vc.x.get());
         if (l + 1 == h->L - 1) {
             coarsest_solve<T>(c, l + 1, vc.b.get(), vc.x.get());
         } else {

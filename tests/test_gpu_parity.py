@@ -33,6 +33,9 @@ def _graph(name):
         "rgg": lambda: W.rgg2d(5000, seed=14),
         "er": lambda: W.erdos_renyi(3000, seed=16),
         "grid64": lambda: W.grid2d(64, 64),
+        # hubs above 4096 entries: block-tier rows in setup and solve
+        "hubs": lambda: W.chung_lu(30000, 2.1, 12.0, seed=7, i0=1.0),
+        "star6k": lambda: W.star(6000),
     }[name]()
 
 
@@ -46,7 +49,7 @@ def _bits(a):
     return np.ascontiguousarray(a).view(np.uint8)
 
 
-SETUP_GRAPHS = ["five", "path", "star", "grid2d", "grid3d", "chung_lu", "rgg", "er", "grid64"]
+SETUP_GRAPHS = ["five", "path", "star", "grid2d", "grid3d", "chung_lu", "rgg", "er", "grid64", "hubs", "star6k"]
 
 
 @pytest.mark.parametrize("gname", SETUP_GRAPHS)
@@ -80,7 +83,7 @@ def test_setup_bit_exact(L, gname):
     s.close()
 
 
-@pytest.mark.parametrize("gname", ["grid2d", "chung_lu", "rgg", "grid3d", "star"])
+@pytest.mark.parametrize("gname", ["grid2d", "chung_lu", "rgg", "grid3d", "star", "hubs"])
 @pytest.mark.parametrize("adaptive", [True, False])
 def test_one_cycle_elementwise(L, gname, adaptive):
     g = _graph(gname)
@@ -101,7 +104,7 @@ def test_one_cycle_elementwise(L, gname, adaptive):
     s.close()
 
 
-@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "five", "path"])
+@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "five", "path", "star6k"])
 def test_solve_fp64_matches_oracle_and_dense(L, gname):
     g = _graph(gname)
     s, h = _both(L, g)
@@ -122,7 +125,7 @@ def test_solve_fp64_matches_oracle_and_dense(L, gname):
     s.close()
 
 
-@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg"])
+@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "hubs"])
 def test_solve_fp32_ir(L, gname):
     g = _graph(gname)
     s, h = _both(L, g)

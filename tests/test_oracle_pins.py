@@ -100,6 +100,16 @@ def test_canon_sum_definition():
     # left-to-right sum would give 1.0.
     t = np.zeros(64); t[0] = 1e16; t[32] = 1.0; t[1] = -1e16
     assert oracle.canon_sum(t) == 0.0
+    # len > 512: 1024 strided partials, 32-wide trees per group of 32, then a
+    # tree over the 32 group results.  p0 = 1e16 (t[1024] = 1 is lost), p1 = -1e16:
+    # group 0 cancels to 0.  p32 = 3 lands in group 1, so the total is 3.0, where
+    # a left-to-right sum would give 1e16 - 1e16 + 1 + 3 = 4.0.
+    t = np.zeros(1100); t[0] = 1e16; t[1024] = 1.0; t[1] = -1e16; t[32] = 3.0
+    assert oracle.canon_sum(t) == 3.0
+    # The 32-lane rule (len <= 512): t[0] = 1e16, t[32] = 3, t[64] = 1, t[1] = -1e16:
+    # lane 0 = (1e16 + 3) + 1 = 1e16 + 4 (ties to even twice), lane 1 = -1e16 -> 4.0.
+    t = np.zeros(512); t[0] = 1e16; t[32] = 3.0; t[64] = 1.0; t[1] = -1e16
+    assert oracle.canon_sum(t) == 4.0
     # integer-valued terms are summed exactly in any order
     t = rng.integers(-1000, 1000, 10_000).astype(np.float64)
     assert oracle.canon_sum(t) == float(t.sum())
@@ -224,9 +234,11 @@ def test_colouring_is_greedy_in_priority_order(gname):
     assert np.all(colour[rows] != colour[g.col])           # proper
     assert nc == colour.max() + 1
     # Jones-Plassmann with smallest-free colours equals the sequential greedy
-    # colouring in decreasing priority (ties to the lower index).
+    # colouring in decreasing priority: degree first, then the hash, ties to the
+    # lower index.
     pri = [_splitmix64_py(key + u) for u in range(g.n)]
-    order = sorted(range(g.n), key=lambda u: (-pri[u], u))
+    deg = np.diff(g.rp)
+    order = sorted(range(g.n), key=lambda u: (-int(deg[u]), -pri[u], u))
     want = -np.ones(g.n, dtype=int)
     for u in order:
         used = {want[v] for v in g.col[g.rp[u]:g.rp[u + 1]] if want[v] >= 0}
