@@ -302,7 +302,7 @@ def main():
         avg = prof_ms / prof_cnt
         achieved = prof_bytes / (avg / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "finest-level Gauss-Seidel sweep (all colours)",
+                "traffic": None, "kernel": "cycle engine (one launch = one refinement step: ir_inner FP32 cycles + FP64 residual)",
                 "bytes_per_launch": prof_bytes, "avg_ms": avg, "launches": prof_cnt,
                 "peak_kind": f"{peak_kind} hbm_gbs"}
 

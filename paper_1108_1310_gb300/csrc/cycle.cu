@@ -1,0 +1,691 @@
+// cycle.cu -- the cycle engine: one persistent cooperative kernel per cycle
+// (or per FP32-in-FP64 refinement step) that interprets a program of ops
+// built on the host by replaying the cycle schedule of Sec. 4.2 / Fig. 4.2
+// (Livne & Brandt, arXiv 1108.1310).
+//
+// LAMG's cycles visit the coarse levels many times (fractional cycle index
+// up to 2, Eq. (4.1)), and multicolour Gauss-Seidel needs one dependent phase
+// per colour, so a cycle is thousands of short dependent phases.  Launching
+// them as separate kernels makes the cycle latency-bound.  Here every phase is
+// an op executed by all blocks between grid barriers; ops of small levels (and
+// runs of tiny colours) are flagged single-block and run by block 0 alone with
+// __syncthreads between them, costing one grid barrier per run.
+//
+// The grid barrier spins with a bounded count; when it runs out the kernel
+// sets an error word and every block returns (the host reports
+// LAMG_ERR_TIMEOUT).  The launch is cooperative, so all blocks are resident.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "solve_rows.cuh"
+
+namespace lamg {
+
+constexpr int kEngThreads = 1024;
+constexpr long long kMaxSpins = 1ll << 23;  // about a second of polling
+
+template <class T>
+struct MKLevel {
+    int32_t n, nc;
+    const int32_t *rp, *col;
+    const T *w;
+    const int32_t *cb;
+    const int32_t *wrows, *brows;
+    int32_t nw, nb;
+    const int32_t *pagg, *mptr, *mlist, *wagg, *bagg;
+    int32_t nwagg, nbagg;
+    T *x, *b, *r, *xs0, *xs1, *rs0, *rs1;
+    const double *minv;
+};
+
+enum : int32_t {
+    OP_SWEEP = 0,     // level, colour a (all blocks)
+    OP_SWEEP_RUN,     // level, colours a..b-1 (single block, __syncthreads between colours)
+    OP_RESID,         // r = b - A x; a >= 0: also save x, r into slot a (recombination)
+    OP_RESTRICT,      // b^c = mu P^T r, x^c = 0
+    OP_ZERO,          // x = 0 (coarsest solved by sweeps)
+    OP_COARSE,        // x = M^-1 b (dense coarsest, FP64 arithmetic)
+    OP_PROLONG,       // x += P x^c
+    OP_RECOMB_DOTS,   // partial dot products, theta = a
+    OP_RECOMB_APPLY,  // alpha from the partials, y = x + sum alpha_i (x_i - x)
+    OP_MEAN_PART,     // partial sums of x (cycle precision)
+    OP_MEAN_APPLY,    // x -= mean
+    OP_IR_PREP,       // b32 = (float) r64, x32 = 0
+    OP_IR_UPDATE,     // x64 += (double) x32
+    OP_MEAN64_PART,   // partial sums of x64
+    OP_MEAN64_APPLY,  // x64 -= mean
+    OP_RES64,         // r64 = b64 - A x64 (FP64) and partial sums of r64^2
+    OP_NORM64_FIN,    // out[0] = sum of the partials
+    OP_SWEEP_SMEM,    // level, a = sweeps: whole sweeps from shared memory (single block)
+};
+
+constexpr int kEngSmem = 200 * 1024;  // dynamic shared memory of the engine block
+
+// bytes the shared-memory sweep needs for a level: rp, col, w, x, b, colour bounds
+template <class T>
+__host__ __device__ __forceinline__ int64_t smem_bytes(int64_t n, int64_t nnz, int64_t ncol) {
+    auto al = [](int64_t b) { return (b + 15) & ~int64_t(15); };
+    return al(4 * (n + 1)) + al(4 * nnz) + al((int64_t)sizeof(T) * nnz) + 2 * al((int64_t)sizeof(T) * n) +
+           al(16 * ncol);
+}
+
+struct Op {
+    int32_t type, level, a, b, sb;
+};
+
+// colour count of a level is carried in the op (b) for the shared-memory sweep
+
+template <class T>
+struct EngineArgs {
+    const Op *prog;
+    int32_t begin, end;
+    const MKLevel<T> *lv;
+    MKLevel<double> L0;     // FP64 finest level (outer refinement / residual)
+    T mu;
+    double *part;           // gridDim * 8 partial sums
+    double *alpha;          // 2 per level
+    double *out;            // results
+    unsigned int *bar;      // barrier: count, generation
+    int32_t *err;
+    unsigned long long *optime;  // optional per (level, op, single-block) time and count
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier (bounded spin)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err) {
+    __shared__ int bad;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bad = 0;
+        volatile unsigned int *vgen = bar + 1;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if ((++spins & 63) == 0) {
+                    if (*(volatile int32_t *)err) { bad = 1; break; }
+                    if (spins > kMaxSpins) { atomicExch(err, 1); bad = 1; break; }
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return bad == 0;
+}
+
+// ---------------------------------------------------------------------------
+// ops; (bid, nb) = this block's index among the nb blocks executing the op
+// ---------------------------------------------------------------------------
+
+template <class T>
+__device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid, int nb) {
+    const int32_t t0 = L.cb[4 * c], t1 = L.cb[4 * c + 1], t2 = L.cb[4 * c + 2], t3 = L.cb[4 * c + 3];
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    for (int64_t i = t0 + tid; i < t1; i += nthr) gs_row<M_THR, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
+    const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    for (int64_t i = t1 + wid; i < t2; i += nwarp) gs_row<M_WARP, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
+    for (int64_t i = t2 + bid; i < t3; i += nb) gs_row<M_BLK, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
+}
+
+template <class T>
+__device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const T *x, T *r, T *xs, T *rs, int bid,
+                                         int nb) {
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    for (int64_t i = tid; i < L.n; i += nthr) {
+        const int32_t ii = (int32_t)i;
+        if (L.rp[ii + 1] - L.rp[ii] > kLongRow) continue;
+        resid_row<M_THR, T>(ii, L.rp, L.col, L.w, b, x, r);
+        if (xs) { xs[ii] = x[ii]; rs[ii] = r[ii]; }
+    }
+    const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    for (int64_t k = wid; k < L.nw; k += nwarp) {
+        const int32_t ii = L.wrows[k];
+        resid_row<M_WARP, T>(ii, L.rp, L.col, L.w, b, x, r);
+        if (xs && (threadIdx.x & 31) == 0) { xs[ii] = x[ii]; rs[ii] = r[ii]; }
+    }
+    for (int64_t k = bid; k < L.nb; k += nb) {
+        const int32_t ii = L.brows[k];
+        resid_row<M_BLK, T>(ii, L.rp, L.col, L.w, b, x, r);
+        if (xs && threadIdx.x == 0) { xs[ii] = x[ii]; rs[ii] = r[ii]; }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void restrict_op(const MKLevel<T> &F, const MKLevel<T> &C, T mu, int bid, int nb) {
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    for (int64_t J = tid; J < C.n; J += nthr) {
+        const int32_t jj = (int32_t)J;
+        C.x[jj] = T(0);
+        if (F.mptr[jj + 1] - F.mptr[jj] > kLongRow) continue;
+        restrict_row<M_THR, T>(jj, F.mptr, F.mlist, F.r, mu, C.b);
+    }
+    const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    for (int64_t k = wid; k < F.nwagg; k += nwarp) restrict_row<M_WARP, T>(F.wagg[k], F.mptr, F.mlist, F.r, mu, C.b);
+    for (int64_t k = bid; k < F.nbagg; k += nb) restrict_row<M_BLK, T>(F.bagg[k], F.mptr, F.mlist, F.r, mu, C.b);
+}
+
+template <class T>
+__device__ __forceinline__ double block_sum_d(double v) {
+    __shared__ double sh[32];
+    v = warp_allsum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; k++) t += sh[k];
+    __syncthreads();
+    return t;  // in every thread
+}
+
+// sum of the nb block partials at slot k (same order in every block)
+__device__ __forceinline__ double sum_partials(const double *part, int nb, int k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * 8 + k];
+    return block_sum_d<double>(v);
+}
+
+template <class T>
+__device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const MKLevel<T> &L = a.lv[op.level];
+    switch (op.type) {
+        case OP_SWEEP:
+            sweep_colour<T>(L, op.a, bid, nb);
+            break;
+        case OP_SWEEP_RUN:
+            for (int c = op.a; c < op.b; c++) {
+                sweep_colour<T>(L, c, 0, 1);
+                __syncthreads();
+            }
+            break;
+        case OP_RESID: {
+            T *xs = op.a == 0 ? L.xs0 : (op.a == 1 ? L.xs1 : nullptr);
+            T *rs = op.a == 0 ? L.rs0 : (op.a == 1 ? L.rs1 : nullptr);
+            residual<T>(L, L.b, L.x, L.r, xs, rs, bid, nb);
+            break;
+        }
+        case OP_RESTRICT:
+            restrict_op<T>(L, a.lv[op.level + 1], a.mu, bid, nb);
+            break;
+        case OP_ZERO:
+            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] = T(0);
+            break;
+        case OP_COARSE: {
+            const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+            const int lane = threadIdx.x & 31;
+            for (int64_t i = wid; i < L.n; i += nwarp) {
+                double acc = 0.0;
+                for (int32_t j = lane; j < L.n; j += 32) acc += L.minv[i * L.n + j] * (double)L.b[j];
+                acc = warp_allsum(acc);
+                if (lane == 0) L.x[i] = (T)acc;
+            }
+            break;
+        }
+        case OP_PROLONG: {
+            const MKLevel<T> &C = a.lv[op.level + 1];
+            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] += C.x[L.pagg[i]];
+            break;
+        }
+        case OP_RECOMB_DOTS: {
+            double g00 = 0, g01 = 0, g11 = 0, h0 = 0, h1 = 0;
+            for (int64_t i = tid; i < L.n; i += nthr) {
+                const double ri = (double)L.r[i];
+                const double d0 = ri - (double)L.rs0[i];
+                g00 += d0 * d0;
+                h0 += ri * d0;
+                if (op.a == 2) {
+                    const double d1 = ri - (double)L.rs1[i];
+                    g01 += d0 * d1;
+                    g11 += d1 * d1;
+                    h1 += ri * d1;
+                }
+            }
+            const double v[5] = {g00, g01, g11, h0, h1};
+            for (int k = 0; k < 5; k++) {
+                const double t = block_sum_d<double>(v[k]);
+                if (threadIdx.x == 0) a.part[(int64_t)bid * 8 + k] = t;
+            }
+            break;
+        }
+        case OP_RECOMB_APPLY: {
+            // Eq. (3.13): alpha minimises ||b - A y||_2; normal equations of size theta
+            const double G00 = sum_partials(a.part, nb, 0), G01 = sum_partials(a.part, nb, 1);
+            const double G11 = sum_partials(a.part, nb, 2), h0 = sum_partials(a.part, nb, 3);
+            const double h1 = sum_partials(a.part, nb, 4);
+            double a0 = 0.0, a1 = 0.0;
+            if (op.a == 1) {
+                if (G00 > 0.0) a0 = h0 / G00;
+            } else {
+                const double det = G00 * G11 - G01 * G01;
+                if (det > 1e-14 * G00 * G11 && det > 0.0) {
+                    a0 = (h0 * G11 - G01 * h1) / det;
+                    a1 = (G00 * h1 - G01 * h0) / det;
+                } else if (G00 > 0.0) {
+                    a0 = h0 / G00;
+                }
+            }
+            for (int64_t i = tid; i < L.n; i += nthr) {
+                const double xi = (double)L.x[i];
+                double y = xi + a0 * ((double)L.xs0[i] - xi);
+                if (op.a == 2) y += a1 * ((double)L.xs1[i] - xi);
+                L.x[i] = (T)y;
+            }
+            break;
+        }
+        case OP_MEAN_PART: {
+            double v = 0.0;
+            for (int64_t i = tid; i < L.n; i += nthr) v += (double)L.x[i];
+            v = block_sum_d<double>(v);
+            if (threadIdx.x == 0) a.part[(int64_t)bid * 8] = v;
+            break;
+        }
+        case OP_MEAN_APPLY: {
+            const double m = sum_partials(a.part, nb, 0) / (double)L.n;
+            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] = (T)((double)L.x[i] - m);
+            break;
+        }
+        case OP_IR_PREP:
+            for (int64_t i = tid; i < L.n; i += nthr) {
+                L.b[i] = (T)a.L0.r[i];
+                L.x[i] = T(0);
+            }
+            break;
+        case OP_IR_UPDATE:
+            for (int64_t i = tid; i < L.n; i += nthr) a.L0.x[i] += (double)L.x[i];
+            break;
+        case OP_MEAN64_PART: {
+            double v = 0.0;
+            for (int64_t i = tid; i < a.L0.n; i += nthr) v += a.L0.x[i];
+            v = block_sum_d<double>(v);
+            if (threadIdx.x == 0) a.part[(int64_t)bid * 8] = v;
+            break;
+        }
+        case OP_MEAN64_APPLY: {
+            const double m = sum_partials(a.part, nb, 0) / (double)a.L0.n;
+            for (int64_t i = tid; i < a.L0.n; i += nthr) a.L0.x[i] -= m;
+            break;
+        }
+        case OP_RES64: {
+            residual<double>(a.L0, a.L0.b, a.L0.x, a.L0.r, nullptr, nullptr, bid, nb);
+            // the residual entries this block wrote are not known here; sum squares after a barrier
+            break;
+        }
+        case OP_NORM64_FIN: {
+            double v = 0.0;
+            for (int64_t i = tid; i < a.L0.n; i += nthr) {
+                const double t = a.L0.r[i];
+                v += t * t;
+            }
+            v = block_sum_d<double>(v);
+            if (threadIdx.x == 0) a.part[(int64_t)bid * 8 + 5] = v;
+            break;
+        }
+        case OP_SWEEP_SMEM: {
+            // single block: stage the level, run a sweeps of all b colours, write x back
+            extern __shared__ __align__(16) unsigned char smem[];
+            const int32_t n = L.n, nnz = L.rp[n], nc = op.b;
+            auto al = [](int64_t v) { return (v + 15) & ~int64_t(15); };
+            unsigned char *p = smem;
+            int32_t *srp = (int32_t *)p; p += al(4 * (int64_t)(n + 1));
+            int32_t *scol = (int32_t *)p; p += al(4 * (int64_t)nnz);
+            T *sw = (T *)p; p += al((int64_t)sizeof(T) * nnz);
+            T *sx = (T *)p; p += al((int64_t)sizeof(T) * n);
+            T *sbv = (T *)p; p += al((int64_t)sizeof(T) * n);
+            int32_t *scb = (int32_t *)p;
+            for (int32_t k = threadIdx.x; k <= n; k += blockDim.x) srp[k] = L.rp[k];
+            for (int32_t k = threadIdx.x; k < nnz; k += blockDim.x) { scol[k] = L.col[k]; sw[k] = L.w[k]; }
+            for (int32_t k = threadIdx.x; k < n; k += blockDim.x) { sx[k] = L.x[k]; sbv[k] = L.b[k]; }
+            for (int32_t k = threadIdx.x; k < 4 * nc; k += blockDim.x) scb[k] = L.cb[k];
+            __syncthreads();
+            const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+            for (int rep = 0; rep < op.a; rep++)
+                for (int32_t c = 0; c < nc; c++) {
+                    const int32_t t0 = scb[4 * c], t1 = scb[4 * c + 1], t2 = scb[4 * c + 2], t3 = scb[4 * c + 3];
+                    for (int32_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) gs_row<M_THR, T>(i, srp, scol, sw, sbv, sx);
+                    for (int32_t i = t1 + warp; i < t2; i += nwarp) gs_row<M_WARP, T>(i, srp, scol, sw, sbv, sx);
+                    for (int32_t i = t2; i < t3; i++) gs_row<M_BLK, T>(i, srp, scol, sw, sbv, sx);
+                    __syncthreads();
+                }
+            for (int32_t k = threadIdx.x; k < n; k += blockDim.x) L.x[k] = sx[k];
+            break;
+        }
+        default:
+            break;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
+    int32_t pc = a.begin;
+    while (pc < a.end) {
+        const Op op = a.prog[pc];
+        const bool timed = a.optime && blockIdx.x == 0 && threadIdx.x == 0;
+        const unsigned long long t0 = timed ? gtimer() : 0ull;
+        if (op.sb) {
+            int32_t q = pc;
+            if (blockIdx.x == 0) {
+                while (q < a.end && a.prog[q].sb) {
+                    exec_op<T>(a, a.prog[q], 0, 1);
+                    __syncthreads();
+                    q++;
+                }
+            } else {
+                while (q < a.end && a.prog[q].sb) q++;
+            }
+            pc = q;
+        } else {
+            exec_op<T>(a, op, blockIdx.x, gridDim.x);
+            pc++;
+        }
+        if (!grid_sync(a.bar, a.err)) return;
+        if (timed) {
+            const int key = (op.level * 32 + op.type) * 2 + (op.sb ? 1 : 0);
+            a.optime[2 * key] += gtimer() - t0;
+            a.optime[2 * key + 1] += 1;
+        }
+    }
+}
+
+// ||r64||^2 from the per-block partials written by OP_NORM64_FIN
+__global__ void k_engine_norm(const double *part, int nb, double *out) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * 8 + 5];
+    v = block_sum_d<double>(v);
+    if (threadIdx.x == 0) out[0] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Program builder (host): replays the cycle schedule of the oracle
+// ---------------------------------------------------------------------------
+
+struct Builder {
+    lamg_ctx *h;
+    int prec;            // 0 = FP64, 1 = FP32
+    int adaptive;
+    std::vector<Op> prog;
+    std::vector<int32_t> visits;
+
+    // a level runs on block 0 alone when it is small and its sweep fits in shared memory
+    bool level_sb(int l) const {
+        const SolveLevel &V = h->lv[l];
+        const int nc = (int)V.cb.size() / 4;
+        const int64_t need = prec == 0 ? smem_bytes<double>(V.n, V.nnz, nc) : smem_bytes<float>(V.n, V.nnz, nc);
+        return V.nnz + V.n <= kSBWork && need <= kEngSmem;
+    }
+    void emit(int type, int level, int a, int b, bool sb) { prog.push_back(Op{type, level, a, b, sb ? 1 : 0}); }
+
+    // `count` consecutive sweeps of level l
+    void sweeps(int l, int count) {
+        if (count <= 0) return;
+        const SolveLevel &V = h->lv[l];
+        const int nc = (int)V.cb.size() / 4;
+        if (level_sb(l)) {
+            const int64_t need = prec == 0 ? smem_bytes<double>(V.n, V.nnz, nc) : smem_bytes<float>(V.n, V.nnz, nc);
+            if (need <= kEngSmem) {
+                emit(OP_SWEEP_SMEM, l, count, nc, true);
+                return;
+            }
+        }
+        for (int k = 0; k < count; k++) sweep(l);
+    }
+    void sweep(int l) {
+        const SolveLevel &V = h->lv[l];
+        const bool sb = level_sb(l);
+        const int nc = (int)V.cb.size() / 4;
+        if (sb) {
+            emit(OP_SWEEP_RUN, l, 0, nc, true);
+            return;
+        }
+        const std::vector<int32_t> &seg = V.seg[prec];
+        for (size_t q = 0; q < seg.size(); q += 3) {
+            if (seg[q + 2]) emit(OP_SWEEP_RUN, l, seg[q], seg[q + 1], true);
+            else emit(OP_SWEEP, l, seg[q], seg[q] + 1, false);
+        }
+    }
+    void coarsest(int l) {
+        const SolveLevel &V = h->lv[l];
+        if (V.dense) {
+            emit(OP_COARSE, l, 0, 0, V.n <= 64);
+        } else {
+            emit(OP_ZERO, l, 0, 0, level_sb(l));
+            sweeps(l, h->opt.coarse_sweeps);
+        }
+    }
+    void visit(int l, int theta) {
+        const bool recomb = adaptive && l >= 1;
+        const bool sb = level_sb(l);
+        for (int i = 0; i < theta; i++) {
+            sweeps(l, h->opt.nu1);
+            emit(OP_RESID, l, recomb ? i : -1, 0, sb);
+            emit(OP_RESTRICT, l, 0, 0, sb);
+            if (l + 1 == h->L - 1) {
+                coarsest(l + 1);
+            } else {
+                const int32_t k = visits[l]++;
+                const double g = h->sl[l].gamma_l;
+                int th = (int)(std::ceil((double)(k + 1) * g) - std::ceil((double)k * g));
+                th = th < 1 ? 1 : (th > 2 ? 2 : th);
+                visit(l + 1, th);
+            }
+            emit(OP_PROLONG, l, 0, 0, sb);
+            sweeps(l, h->opt.nu2);
+        }
+        if (recomb) {
+            emit(OP_RESID, l, -1, 0, sb);
+            emit(OP_RECOMB_DOTS, l, theta, 0, sb);
+            emit(OP_RECOMB_APPLY, l, theta, 0, sb);
+        }
+    }
+    void cycle() {
+        visits.assign(h->L, 0);
+        if (h->L == 1) coarsest(0);
+        else visit(0, 1);
+        const bool sb = level_sb(0);
+        emit(OP_MEAN_PART, 0, 0, 0, sb);
+        emit(OP_MEAN_APPLY, 0, 0, 0, sb);
+    }
+};
+
+// Build (and cache) the program of one step.
+//   kind 0: FP64 cycle + mean + FP64 residual norm (solve step)
+//   kind 1: FP32 refinement step: prep, ir_inner FP32 cycles, update, mean, FP64 residual norm
+//   kind 2: one FP64 cycle + mean only
+void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out) {
+    Builder B{h, kind == 1 ? 1 : 0, adaptive, {}, {}};
+    if (kind == 1) {
+        B.emit(OP_IR_PREP, 0, 0, 0, false);
+        for (int k = 0; k < std::max(1, h->opt.ir_inner); k++) B.cycle();
+        B.emit(OP_IR_UPDATE, 0, 0, 0, false);
+        B.emit(OP_MEAN64_PART, 0, 0, 0, false);
+        B.emit(OP_MEAN64_APPLY, 0, 0, 0, false);
+    } else {
+        B.cycle();
+    }
+    if (kind != 2) {
+        B.emit(OP_RES64, 0, 0, 0, false);
+        B.emit(OP_NORM64_FIN, 0, 0, 0, false);
+    }
+    if (const char *e = std::getenv("LAMG_ENGINE_STATS"); e && e[0] == '1') {
+        int64_t grid_ops = 0, runs = 0, sb_ops = 0;
+        for (size_t i = 0; i < B.prog.size(); i++) {
+            if (B.prog[i].sb) {
+                sb_ops++;
+                if (i == 0 || !B.prog[i - 1].sb) runs++;
+            } else {
+                grid_ops++;
+            }
+        }
+        std::fprintf(stderr, "lamg-engine kind %d: %zu ops, %lld grid ops, %lld single-block runs (%lld ops), %lld barriers\n",
+                     kind, B.prog.size(), (long long)grid_ops, (long long)runs, (long long)sb_ops,
+                     (long long)(grid_ops + runs));
+    }
+    out.resize(B.prog.size() * 5);
+    for (size_t i = 0; i < B.prog.size(); i++) {
+        out[5 * i] = B.prog[i].type;
+        out[5 * i + 1] = B.prog[i].level;
+        out[5 * i + 2] = B.prog[i].a;
+        out[5 * i + 3] = B.prog[i].b;
+        out[5 * i + 4] = B.prog[i].sb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Runner
+// ---------------------------------------------------------------------------
+
+template <class T>
+static MKLevel<T> describe(lamg_ctx *h, int l, LevelVecs<T> &v, const T *w) {
+    const SolveLevel &V = h->lv[l];
+    MKLevel<T> d{};
+    d.n = V.n;
+    d.nc = (l + 1 < h->L) ? h->lv[l + 1].n : 0;
+    d.rp = V.rp.get();
+    d.col = V.col.get();
+    d.w = w;
+    d.cb = V.cb_dev.get();
+    d.wrows = V.wrows.get();
+    d.brows = V.brows.get();
+    d.nw = V.nw;
+    d.nb = V.nb;
+    d.pagg = V.pagg.get();
+    d.mptr = V.mptr.get();
+    d.mlist = V.mlist.get();
+    d.wagg = V.wagg.get();
+    d.bagg = V.bagg.get();
+    d.nwagg = V.nwagg;
+    d.nbagg = V.nbagg;
+    d.x = v.x.get();
+    d.b = v.b.get();
+    d.r = v.r.get();
+    d.xs0 = v.xs0.get();
+    d.xs1 = v.xs1.get();
+    d.rs0 = v.rs0.get();
+    d.rs1 = v.rs1.get();
+    d.minv = V.minv.get();
+    return d;
+}
+
+void engine_prepare(lamg_ctx *h) {
+    if (h->eng_lv64.get()) return;
+    std::vector<MKLevel<double>> d64(h->L);
+    std::vector<MKLevel<float>> d32(h->L);
+    for (int l = 0; l < h->L; l++) {
+        d64[l] = describe<double>(h, l, h->v64[l], h->lv[l].w64.get());
+        d32[l] = describe<float>(h, l, h->v32[l], h->lv[l].w32.get());
+    }
+    h->eng_lv64.alloc(sizeof(MKLevel<double>) * h->L);
+    h->eng_lv32.alloc(sizeof(MKLevel<float>) * h->L);
+    LAMG_CUDA(cudaMemcpy(h->eng_lv64.get(), d64.data(), sizeof(MKLevel<double>) * h->L, cudaMemcpyHostToDevice));
+    LAMG_CUDA(cudaMemcpy(h->eng_lv32.get(), d32.data(), sizeof(MKLevel<float>) * h->L, cudaMemcpyHostToDevice));
+    int dev = 0, sms = 0, per = 0;
+    LAMG_CUDA(cudaGetDevice(&dev));
+    LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int p64 = 0, p32 = 0;
+    LAMG_CUDA(cudaFuncSetAttribute(k_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEngSmem));
+    LAMG_CUDA(cudaFuncSetAttribute(k_engine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEngSmem));
+    LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, k_engine<double>, kEngThreads, kEngSmem));
+    LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, k_engine<float>, kEngThreads, kEngSmem));
+    per = std::min(std::min(p64, p32), 1);
+    LAMG_REQUIRE(per >= 1, LAMG_ERR_CUDA, "cycle engine cannot be resident");
+    h->eng_grid = sms * per;
+    h->eng_part.alloc((size_t)h->eng_grid * 8);
+    h->eng_bar.alloc(2);
+    h->eng_err.alloc(1);
+    LAMG_CUDA(cudaMemset(h->eng_bar.get(), 0, 2 * sizeof(unsigned int)));
+    LAMG_CUDA(cudaMemset(h->eng_err.get(), 0, sizeof(int32_t)));
+    if (const char *e = std::getenv("LAMG_ENGINE_PROFILE"); e && e[0] == '1') {
+        h->eng_optime.alloc(128 * 32 * 2 * 2);
+        LAMG_CUDA(cudaMemset(h->eng_optime.get(), 0, h->eng_optime.bytes()));
+    }
+}
+
+// Development aid (LAMG_ENGINE_PROFILE=1): print the accumulated op times.
+void engine_report(lamg_ctx *h) {
+    if (!h->eng_optime.get()) return;
+    std::vector<unsigned long long> t(h->eng_optime.n);
+    LAMG_CUDA(cudaMemcpy(t.data(), h->eng_optime.get(), h->eng_optime.bytes(), cudaMemcpyDeviceToHost));
+    static const char *names[] = {"sweep", "sweep_run", "resid", "restrict", "zero", "coarse", "prolong",
+                                  "recomb_dots", "recomb_apply", "mean_part", "mean_apply", "ir_prep",
+                                  "ir_update", "mean64_part", "mean64_apply", "res64", "norm64", "sweep_smem"};
+    for (int l = 0; l < 128; l++)
+        for (int ty = 0; ty < 18; ty++)
+            for (int sb = 0; sb < 2; sb++) {
+                const int key = (l * 32 + ty) * 2 + sb;
+                if (t[2 * key + 1])
+                    std::fprintf(stderr, "lamg-optime level %2d %-13s %s n=%8llu total %10.3f ms  per %8.2f us\n", l,
+                                 names[ty], sb ? "sb  " : "grid", t[2 * key + 1], t[2 * key] * 1e-6,
+                                 t[2 * key] * 1e-3 / t[2 * key + 1]);
+            }
+    LAMG_CUDA(cudaMemset(h->eng_optime.get(), 0, h->eng_optime.bytes()));
+}
+
+// Run program `kind` once on stream s; returns after the launch is queued.
+void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s) {
+    auto &slot = h->eng_prog[kind * 2 + (adaptive ? 1 : 0)];
+    int32_t &len = h->eng_len[kind * 2 + (adaptive ? 1 : 0)];
+    if (!slot.get()) {
+        std::vector<int32_t> prog;
+        build_program(h, kind, adaptive, prog);
+        slot.alloc(prog.size());
+        LAMG_CUDA(cudaMemcpy(slot.get(), prog.data(), sizeof(int32_t) * prog.size(), cudaMemcpyHostToDevice));
+        len = (int32_t)(prog.size() / 5);
+    }
+    MKLevel<double> L0 = describe<double>(h, 0, h->v64[0], h->lv[0].w64.get());
+    L0.r = h->r64.get();
+    const dim3 grid(h->eng_grid), block(kEngThreads);
+    if (kind == 1) {
+        EngineArgs<float> a{(const Op *)slot.get(), 0, len, (const MKLevel<float> *)h->eng_lv32.get(), L0,
+                            (float)mu, h->eng_part.get(), nullptr, h->scratch.get(), h->eng_bar.get(),
+                            h->eng_err.get(), h->eng_optime.get()};
+        void *args[] = {&a};
+        LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<float>, grid, block, args, kEngSmem, s));
+    } else {
+        EngineArgs<double> a{(const Op *)slot.get(), 0, len, (const MKLevel<double> *)h->eng_lv64.get(), L0, mu,
+                             h->eng_part.get(), nullptr, h->scratch.get(), h->eng_bar.get(), h->eng_err.get(),
+                             h->eng_optime.get()};
+        void *args[] = {&a};
+        LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<double>, grid, block, args, kEngSmem, s));
+    }
+    note_launch();
+    if (kind != 2) {
+        k_engine_norm<<<1, 256, 0, s>>>(h->eng_part.get(), h->eng_grid, h->scratch.get());
+        LAMG_CHECK_LAUNCH();
+    }
+}
+
+// Error word of the last runs (bounded barrier timeout); clears it.
+bool engine_failed(lamg_ctx *h, cudaStream_t s) {
+    int32_t e = 0;
+    LAMG_CUDA(cudaMemcpyAsync(&e, h->eng_err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LAMG_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+        LAMG_CUDA(cudaMemsetAsync(h->eng_err.get(), 0, sizeof(int32_t), s));
+        LAMG_CUDA(cudaMemsetAsync(h->eng_bar.get(), 0, 2 * sizeof(unsigned int), s));
+    }
+    return e != 0;
+}
+
+int64_t engine_program_ops(lamg_ctx *h, int kind, int adaptive) {
+    return h->eng_len[kind * 2 + (adaptive ? 1 : 0)];
+}
+
+}  // namespace lamg

@@ -167,18 +167,21 @@ struct lamg_ctx {
     lamg::DBuf<double> xnat, bnat;  // level-1 vectors for host-array solves
     lamg::DBuf<double> r64;         // FP64 outer residual (permuted)
     double *host_pinned = nullptr;  // pinned readback slots
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t g64 = nullptr, g32 = nullptr;   // captured cycles
-    int32_t g64_adaptive = -1, g32_adaptive = -1;
-    int64_t g64_kernels = 0, g32_kernels = 0, g64p_kernels = 0, g32p_kernels = 0;
-    // profiling of the finest-level sweeps
+    // cycle engine: level descriptors, programs (FP64 step, FP32-IR step, one cycle) x adaptive
+    lamg::DBuf<char> eng_lv64, eng_lv32;
+    lamg::DBuf<int32_t> eng_prog[6];
+    int32_t eng_len[6] = {0, 0, 0, 0, 0, 0};
+    lamg::DBuf<double> eng_part;
+    lamg::DBuf<unsigned int> eng_bar;
+    lamg::DBuf<int32_t> eng_err;
+    lamg::DBuf<unsigned long long> eng_optime;
+    int32_t eng_grid = 0;
+    // profiling of the engine launches
     int32_t prof_on = 0;
     std::vector<cudaEvent_t> prof_ev;
     double prof_ms = 0.0;
     int64_t prof_count = 0;
     int64_t prof_bytes = 0;
-    cudaGraphExec_t g64p = nullptr, g32p = nullptr;  // profiled variants
-    int32_t g64p_adaptive = -1, g32p_adaptive = -1;
     lamg_stats last{};
 };
 
@@ -189,6 +192,16 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
                      const void *w, int32_t w_is_fp32, cudaStream_t s);
 void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
                     int32_t w_is_fp32, cudaStream_t s);
+
+// single-block threshold of the cycle engine (n + nnz of a level)
+constexpr int64_t kSBWork = 16384;
+
+// cycle.cu
+void engine_prepare(lamg_ctx *h);
+void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s);
+bool engine_failed(lamg_ctx *h, cudaStream_t s);
+void engine_report(lamg_ctx *h);
+void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out);
 
 // solve.cu
 void build_solve_layout(lamg_ctx *h, cudaStream_t s);
