@@ -179,6 +179,35 @@ lamg_status lamg_level_copy(lamg_handle h, int32_t level, int32_t field, void *h
 lamg_status lamg_cycle(lamg_handle h, const double *b, double *x, int32_t adaptive,
                        lamg_stream stream);
 
+/* ---- allocation-free cycle (a library addition: the paper has no counterpart) ----
+ *
+ * Does what lamg_cycle does -- one cycle plus the mean subtraction on device
+ * x, FP64 arithmetic, same results -- but allocates no device or host memory.
+ * It is for callers that cannot allocate inside their loop: a Krylov solver
+ * applying one cycle per iteration as a preconditioner under a fixed memory
+ * budget, or a serving loop where an allocation could stall on the device or
+ * fail once the memory is committed elsewhere.
+ *
+ *  - The handle must already own its solve buffers and the one-cycle program
+ *    for this `adaptive` value: call lamg_cycle once with the same `adaptive`
+ *    first (lamg_solve creates the buffers but not that program).  An
+ *    unprepared handle gets LAMG_ERR_ARG and nothing runs.
+ *  - The run's scratch (one row of 8 partial sums per engine block, the grid
+ *    barrier's two words and an error word) is a fixed 33,024-byte array in
+ *    the library's device image, one per device, with room for at most 512
+ *    engine blocks; a device whose engine grid is larger (SM count x resident
+ *    blocks per SM) is rejected with LAMG_ERR_ARG.  The first call on a device
+ *    looks the array's address up, with that device current; make this first
+ *    call before any stream capture begins.  Every call clears the barrier and
+ *    error words before its launch.
+ *  - The array is shared by every handle on the device: calls whose GPU work
+ *    overlaps (issued on different streams or from different threads) race on
+ *    it and on the handle, and give wrong results.  Serialise them.
+ *  - Synchronises `stream` before returning; LAMG_ERR_TIMEOUT as for lamg_cycle.
+ */
+lamg_status lamg_cycle_noalloc(lamg_handle h, const double *b, double *x, int32_t adaptive,
+                               lamg_stream stream);
+
 /* Average device time, in milliseconds, and count of the finest-level
  * relaxation sweep launches timed with CUDA events while profiling is on
  * (enable = 1 resets the counters; 0 stops recording). */

@@ -284,6 +284,13 @@ lamg_status lamg_cycle(lamg_handle h, const double *b, double *x, int32_t adapti
     });
 }
 
+lamg_status lamg_cycle_noalloc(lamg_handle h, const double *b, double *x, int32_t adaptive, lamg_stream stream) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && b && x, LAMG_ERR_ARG, "NULL argument");
+        cycle_device_noalloc(h, b, x, adaptive, (cudaStream_t)stream);
+    });
+}
+
 lamg_status lamg_profile(lamg_handle h, int32_t enable, double *avg_ms, int64_t *count, int64_t *bytes) {
     return guarded([&] {
         LAMG_REQUIRE(h, LAMG_ERR_ARG, "NULL handle");

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "solve_rows.cuh"
 
@@ -682,6 +683,72 @@ bool engine_failed(lamg_ctx *h, cudaStream_t s) {
         LAMG_CUDA(cudaMemsetAsync(h->eng_bar.get(), 0, 2 * sizeof(unsigned int), s));
     }
     return e != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free one-cycle run (lamg_cycle_noalloc)
+// ---------------------------------------------------------------------------
+// The engine's per-launch scratch -- a row of 8 partial sums per block, the two
+// grid-barrier words and the error word -- lives in this fixed array of the
+// library's device image instead of the handle's buffers, so a run allocates
+// nothing.  Layout: part[kNoAllocMaxBlocks * 8] doubles, then bar[2] (unsigned)
+// at +0, err (int32) at +16 of the 256-byte tail.  The partial sums are always
+// written before they are read; the barrier and error words must start at zero
+// and are cleared by every call.  One array per device, shared by all handles.
+constexpr int kNoAllocMaxBlocks = 512;
+constexpr size_t kNoAllocPartBytes = (size_t)kNoAllocMaxBlocks * 8 * sizeof(double);
+constexpr size_t kNoAllocBytes = kNoAllocPartBytes + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+static unsigned char *noalloc_scratch() {
+    int dev = -1;
+    LAMG_CUDA(cudaGetDevice(&dev));
+    LAMG_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, LAMG_ERR_ARG, "lamg_cycle_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            throw Error{LAMG_ERR_CUDA, std::string("lamg_cycle_noalloc: scratch address lookup failed: ") +
+                                           cudaGetErrorString(e)};
+        g_noalloc_addr[dev] = (unsigned char *)p;
+    }
+    return g_noalloc_addr[dev];
+}
+
+bool engine_noalloc_ready(lamg_ctx *h, int adaptive) {
+    return h->eng_lv64.get() && h->eng_prog[2 * 2 + (adaptive ? 1 : 0)].get() && h->eng_grid > 0;
+}
+
+// Launch the one-cycle program (kind 2) with the fixed scratch; queues the
+// launch and returns the device address of the error word.
+int32_t *engine_run_noalloc(lamg_ctx *h, int adaptive, double mu, cudaStream_t s) {
+    LAMG_REQUIRE(engine_noalloc_ready(h, adaptive), LAMG_ERR_ARG,
+                 "lamg_cycle_noalloc: handle not prepared (call lamg_cycle once with the same adaptive flag)");
+    LAMG_REQUIRE(h->eng_grid <= kNoAllocMaxBlocks, LAMG_ERR_ARG,
+                 "lamg_cycle_noalloc: engine grid of " + std::to_string(h->eng_grid) +
+                     " blocks exceeds the fixed scratch limit of " + std::to_string(kNoAllocMaxBlocks));
+    unsigned char *base = noalloc_scratch();
+    double *part = (double *)base;
+    unsigned int *bar = (unsigned int *)(base + kNoAllocPartBytes);
+    int32_t *err = (int32_t *)(base + kNoAllocPartBytes + 16);
+    LAMG_CUDA(cudaMemsetAsync(base + kNoAllocPartBytes, 0, 256, s));
+    const int k = 2 * 2 + (adaptive ? 1 : 0);
+    MKLevel<double> L0 = describe<double>(h, 0, h->v64[0], h->lv[0].w64.get());
+    L0.r = h->r64.get();
+    EngineArgs<double> a{(const Op *)h->eng_prog[k].get(), 0, h->eng_len[k],
+                         (const MKLevel<double> *)h->eng_lv64.get(), L0, mu, part, nullptr, h->scratch.get(),
+                         bar, err, nullptr};
+    void *args[] = {&a};
+    LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<double>, dim3(h->eng_grid), dim3(kEngThreads), args,
+                                          kEngSmem, s));
+    note_launch();
+    return err;
 }
 
 int64_t engine_program_ops(lamg_ctx *h, int kind, int adaptive) {

@@ -202,6 +202,8 @@ void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s);
 bool engine_failed(lamg_ctx *h, cudaStream_t s);
 void engine_report(lamg_ctx *h);
 void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out);
+bool engine_noalloc_ready(lamg_ctx *h, int adaptive);
+int32_t *engine_run_noalloc(lamg_ctx *h, int adaptive, double mu, cudaStream_t s);
 
 // solve.cu
 void build_solve_layout(lamg_ctx *h, cudaStream_t s);
@@ -210,6 +212,7 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
 void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X, int64_t ld,
                           double tol, lamg_precision p, cudaStream_t s, lamg_stats *st);
 void cycle_device(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s);
+void cycle_device_noalloc(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s);
 void adjoint_device(lamg_ctx *h, const double *x, const double *g, double *lambda,
                     const int32_t *eu, const int32_t *ev, int64_t m, void *dw, int32_t dw32,
                     double tol, lamg_precision p, cudaStream_t s, lamg_stats *st);

@@ -518,6 +518,27 @@ void cycle_device(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cud
     after_step(h, 2, s);
 }
 
+// One cycle without any allocation: the handle's buffers and program must
+// exist already; the engine scratch is the library's fixed device array.
+void cycle_device_noalloc(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s) {
+    LAMG_REQUIRE(!h->v64.empty() && h->scratch.get() && h->r64.get() && engine_noalloc_ready(h, adaptive),
+                 LAMG_ERR_ARG,
+                 "lamg_cycle_noalloc: handle not prepared (call lamg_cycle once with the same adaptive flag)");
+    const int32_t n = h->lv[0].n;
+    const SolveLevel &V0 = h->lv[0];
+    k_gather_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, V0.perm.get(), b, h->v64[0].b.get());
+    LAMG_CHECK_LAUNCH();
+    k_gather_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, V0.perm.get(), x, h->v64[0].x.get());
+    LAMG_CHECK_LAUNCH();
+    int32_t *err = engine_run_noalloc(h, adaptive, adaptive ? 1.0 : h->opt.mu_flat, s);
+    k_scatter_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, V0.perm.get(), h->v64[0].x.get(), x);
+    LAMG_CHECK_LAUNCH();
+    int32_t e = 0;
+    LAMG_CUDA(cudaMemcpyAsync(&e, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LAMG_CUDA(cudaStreamSynchronize(s));
+    LAMG_REQUIRE(e == 0, LAMG_ERR_TIMEOUT, "cycle engine: grid barrier timed out");
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint: lambda = A^+ (g - mean g), dw_e = -(lambda_u - lambda_v)(x_u - x_v)
 // ---------------------------------------------------------------------------

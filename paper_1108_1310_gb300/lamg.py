@@ -75,6 +75,7 @@ def _load():
         "lamg_level_info": (I32, [P, I32, P]),
         "lamg_level_copy": (I32, [P, I32, I32, P, I64]),
         "lamg_cycle": (I32, [P, P, P, I32, P]),
+        "lamg_cycle_noalloc": (I32, [P, P, P, I32, P]),
         "lamg_profile": (I32, [P, I32, P, P, P]),
         "lamg_launch_count": (I32, [P]),
     }
@@ -232,6 +233,13 @@ def lamg_cycle(h, b, x, adaptive: bool = True, stream=None):
     _dev(b, torch.float64, "b")
     _dev(x, torch.float64, "x")
     _check(_lib.lamg_cycle(h, _ptr(b), _ptr(x), int(adaptive), _stream(stream)), "lamg_cycle")
+
+
+def lamg_cycle_noalloc(h, b, x, adaptive: bool = True, stream=None):
+    """lamg_cycle without allocation; the handle must have run lamg_cycle once."""
+    _dev(b, torch.float64, "b")
+    _dev(x, torch.float64, "x")
+    _check(_lib.lamg_cycle_noalloc(h, _ptr(b), _ptr(x), int(adaptive), _stream(stream)), "lamg_cycle_noalloc")
 
 
 def lamg_profile(h, enable: bool):
