@@ -35,6 +35,13 @@ WORKLOADS = {
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
 }
 TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10}
+# batched forms (many right-hand sides on one hierarchy; many graphs as one union)
+BATCHED = {
+    "rgg2m_b64": "64 zero-sum Gaussian RHS on a 2M-node 2-D RGG (mean degree 12, w = exp(-d^2/r^2), FP32); "
+                 "FP32 cycles in FP64 IR to 1e-8, lamg_solve_batched",
+    "er500": "500 Erdos-Renyi graphs (LCC), n uniform in [1k, 200k], mean degree 8, unit weights, one zero-sum "
+             "RHS each, as one block-diagonal union (lamg_setup_graphs); FP32 cycles in FP64 IR to 1e-8 per graph",
+}
 CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64)}
 
 
@@ -146,13 +153,108 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(args, L, W, torch, dev, stream, rank, world):
+    """One step = setup + solve of every right-hand side / every graph to 1e-8."""
+    tol = 1e-8
+    if args.workload == "rgg2m_b64":
+        g, gptr, R = W.config_graph("rgg2m"), None, 64
+        B = torch.tensor(W.zero_sum_rhs(g.n, 3, count=R), device=dev)
+    else:
+        (g, gptr), R = W.er_batch(500, 1000, 200_000, seed=7), 1
+        B = torch.tensor(W.zero_sum_rhs_graphs(gptr, 3), device=dev)
+    rp = torch.tensor(g.rp, device=dev)
+    col = torch.tensor(g.col, device=dev)
+    w = torch.tensor(g.w, device=dev).to(torch.float32)
+    X = torch.zeros_like(B)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def setup():
+        if gptr is None:
+            return L.lamg_setup(g.n, rp, col, w, opt, stream)
+        return L.lamg_setup_graphs(gptr, rp, col, w, opt, stream)
+
+    def solve(h, prec):
+        X.zero_()
+        if R > 1:
+            sts = L.lamg_solve_batched(h, B, X, tol, prec, stream)
+            return sum(s.cycles for s in sts), max(s.rel_res for s in sts), sts[0].levels
+        st = L.lamg_solve(h, B, X, tol, prec, stream)
+        return st.cycles, st.rel_res, st.levels
+
+    def step():
+        h = setup()
+        r = solve(h, L.LAMG_FP32_IR)
+        L.lamg_free(h)
+        return r
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    times, res = [], []
+    launches0 = L.lamg_launch_count()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res.append(step())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            flush.fill_(1.0)
+    launches = L.lamg_launch_count() - launches0
+    ms = sum(times) / len(times)
+    cyc = sum(r[0] for r in res) / len(res)
+
+    def timed(fn):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    # the same solves in plain FP64, and (many RHS) one right-hand side alone, on one hierarchy
+    h = setup()
+    t32, r32 = timed(lambda: solve(h, L.LAMG_FP32_IR))
+    t64, r64 = timed(lambda: solve(h, L.LAMG_FP64))
+    cmp = {"solve_ms_fp32ir": t32, "cycles_fp32ir": r32[0], "rel_res_fp32ir": r32[1],
+           "solve_ms_fp64": t64, "cycles_fp64": r64[0], "rel_res_fp64": r64[1]}
+    if R > 1:
+        b1 = B[:, 0].contiguous()
+        x1 = torch.zeros_like(b1)
+        t1, st1 = timed(lambda: L.lamg_solve(h, b1, x1, tol, L.LAMG_FP32_IR, stream))
+        t1d, st1d = timed(lambda: L.lamg_solve(h, b1, x1.zero_(), tol, L.LAMG_FP64, stream))
+        cmp.update({"single_rhs_ms_fp32ir": t1, "single_rhs_ms_fp64": t1d,
+                    "batched_ms_per_rhs_fp32ir": t32 / R, "batched_ms_per_rhs_fp64": t64 / R})
+    L.lamg_free(h)
+    line = {
+        "metric": "edges*cycles/s (LAMG setup + solve to tol)",
+        "value": world * g.m * cyc / (ms / 1e3), "unit": "edges*cycles/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": BATCHED[args.workload], "n": g.n, "m": g.m,
+                   "rhs": R, "graphs": 1 if gptr is None else len(gptr) - 1, "tol": tol,
+                   "levels": res[-1][2], "cycles_all_columns": cyc, "max_rel_res": res[-1][1],
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
+        "fp64_vs_ir": cmp, "e2e": None, "roofline": None, "cpu_baseline": None,
+        "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu")
-    ap.add_argument("--workload", default="chung_lu1m", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="chung_lu1m", choices=list(WORKLOADS) + list(BATCHED))
     ap.add_argument("--precision", default=None, choices=["fp32ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -177,6 +279,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    if args.workload in BATCHED:
+        return run_batched(args, L, W, torch, dev, stream, rank, world)
     gname, pdef, desc = WORKLOADS[args.workload]
     prec_name = args.precision or pdef
     prec = L.LAMG_FP32_IR if prec_name == "fp32ir" else L.LAMG_FP64

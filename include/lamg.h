@@ -118,6 +118,29 @@ lamg_status lamg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, co
                        int32_t w_is_fp32, const lamg_options *opt, lamg_stream stream,
                        lamg_handle *out);
 
+/* lamg_setup_graphs -- one hierarchy for a block-diagonal union of
+ * num_graphs independent graphs (the batched many-graphs form; the paper
+ * treats one connected graph, Sec. 1, and says to split a disconnected one
+ * into its components).  Graph g owns the level-1 nodes
+ * [graph_ptr[g], graph_ptr[g+1]) of the CSR, which holds all graphs.
+ *  graph_ptr  HOST int64[num_graphs + 1], graph_ptr[0] = 0,
+ *             graph_ptr[num_graphs] = n, strictly increasing; copied.
+ * The setup rules of Sec. 4.1 run unchanged on the union (they are local to
+ * nodes and edges; the stopping tests use the union's totals).  Per graph:
+ * the zero-sum test on b, the level-1 mean projection and the stopping test
+ * ||r_g|| <= tol ||b_g|| of lamg_solve; the dense coarsest solve uses
+ * A + sum_K 1_K 1_K^T / n_K over the coarsest level's components K.  A graph
+ * coarsened to one isolated node is left unchanged by relaxation.
+ * Errors as lamg_setup, plus: an edge joining two graphs, or graph_ptr
+ * malformed: LAMG_ERR_ARG; a graph not connected: LAMG_ERR_DISCONNECTED
+ * (with opt->validate).  lamg_solve, lamg_solve_host, lamg_cycle and
+ * lamg_adjoint work per graph on such a handle (st->rel_res is the largest
+ * per-graph relative residual); lamg_solve_batched needs num_graphs = 1. */
+lamg_status lamg_setup_graphs(int32_t num_graphs, const int64_t *graph_ptr, int64_t n,
+                              const int64_t *row_ptr, const int32_t *col, const void *w,
+                              int32_t w_is_fp32, const lamg_options *opt, lamg_stream stream,
+                              lamg_handle *out);
+
 /* lamg_solve -- cycles of Sec. 4.2 until ||b - A x||_2 <= tol ||b||_2.
  *  b  device FP64[n], zero-sum (LAMG_ERR_RHS_NOT_ZERO_SUM otherwise)
  *  x  device FP64[n]; in: initial guess, out: the zero-mean iterate
@@ -134,11 +157,18 @@ lamg_status lamg_solve(lamg_handle h, const double *b, double *x, double tol,
 lamg_status lamg_solve_host(lamg_handle h, const double *b_host, double *x_host, double tol,
                             lamg_precision precision, lamg_stream stream, lamg_stats *st);
 
-/* lamg_solve_batched -- nrhs right-hand sides on one hierarchy (the solve is
- * re-used, Sec. 1: "a smaller cost to re-solve the system for multiple b's").
- *  B, X  device FP64, row-interleaved: entry (u, j) at [u * ld + j], ld >= nrhs
- *  Every column of B must be zero-sum.  Each column converges to tol; the
- *  call returns when all have.  st: host array of nrhs stats, may be NULL. */
+/* lamg_solve_batched -- nrhs right-hand sides on one hierarchy.  The setup
+ * is reused (Sec. 1: once the hierarchy exists, further right-hand sides
+ * cost only cycles), and up to 128 columns at a time run through one cycle
+ * program whose kernels gather 4 interleaved columns per neighbour (SpMM).
+ *  B, X  device FP64, row-interleaved: entry (u, j) at [u * ld + j], ld >= nrhs.
+ *        X in: initial guesses, out: zero-mean iterates.
+ *  Every column of B must be zero-sum (LAMG_ERR_RHS_NOT_ZERO_SUM names the
+ *  first one that is not).  Each column has its own recombination
+ *  coefficients, mean projection and stopping test; the call returns when all
+ *  columns have reached tol (LAMG_ERR_NOT_CONVERGED, X valid, otherwise).
+ *  st: host array of nrhs stats (cycles/outer_steps: when that column
+ *  converged; rel_res: at exit), may be NULL. */
 lamg_status lamg_solve_batched(lamg_handle h, int32_t nrhs, const double *B, double *X,
                                int64_t ld, double tol, lamg_precision precision,
                                lamg_stream stream, lamg_stats *st);

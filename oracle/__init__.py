@@ -61,6 +61,7 @@ def lib():
                 "orc_canon_sum": (_D, [_P, _I64]),
                 "orc_canon_sum_global": (_D, [_P, _I64]),
                 "orc_validate": (_I32, [_I64, _P, _P, _P]),
+                "orc_validate_graphs": (_I32, [_I64, _P, _P, _P, _I32, _P]),
                 "orc_laplacian_dense": (None, [_I64, _P, _P, _P, _P]),
                 "orc_colour": (_I32, [_I64, _P, _P, _U64, _P]),
                 "orc_gs_sweep_lex": (None, [_I64, _P, _P, _P, _P, _P]),
@@ -69,6 +70,7 @@ def lib():
                 "orc_hubs": (None, [_I64, _P, _P, _P, _D, _P]),
                 "orc_dense_pinv_solve": (_I32, [_I64, _P, _P, _P]),
                 "orc_setup": (_I32, [_I64, _P, _P, _P, _P, _P]),
+                "orc_setup_graphs": (_I32, [_I64, _P, _P, _P, _I32, _P, _P, _P]),
                 "orc_free": (None, [_P]),
                 "orc_num_levels": (_I32, [_P]),
                 "orc_level_info": (None, [_P, _I32, _P]),
@@ -118,6 +120,13 @@ def canon_sum(t) -> float:
 def canon_sum_global(t) -> float:
     t = np.ascontiguousarray(t, dtype=np.float64)
     return float(lib().orc_canon_sum_global(_p(t), t.size))
+
+
+def validate_graphs(n, rp, col, w, gptr) -> int:
+    """Status of a block-diagonal union of graphs (node ranges gptr)."""
+    rp, col, w = _csr(rp, col, w)
+    gp = np.ascontiguousarray(gptr, dtype=np.int64)
+    return int(lib().orc_validate_graphs(n, _p(rp), _p(col), _p(w), len(gp) - 1, _p(gp)))
 
 
 def validate(n, rp, col, w) -> int:
@@ -183,6 +192,10 @@ def dense_pinv_solve(A, b):
     return x
 
 
+# status codes of oracle/lamg_oracle.h
+OK, ERR_ARG, ERR_NOT_SYMMETRIC, ERR_BAD_WEIGHT, ERR_DISCONNECTED, ERR_RHS_NOT_ZERO_SUM = 0, 1, 2, 3, 4, 5
+
+
 class OracleError(RuntimeError):
     def __init__(self, status):
         super().__init__(f"oracle status {status}")
@@ -192,13 +205,19 @@ class OracleError(RuntimeError):
 class Hierarchy:
     """The oracle's LAMG hierarchy (setup phase, Sec. 4.1) with its solve (Sec. 4.2)."""
 
-    def __init__(self, n, rp, col, w, opts: Opts | None = None, **kw):
+    def __init__(self, n, rp, col, w, opts: Opts | None = None, gptr=None, **kw):
         self.opts = opts if opts is not None else default_opts(**kw)
         rp, col, w = _csr(rp, col, w)
         self.n = int(n)
         self._rp, self._col, self._w = rp, col, w
         h = C.c_void_p()
-        st = lib().orc_setup(self.n, _p(rp), _p(col), _p(w), C.byref(self.opts), C.byref(h))
+        if gptr is None:
+            st = lib().orc_setup(self.n, _p(rp), _p(col), _p(w), C.byref(self.opts), C.byref(h))
+        else:
+            # block-diagonal union of graphs: graph g owns nodes gptr[g]..gptr[g+1]-1
+            self._gptr = np.ascontiguousarray(gptr, dtype=np.int64)
+            st = lib().orc_setup_graphs(self.n, _p(rp), _p(col), _p(w), len(self._gptr) - 1, _p(self._gptr),
+                                        C.byref(self.opts), C.byref(h))
         if st:
             raise OracleError(st)
         self._h = h

@@ -139,8 +139,11 @@ static int64_t find_entry(const int64_t *rp, const int32_t *col, int64_t u, int3
 
 /* The input is the off-diagonal pattern of A as a CSR with both directions of
  * every edge, columns strictly increasing per row, no self loops, w > 0 finite
- * and w_uv == w_vu (Eq. (1.2)); the graph must be connected (Sec. 1). */
-int32_t orc_validate(int64_t n, const int64_t *rp, const int32_t *col, const double *w) {
+ * and w_uv == w_vu (Eq. (1.2)); the graph must be connected (Sec. 1).
+ * With several graphs (block-diagonal union, nodes of graph g in
+ * [gptr[g], gptr[g+1])), no edge may join two graphs (ORC_ERR_ARG) and every
+ * graph must be connected (ORC_ERR_DISCONNECTED). */
+static int32_t validate_core(int64_t n, const int64_t *rp, const int32_t *col, const double *w) {
     if (n < 1 || rp[0] != 0) return ORC_ERR_ARG;
     for (int64_t u = 0; u < n; u++) {
         if (rp[u + 1] < rp[u]) return ORC_ERR_ARG;
@@ -157,18 +160,51 @@ int32_t orc_validate(int64_t n, const int64_t *rp, const int32_t *col, const dou
             int64_t f = find_entry(rp, col, col[e], (int32_t)u);
             if (f < 0 || w[f] != w[e]) return ORC_ERR_NOT_SYMMETRIC;
         }
-    /* connectivity: breadth-first search from node 0 */
-    uint8_t *seen = (uint8_t *)calloc((size_t)n, 1);
-    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    int64_t head = 0, tail = 0;
-    seen[0] = 1; queue[tail++] = 0;
-    while (head < tail) {
-        int32_t u = queue[head++];
-        for (int64_t e = rp[u]; e < rp[u + 1]; e++)
-            if (!seen[col[e]]) { seen[col[e]] = 1; queue[tail++] = col[e]; }
+    return ORC_OK;
+}
+
+/* Connected components by breadth-first search: comp[u] = index of the
+ * component in order of its smallest node; returns the count. */
+static int32_t components(int64_t n, const int64_t *rp, const int32_t *col, int32_t *comp) {
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    for (int64_t u = 0; u < n; u++) comp[u] = -1;
+    int32_t nc = 0;
+    for (int64_t s0 = 0; s0 < n; s0++) {
+        if (comp[s0] >= 0) continue;
+        int64_t head = 0, tail = 0;
+        comp[s0] = nc; queue[tail++] = (int32_t)s0;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            for (int64_t e = rp[u]; e < rp[u + 1]; e++)
+                if (comp[col[e]] < 0) { comp[col[e]] = nc; queue[tail++] = col[e]; }
+        }
+        nc++;
     }
-    free(seen); free(queue);
-    return tail == n ? ORC_OK : ORC_ERR_DISCONNECTED;
+    free(queue);
+    return nc;
+}
+
+int32_t orc_validate_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                            int32_t ngraphs, const int64_t *gptr) {
+    if (ngraphs < 1 || gptr[0] != 0 || gptr[ngraphs] != n) return ORC_ERR_ARG;
+    for (int32_t g = 0; g < ngraphs; g++)
+        if (gptr[g + 1] <= gptr[g]) return ORC_ERR_ARG;
+    int32_t st = validate_core(n, rp, col, w);
+    if (st != ORC_OK) return st;
+    for (int32_t g = 0; g < ngraphs; g++)
+        for (int64_t u = gptr[g]; u < gptr[g + 1]; u++)
+            for (int64_t e = rp[u]; e < rp[u + 1]; e++)
+                if (col[e] < gptr[g] || col[e] >= gptr[g + 1]) return ORC_ERR_ARG;
+    int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t nc = components(n, rp, col, comp);
+    free(comp);
+    return nc == ngraphs ? ORC_OK : ORC_ERR_DISCONNECTED;
+}
+
+int32_t orc_validate(int64_t n, const int64_t *rp, const int32_t *col, const double *w) {
+    if (n < 1) return ORC_ERR_ARG;
+    int64_t gptr[2] = {0, n};
+    return orc_validate_graphs(n, rp, col, w, 1, gptr);
 }
 
 /* Eq. (1.2): a_uu = sum of incident weights, a_uv = -w_uv. */
@@ -257,6 +293,7 @@ int32_t orc_colour(int64_t n, const int64_t *rp, const int32_t *col, uint64_t ke
 static void gs_update(int64_t u, const int64_t *rp, const int32_t *col, const double *w,
                       const double *b, double *x) {
     double s = b[u], d = 0.0;
+    if (rp[u + 1] == rp[u]) return;   /* isolated node (a whole graph of a union, coarsened away): unchanged */
     for (int64_t e = rp[u]; e < rp[u + 1]; e++) { s = s + w[e] * x[col[e]]; d = d + w[e]; }
     x[u] = s / d;
 }
@@ -414,6 +451,23 @@ static void subtract_mean(int64_t n, double *x) {
     for (int64_t i = 0; i < n; i++) x[i] -= m;
 }
 
+/* Mean subtraction on each component separately (comp[u] in [0, ncomp)):
+ * the sums run over the nodes in index order, as subtract_mean does. */
+static void subtract_mean_comp(int64_t n, double *x, const int32_t *comp, int32_t ncomp) {
+    if (ncomp <= 1) { subtract_mean(n, x); return; }
+    double *s = (double *)calloc((size_t)ncomp, sizeof(double));
+    int64_t *c = (int64_t *)calloc((size_t)ncomp, sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) { s[comp[i]] += x[i]; c[comp[i]]++; }
+    for (int32_t k = 0; k < ncomp; k++) s[k] /= (double)c[k];
+    for (int64_t i = 0; i < n; i++) x[i] -= s[comp[i]];
+    free(s); free(c);
+}
+
+/* Mean subtraction on each graph's contiguous node range. */
+static void subtract_mean_ranges(double *x, int32_t ngraphs, const int64_t *gptr) {
+    for (int32_t g = 0; g < ngraphs; g++) subtract_mean(gptr[g + 1] - gptr[g], x + gptr[g]);
+}
+
 int32_t orc_dense_pinv_solve(int64_t n, const double *A, const double *b, double *x) {
     double *M = (double *)malloc(sizeof(double) * (size_t)(n * n));
     for (int64_t i = 0; i < n * n; i++) M[i] = A[i] + 1.0 / (double)n;
@@ -441,11 +495,14 @@ typedef struct {
     double alpha, gamma_l, tv_ratio;
     int32_t rounds, sel_round;
     double *chol;                     /* coarsest dense factor, if direct */
+    int32_t *comp; int32_t ncomp;     /* coarsest: connected components */
 } orc_level;
 
 struct orc_hier {
     orc_opts o;
     int32_t L;
+    int32_t ngraphs;                  /* graphs of the block-diagonal union */
+    int64_t *gptr;                    /* level-1 node ranges of the graphs */
     orc_level lv[128];
 };
 
@@ -474,6 +531,7 @@ static double relax_tvs(orc_level *L, const orc_opts *o, int32_t level) {
             for (int64_t u = 0; u < n; u++) {
                 if (L->colour[u] != c) continue;
                 int64_t deg = L->rp[u + 1] - L->rp[u];
+                if (deg == 0) continue;   /* isolated node: its TVs keep their random values */
                 for (int k = 0; k < K; k++) {
                     for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++)
                         t[e - L->rp[u]] = L->w[e] * L->X[(int64_t)L->col[e] * K + k];
@@ -681,13 +739,24 @@ static void level_prepare(orc_level *L, uint64_t seed, int32_t level) {
     L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), L->colour, &L->jp_rounds);
 }
 
+/* Coarsest level: the direct solve uses (A + sum_K 1_K 1_K^T / n_K)^-1 over the
+ * connected components K of the level (one component for a connected input),
+ * which maps a right-hand side that is zero-sum on every component to the
+ * solution with zero mean on every component. */
 static int make_coarsest(orc_level *L, const orc_opts *o) {
     L->coarsest = 1;
-    if (L->n <= o->dense_max) {
-        int64_t n = L->n;
+    int64_t n = L->n;
+    L->comp = (int32_t *)xcalloc((size_t)n, sizeof(int32_t));
+    L->ncomp = components(n, L->rp, L->col, L->comp);
+    if (n <= o->dense_max) {
+        int64_t *size = (int64_t *)calloc((size_t)L->ncomp, sizeof(int64_t));
+        for (int64_t i = 0; i < n; i++) size[L->comp[i]]++;
         L->chol = (double *)xcalloc((size_t)(n * n), sizeof(double));
         orc_laplacian_dense(n, L->rp, L->col, L->w, L->chol);
-        for (int64_t i = 0; i < n * n; i++) L->chol[i] += 1.0 / (double)n;
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = 0; j < n; j++)
+                if (L->comp[i] == L->comp[j]) L->chol[i * n + j] += 1.0 / (double)size[L->comp[i]];
+        free(size);
         if (chol_factor(n, L->chol)) return ORC_ERR_ARG;
     }
     return ORC_OK;
@@ -696,13 +765,16 @@ static int make_coarsest(orc_level *L, const orc_opts *o) {
 /* Setup phase, Sec. 4.1: coarsen by caliber-1 aggregation until n < 150, or
  * until relaxation converges rapidly (TV energy ratio per sweep <= 0.1), or the
  * aggregation stalls (alpha > 0.9), or the depth limit. */
-int32_t orc_setup(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
-                  const orc_opts *o, orc_hier **out) {
+int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                         int32_t ngraphs, const int64_t *gptr, const orc_opts *o, orc_hier **out) {
     *out = NULL;
-    int32_t st = orc_validate(n, rp, col, w);
+    int32_t st = orc_validate_graphs(n, rp, col, w, ngraphs, gptr);
     if (st != ORC_OK) return st;
     orc_hier *h = (orc_hier *)calloc(1, sizeof(orc_hier));
     h->o = *o;
+    h->ngraphs = ngraphs;
+    h->gptr = (int64_t *)xcalloc((size_t)ngraphs + 1, sizeof(int64_t));
+    memcpy(h->gptr, gptr, sizeof(int64_t) * ((size_t)ngraphs + 1));
     orc_level *L0 = &h->lv[0];
     L0->n = n; L0->nnz = rp[n];
     L0->rp = (int64_t *)xcalloc((size_t)(n + 1), sizeof(int64_t));
@@ -756,13 +828,22 @@ int32_t orc_setup(int64_t n, const int64_t *rp, const int32_t *col, const double
     return ORC_OK;
 }
 
+int32_t orc_setup(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                  const orc_opts *o, orc_hier **out) {
+    *out = NULL;
+    if (n < 1) return ORC_ERR_ARG;
+    int64_t gptr[2] = {0, n};
+    return orc_setup_graphs(n, rp, col, w, 1, gptr, o, out);
+}
+
 void orc_free(orc_hier *h) {
     if (!h) return;
+    free(h->gptr);
     for (int32_t l = 0; l < h->L; l++) {
         orc_level *L = &h->lv[l];
         free(L->rp); free(L->col); free(L->w); free(L->diag); free(L->colour);
         free(L->X); free(L->aff); free(L->q); free(L->score); free(L->hub);
-        free(L->state); free(L->agg); free(L->chol);
+        free(L->state); free(L->agg); free(L->chol); free(L->comp);
     }
     free(h);
 }
@@ -841,10 +922,10 @@ static double dot(int64_t n, const double *a, const double *b) {
 }
 
 static void coarsest_solve(const orc_level *L, const orc_opts *o, const double *b, double *x) {
-    if (L->chol) { chol_solve(L->n, L->chol, b, x); subtract_mean(L->n, x); return; }
+    if (L->chol) { chol_solve(L->n, L->chol, b, x); subtract_mean_comp(L->n, x, L->comp, L->ncomp); return; }
     for (int64_t i = 0; i < L->n; i++) x[i] = 0.0;
     for (int s = 0; s < o->coarse_sweeps; s++) relax(L, b, x);
-    subtract_mean(L->n, x);
+    subtract_mean_comp(L->n, x, L->comp, L->ncomp);
 }
 
 /* Iterate recombination, Eq. (3.13): y = x + sum_i alpha_i (x_i - x) with alpha
@@ -958,7 +1039,7 @@ static void cycle_once(solve_ctx *c, const double *b, double *x) {
     for (int32_t l = 0; l < h->L; l++) c->visits[l] = 0;
     visit(c, 0, 1);
     memcpy(x, c->x[0], sizeof(double) * (size_t)n);
-    subtract_mean(n, x);
+    subtract_mean_ranges(x, h->ngraphs, h->gptr);
 }
 
 static double norm2(int64_t n, const double *v) { return sqrt(dot(n, v, v)); }
@@ -971,22 +1052,33 @@ int32_t orc_cycle(const orc_hier *h, const double *b, double *x, int32_t adaptiv
     return ORC_OK;
 }
 
+/* Cycles until every graph g of the union has ||b_g - A x_g|| <= tol ||b_g||
+ * (one graph: the plain relative residual test).  res_hist holds the norm of
+ * the whole residual. */
 int32_t orc_solve(const orc_hier *h, const double *b, double *x, double tol, int32_t max_cycles,
                   int32_t adaptive, double *res_hist, int32_t *cycles_out) {
     const orc_level *F = &h->lv[0];
     int64_t n = F->n;
-    double sb = 0.0, ab = 0.0;
-    for (int64_t i = 0; i < n; i++) { sb += b[i]; ab += fabs(b[i]); }
-    if (fabs(sb) > 1e-10 * (ab > 0 ? ab : 1.0)) return ORC_ERR_RHS_NOT_ZERO_SUM;
+    int32_t G = h->ngraphs;
+    for (int32_t g = 0; g < G; g++) {
+        double sb = 0.0, ab = 0.0;
+        for (int64_t i = h->gptr[g]; i < h->gptr[g + 1]; i++) { sb += b[i]; ab += fabs(b[i]); }
+        if (fabs(sb) > 1e-10 * (ab > 0 ? ab : 1.0)) return ORC_ERR_RHS_NOT_ZERO_SUM;
+    }
     solve_ctx c;
     ctx_init(&c, h, adaptive);
     double *r = (double *)malloc(sizeof(double) * (size_t)n);
-    double bn = norm2(n, b);
+    double *bn = (double *)malloc(sizeof(double) * (size_t)G);
+    for (int32_t g = 0; g < G; g++) bn[g] = norm2(h->gptr[g + 1] - h->gptr[g], b + h->gptr[g]);
     residual(F, b, x, r);
     double rn = norm2(n, r);
     if (res_hist) res_hist[0] = rn;
     int32_t it = 0;
-    while (it < max_cycles && rn > tol * bn) {
+    for (;;) {
+        int pending = 0;
+        for (int32_t g = 0; g < G && !pending; g++)
+            if (norm2(h->gptr[g + 1] - h->gptr[g], r + h->gptr[g]) > tol * bn[g]) pending = 1;
+        if (!pending || it >= max_cycles) break;
         cycle_once(&c, b, x);
         residual(F, b, x, r);
         rn = norm2(n, r);
@@ -994,7 +1086,7 @@ int32_t orc_solve(const orc_hier *h, const double *b, double *x, double tol, int
         if (res_hist) res_hist[it] = rn;
     }
     if (cycles_out) *cycles_out = it;
-    free(r);
+    free(r); free(bn);
     ctx_free(&c);
     return ORC_OK;
 }
@@ -1005,7 +1097,7 @@ int32_t orc_adjoint(const orc_hier *h, const double *x, const double *g, double 
     int64_t n = h->lv[0].n;
     double *gz = (double *)malloc(sizeof(double) * (size_t)n);
     memcpy(gz, g, sizeof(double) * (size_t)n);
-    subtract_mean(n, gz);
+    subtract_mean_ranges(gz, h->ngraphs, h->gptr);
     for (int64_t i = 0; i < n; i++) lambda[i] = 0.0;
     int32_t st = orc_solve(h, gz, lambda, tol, max_cycles, adaptive, NULL, NULL);
     free(gz);

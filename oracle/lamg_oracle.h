@@ -65,6 +65,11 @@ uint64_t orc_splitmix64(uint64_t key);
 double   orc_canon_sum(const double *t, int64_t len);
 double   orc_canon_sum_global(const double *t, int64_t len);
 int32_t  orc_validate(int64_t n, const int64_t *rp, const int32_t *col, const double *w);
+/* Several graphs as one block-diagonal union: graph g owns nodes
+ * [gptr[g], gptr[g+1]).  No edge may join two graphs (ORC_ERR_ARG); each graph
+ * must be connected (ORC_ERR_DISCONNECTED). */
+int32_t  orc_validate_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                             int32_t ngraphs, const int64_t *gptr);
 void     orc_laplacian_dense(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
                              double *A /* n*n row-major */);
 int32_t  orc_colour(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key,
@@ -83,6 +88,11 @@ int32_t  orc_dense_pinv_solve(int64_t n, const double *A, const double *b, doubl
 /* ---- setup ---- */
 int32_t  orc_setup(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
                    const orc_opts *o, orc_hier **out);
+/* The hierarchy of the block-diagonal union of ngraphs graphs (same setup
+ * rules on the union; the coarsest direct solve, the level-1 mean projection,
+ * the zero-sum test and the stopping test act per component / per graph). */
+int32_t  orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                          int32_t ngraphs, const int64_t *gptr, const orc_opts *o, orc_hier **out);
 void     orc_free(orc_hier *h);
 int32_t  orc_num_levels(const orc_hier *h);
 /* info[0..15]: n, nnz, ncolours, K, nc, rounds, sel_round, coarsest, stop_reason,

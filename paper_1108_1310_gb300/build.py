@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblamg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = {"prims.cu": [], "setup.cu": ["-fmad=false"], "solve.cu": [], "cycle.cu": [], "api.cu": []}
+UNITS = {"prims.cu": [], "setup.cu": ["-fmad=false"], "solve.cu": [], "cycle.cu": [], "batched.cu": [], "api.cu": []}
 
 
 def _nvcc() -> str:

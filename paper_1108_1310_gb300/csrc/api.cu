@@ -131,26 +131,35 @@ void lamg_default_options(lamg_options *o) {
 
 const char *lamg_last_error(void) { return g_last_error.c_str(); }
 
-lamg_status lamg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
-                       int32_t w_is_fp32, const lamg_options *opt, lamg_stream stream, lamg_handle *out) {
+static lamg_status setup_impl(int32_t ngraphs, const int64_t *graph_ptr, int64_t n, const int64_t *row_ptr,
+                              const int32_t *col, const void *w, int32_t w_is_fp32, const lamg_options *opt,
+                              lamg_stream stream, lamg_handle *out) {
     if (out) *out = nullptr;
     lamg_ctx *h = nullptr;
     lamg_status st = guarded([&] {
         LAMG_REQUIRE(out != nullptr, LAMG_ERR_ARG, "out is NULL");
         LAMG_REQUIRE(n >= 1 && n < ((int64_t)1 << 31), LAMG_ERR_ARG, "n must be in [1, 2^31)");
         LAMG_REQUIRE(row_ptr != nullptr, LAMG_ERR_ARG, "NULL row_ptr");
+        LAMG_REQUIRE(ngraphs >= 1 && graph_ptr != nullptr, LAMG_ERR_ARG, "num_graphs must be >= 1 with graph_ptr");
+        LAMG_REQUIRE(graph_ptr[0] == 0 && graph_ptr[ngraphs] == n, LAMG_ERR_ARG,
+                     "graph_ptr must start at 0 and end at n");
+        for (int32_t g = 0; g < ngraphs; g++)
+            LAMG_REQUIRE(graph_ptr[g + 1] > graph_ptr[g], LAMG_ERR_ARG, "graph_ptr must be strictly increasing");
         auto t0 = std::chrono::steady_clock::now();
         h = new lamg_ctx();
+        h->ngraphs = ngraphs;
+        h->gptr.assign(graph_ptr, graph_ptr + ngraphs + 1);
         if (opt) h->opt = *opt; else lamg_default_options(&h->opt);
         LAMG_REQUIRE(h->opt.gamma >= 1.0 && h->opt.nu_tv >= 0 && h->opt.nu1 >= 0 && h->opt.nu2 >= 0 &&
                          h->opt.k_finest >= 1 && h->opt.max_rounds >= 1 && h->opt.max_levels >= 1 &&
                          h->opt.dense_max >= 1,
                      LAMG_ERR_ARG, "invalid options");
         cudaStream_t s = (cudaStream_t)stream;
-        if (h->opt.validate) validate_graph(n, row_ptr, col, w, w_is_fp32, s);
+        if (h->opt.validate) validate_graph(n, row_ptr, col, w, w_is_fp32, s, ngraphs, graph_ptr);
         build_hierarchy(h, n, row_ptr, col, w, w_is_fp32, s);
         build_solve_layout(h, s);
         h->n = n;
+        if (ngraphs > 1) build_graph_maps(h, s);
         auto t1 = std::chrono::steady_clock::now();
         h->t_setup_s = std::chrono::duration<double>(t1 - t0).count();
         int64_t tot = 0;
@@ -167,6 +176,23 @@ lamg_status lamg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     }
     *out = h;
     return LAMG_OK;
+}
+
+lamg_status lamg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
+                       int32_t w_is_fp32, const lamg_options *opt, lamg_stream stream, lamg_handle *out) {
+    const int64_t gp[2] = {0, n};
+    return setup_impl(1, gp, n, row_ptr, col, w, w_is_fp32, opt, stream, out);
+}
+
+lamg_status lamg_setup_graphs(int32_t num_graphs, const int64_t *graph_ptr, int64_t n, const int64_t *row_ptr,
+                              const int32_t *col, const void *w, int32_t w_is_fp32, const lamg_options *opt,
+                              lamg_stream stream, lamg_handle *out) {
+    if (out) *out = nullptr;
+    if (num_graphs < 1 || !graph_ptr) {
+        set_last_error("num_graphs must be >= 1 with graph_ptr");
+        return LAMG_ERR_ARG;
+    }
+    return setup_impl(num_graphs, graph_ptr, n, row_ptr, col, w, w_is_fp32, opt, stream, out);
 }
 
 lamg_status lamg_solve(lamg_handle h, const double *b, double *x, double tol, lamg_precision p,

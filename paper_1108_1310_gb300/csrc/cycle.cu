@@ -20,117 +20,9 @@
 #include <cstdlib>
 #include <mutex>
 
-#include "solve_rows.cuh"
+#include "engine.cuh"
 
 namespace lamg {
-
-constexpr int kEngThreads = 1024;
-constexpr long long kMaxSpins = 1ll << 23;  // about a second of polling
-
-template <class T>
-struct MKLevel {
-    int32_t n, nc;
-    const int32_t *rp, *col;
-    const T *w;
-    const int32_t *cb;
-    const int32_t *wrows, *brows;
-    int32_t nw, nb;
-    const int32_t *pagg, *mptr, *mlist, *wagg, *bagg;
-    int32_t nwagg, nbagg;
-    T *x, *b, *r, *xs0, *xs1, *rs0, *rs1;
-    const double *minv;
-};
-
-enum : int32_t {
-    OP_SWEEP = 0,     // level, colour a (all blocks)
-    OP_SWEEP_RUN,     // level, colours a..b-1 (single block, __syncthreads between colours)
-    OP_RESID,         // r = b - A x; a >= 0: also save x, r into slot a (recombination)
-    OP_RESTRICT,      // b^c = mu P^T r, x^c = 0
-    OP_ZERO,          // x = 0 (coarsest solved by sweeps)
-    OP_COARSE,        // x = M^-1 b (dense coarsest, FP64 arithmetic)
-    OP_PROLONG,       // x += P x^c
-    OP_RECOMB_DOTS,   // partial dot products, theta = a
-    OP_RECOMB_APPLY,  // alpha from the partials, y = x + sum alpha_i (x_i - x)
-    OP_MEAN_PART,     // partial sums of x (cycle precision)
-    OP_MEAN_APPLY,    // x -= mean
-    OP_IR_PREP,       // b32 = (float) r64, x32 = 0
-    OP_IR_UPDATE,     // x64 += (double) x32
-    OP_MEAN64_PART,   // partial sums of x64
-    OP_MEAN64_APPLY,  // x64 -= mean
-    OP_RES64,         // r64 = b64 - A x64 (FP64) and partial sums of r64^2
-    OP_NORM64_FIN,    // out[0] = sum of the partials
-    OP_SWEEP_SMEM,    // level, a = sweeps: whole sweeps from shared memory (single block)
-};
-
-constexpr int kEngSmem = 200 * 1024;  // dynamic shared memory of the engine block
-
-// bytes the shared-memory sweep needs for a level: rp, col, w, x, b, colour bounds
-template <class T>
-__host__ __device__ __forceinline__ int64_t smem_bytes(int64_t n, int64_t nnz, int64_t ncol) {
-    auto al = [](int64_t b) { return (b + 15) & ~int64_t(15); };
-    return al(4 * (n + 1)) + al(4 * nnz) + al((int64_t)sizeof(T) * nnz) + 2 * al((int64_t)sizeof(T) * n) +
-           al(16 * ncol);
-}
-
-struct Op {
-    int32_t type, level, a, b, sb;
-};
-
-// colour count of a level is carried in the op (b) for the shared-memory sweep
-
-template <class T>
-struct EngineArgs {
-    const Op *prog;
-    int32_t begin, end;
-    const MKLevel<T> *lv;
-    MKLevel<double> L0;     // FP64 finest level (outer refinement / residual)
-    T mu;
-    double *part;           // gridDim * 8 partial sums
-    double *alpha;          // 2 per level
-    double *out;            // results
-    unsigned int *bar;      // barrier: count, generation
-    int32_t *err;
-    unsigned long long *optime;  // optional per (level, op, single-block) time and count
-};
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// ---------------------------------------------------------------------------
-// grid barrier (bounded spin)
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err) {
-    __shared__ int bad;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        bad = 0;
-        volatile unsigned int *vgen = bar + 1;
-        const unsigned int gen = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if ((++spins & 63) == 0) {
-                    if (*(volatile int32_t *)err) { bad = 1; break; }
-                    if (spins > kMaxSpins) { atomicExch(err, 1); bad = 1; break; }
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return bad == 0;
-}
 
 // ---------------------------------------------------------------------------
 // ops; (bid, nb) = this block's index among the nb blocks executing the op
@@ -183,25 +75,31 @@ __device__ __forceinline__ void restrict_op(const MKLevel<T> &F, const MKLevel<T
     for (int64_t k = bid; k < F.nbagg; k += nb) restrict_row<M_BLK, T>(F.bagg[k], F.mptr, F.mlist, F.r, mu, C.b);
 }
 
-template <class T>
-__device__ __forceinline__ double block_sum_d(double v) {
-    __shared__ double sh[32];
-    v = warp_allsum(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    const int nw = (int)(blockDim.x >> 5);
-    for (int k = 0; k < nw; k++) t += sh[k];
-    __syncthreads();
-    return t;  // in every thread
-}
-
-// sum of the nb block partials at slot k (same order in every block)
-__device__ __forceinline__ double sum_partials(const double *part, int nb, int k) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * 8 + k];
-    return block_sum_d<double>(v);
+// tail row i: r_i = b_i + sum of w_iv x_v over v < tt0 (outside the tail)
+template <int M, class T>
+__device__ __forceinline__ void tail_pre_row(int32_t i, const MKLevel<T> &L) {
+    const int32_t e = L.rp[i + 1], t0 = L.tt0;
+    const int st = sstride<M>();
+    T acc = T(0), dummy = T(0);
+    int32_t j = L.rp[i] + slane<M>();
+    for (; j + 3 * st < e; j += 4 * st) {
+        int32_t c[4];
+        T wv[4], xv[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) c[k] = L.col[j + k * st];
+#pragma unroll
+        for (int k = 0; k < 4; k++) wv[k] = L.w[j + k * st];
+#pragma unroll
+        for (int k = 0; k < 4; k++) xv[k] = c[k] < t0 ? L.x[c[k]] : T(0);
+#pragma unroll
+        for (int k = 0; k < 4; k++) acc += wv[k] * xv[k];
+    }
+    for (; j < e; j += st) {
+        const int32_t cj = L.col[j];
+        if (cj < t0) acc += L.w[j] * L.x[cj];
+    }
+    reduce2<M>(acc, dummy);
+    if (slane<M>() == 0) L.r[i] = L.b[i] + acc;
 }
 
 template <class T>
@@ -340,6 +238,88 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             if (threadIdx.x == 0) a.part[(int64_t)bid * 8 + 5] = v;
             break;
         }
+        case OP_GMEAN_PART:
+        case OP_GMEAN64_PART:
+        case OP_GNORM64:
+            // one block per graph; natural ids of the graph are contiguous
+            for (int32_t g = bid; g < a.ngraphs; g += nb) {
+                const int64_t s0 = a.gptr[g], e0 = a.gptr[g + 1];
+                double v = 0.0;
+                for (int64_t u = s0 + threadIdx.x; u < e0; u += blockDim.x) {
+                    const int32_t i = a.iperm0[u];
+                    if (op.type == OP_GMEAN_PART) v += (double)L.x[i];
+                    else if (op.type == OP_GMEAN64_PART) v += a.L0.x[i];
+                    else v += a.L0.r[i] * a.L0.r[i];
+                }
+                v = block_sum_d<double>(v);
+                if (threadIdx.x == 0) {
+                    if (op.type == OP_GNORM64) a.gnorm[g] = v;
+                    else a.gsum[g] = v / (double)(e0 - s0);
+                }
+            }
+            break;
+        case OP_GMEAN_APPLY:
+            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] = (T)((double)L.x[i] - a.gsum[a.gid0[i]]);
+            break;
+        case OP_GMEAN64_APPLY:
+            for (int64_t i = tid; i < a.L0.n; i += nthr) a.L0.x[i] -= a.gsum[a.gid0[i]];
+            break;
+        case OP_TAIL_PRE: {
+            // r_i = b_i + sum of w_iv x_v over the neighbours v outside the tail; those
+            // x_v do not change while the tail colours run (they come last in the order)
+            const int32_t t0 = L.tt0, n = L.n;
+            for (int32_t i = t0 + bid; i < n; i += nb) {
+                if (L.rp[i + 1] - L.rp[i] <= kHugeSolve) continue;
+                tail_pre_row<M_BLK, T>(i, L);
+            }
+            const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+            for (int64_t i = t0 + wid; i < n; i += nwarp) {
+                if (L.rp[i + 1] - L.rp[i] > kHugeSolve) continue;
+                tail_pre_row<M_WARP, T>((int32_t)i, L);
+            }
+            break;
+        }
+        case OP_TAIL_RUN: {
+            // single block: x_i = (r_i + sum over tail neighbours) / a_ii, colour by colour
+            extern __shared__ __align__(16) unsigned char smem[];
+            auto al = [](int64_t v) { return (v + 15) & ~int64_t(15); };
+            const int32_t tn = L.tn, tnc = L.tnc, t0 = L.tt0;
+            unsigned char *p = smem;
+            T *sx = (T *)p; p += al((int64_t)sizeof(T) * tn);
+            T *ss = (T *)p; p += al((int64_t)sizeof(T) * tn);
+            T *sd = (T *)p; p += al((int64_t)sizeof(T) * tn);
+            int32_t *srp = (int32_t *)p; p += al(4 * (int64_t)(tn + 1));
+            int32_t *scb = (int32_t *)p; p += al(4 * (int64_t)(tnc + 1));
+            const int32_t *tcol = L.tcol;
+            const T *tw = L.tw;
+            if (op.a) {  // the local CSR fits: stage it too
+                int32_t *c2 = (int32_t *)p; p += al(4 * (int64_t)L.tnnz);
+                T *w2 = (T *)p;
+                for (int32_t k = threadIdx.x; k < L.tnnz; k += blockDim.x) { c2[k] = L.tcol[k]; w2[k] = L.tw[k]; }
+                tcol = c2;
+                tw = w2;
+            }
+            for (int32_t k = threadIdx.x; k < tn; k += blockDim.x) {
+                sx[k] = L.x[t0 + k];
+                ss[k] = L.r[t0 + k];
+                sd[k] = L.tdeg[k];
+            }
+            for (int32_t k = threadIdx.x; k <= tn; k += blockDim.x) srp[k] = L.trp[k];
+            for (int32_t k = threadIdx.x; k <= tnc; k += blockDim.x) scb[k] = L.tcb[k];
+            __syncthreads();
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+            for (int32_t c = 0; c < tnc; c++) {
+                for (int32_t li = scb[c] + warp; li < scb[c + 1]; li += nw) {
+                    T acc = T(0);
+                    for (int32_t k = srp[li] + lane; k < srp[li + 1]; k += 32) acc += tw[k] * sx[tcol[k]];
+                    acc = warp_allsum(acc);
+                    if (lane == 0 && sd[li] != T(0)) sx[li] = (ss[li] + acc) / sd[li];
+                }
+                __syncthreads();
+            }
+            for (int32_t k = threadIdx.x; k < tn; k += blockDim.x) L.x[t0 + k] = sx[k];
+            break;
+        }
         case OP_SWEEP_SMEM: {
             // single block: stage the level, run a sweeps of all b colours, write x back
             extern __shared__ __align__(16) unsigned char smem[];
@@ -422,12 +402,15 @@ struct Builder {
     lamg_ctx *h;
     int prec;            // 0 = FP64, 1 = FP32
     int adaptive;
+    int groups;          // 0: one right-hand side; G >= 1: 4G interleaved columns
     std::vector<Op> prog;
     std::vector<int32_t> visits;
 
     // a level runs on block 0 alone when it is small and its sweep fits in shared memory
+    // (with several columns: when its work times the column groups is small)
     bool level_sb(int l) const {
         const SolveLevel &V = h->lv[l];
+        if (groups) return (V.nnz + V.n) * groups <= kSBWork;
         const int nc = (int)V.cb.size() / 4;
         const int64_t need = prec == 0 ? smem_bytes<double>(V.n, V.nnz, nc) : smem_bytes<float>(V.n, V.nnz, nc);
         return V.nnz + V.n <= kSBWork && need <= kEngSmem;
@@ -439,7 +422,7 @@ struct Builder {
         if (count <= 0) return;
         const SolveLevel &V = h->lv[l];
         const int nc = (int)V.cb.size() / 4;
-        if (level_sb(l)) {
+        if (level_sb(l) && !groups) {
             const int64_t need = prec == 0 ? smem_bytes<double>(V.n, V.nnz, nc) : smem_bytes<float>(V.n, V.nnz, nc);
             if (need <= kEngSmem) {
                 emit(OP_SWEEP_SMEM, l, count, nc, true);
@@ -456,16 +439,29 @@ struct Builder {
             emit(OP_SWEEP_RUN, l, 0, nc, true);
             return;
         }
+        if (groups) {
+            for (int c = 0; c < nc; c++) emit(OP_SWEEP, l, c, c + 1, false);
+            return;
+        }
+        const int cend = V.tn > 0 ? V.tc0 : nc;   // colours before the tail
         const std::vector<int32_t> &seg = V.seg[prec];
         for (size_t q = 0; q < seg.size(); q += 3) {
-            if (seg[q + 2]) emit(OP_SWEEP_RUN, l, seg[q], seg[q + 1], true);
-            else emit(OP_SWEEP, l, seg[q], seg[q] + 1, false);
+            const int c0 = seg[q], c1 = std::min((int)seg[q + 1], cend);
+            if (c0 >= cend) break;
+            if (seg[q + 2]) emit(OP_SWEEP_RUN, l, c0, c1, true);
+            else emit(OP_SWEEP, l, c0, c0 + 1, false);
+        }
+        if (V.tn > 0) {
+            const int64_t base = prec == 0 ? tail_smem_base<double>(V.tn, V.tnc) : tail_smem_base<float>(V.tn, V.tnc);
+            const int64_t csr = prec == 0 ? tail_smem_csr<double>(V.tnnz) : tail_smem_csr<float>(V.tnnz);
+            emit(OP_TAIL_PRE, l, 0, 0, false);
+            emit(OP_TAIL_RUN, l, base + csr <= kEngSmem ? 1 : 0, 0, true);
         }
     }
     void coarsest(int l) {
         const SolveLevel &V = h->lv[l];
         if (V.dense) {
-            emit(OP_COARSE, l, 0, 0, V.n <= 64);
+            emit(OP_COARSE, l, 0, 0, (int64_t)V.n * std::max(groups, 1) <= 64);
         } else {
             emit(OP_ZERO, l, 0, 0, level_sb(l));
             sweeps(l, h->opt.coarse_sweeps);
@@ -500,6 +496,11 @@ struct Builder {
         visits.assign(h->L, 0);
         if (h->L == 1) coarsest(0);
         else visit(0, 1);
+        if (h->ngraphs > 1) {
+            emit(OP_GMEAN_PART, 0, 0, 0, false);
+            emit(OP_GMEAN_APPLY, 0, 0, 0, false);
+            return;
+        }
         const bool sb = level_sb(0);
         emit(OP_MEAN_PART, 0, 0, 0, sb);
         emit(OP_MEAN_APPLY, 0, 0, 0, sb);
@@ -510,20 +511,25 @@ struct Builder {
 //   kind 0: FP64 cycle + mean + FP64 residual norm (solve step)
 //   kind 1: FP32 refinement step: prep, ir_inner FP32 cycles, update, mean, FP64 residual norm
 //   kind 2: one FP64 cycle + mean only
-void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out) {
-    Builder B{h, kind == 1 ? 1 : 0, adaptive, {}, {}};
-    if (kind == 1) {
+//   kind 3: FP64 residual norm only (initial residual of a batched solve)
+// groups > 0 builds the program for 4*groups interleaved right-hand sides.
+void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out, int groups) {
+    Builder B{h, kind == 1 ? 1 : 0, adaptive, groups, {}, {}};
+    if (kind == 3) {
+        // nothing before the residual
+    } else if (kind == 1) {
         B.emit(OP_IR_PREP, 0, 0, 0, false);
         for (int k = 0; k < std::max(1, h->opt.ir_inner); k++) B.cycle();
         B.emit(OP_IR_UPDATE, 0, 0, 0, false);
-        B.emit(OP_MEAN64_PART, 0, 0, 0, false);
-        B.emit(OP_MEAN64_APPLY, 0, 0, 0, false);
+        B.emit(h->ngraphs > 1 ? OP_GMEAN64_PART : OP_MEAN64_PART, 0, 0, 0, false);
+        B.emit(h->ngraphs > 1 ? OP_GMEAN64_APPLY : OP_MEAN64_APPLY, 0, 0, 0, false);
     } else {
         B.cycle();
     }
     if (kind != 2) {
         B.emit(OP_RES64, 0, 0, 0, false);
         B.emit(OP_NORM64_FIN, 0, 0, 0, false);
+        if (h->ngraphs > 1) B.emit(OP_GNORM64, 0, 0, 0, false);
     }
     if (const char *e = std::getenv("LAMG_ENGINE_STATS"); e && e[0] == '1') {
         int64_t grid_ops = 0, runs = 0, sb_ops = 0;
@@ -535,8 +541,8 @@ void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &ou
                 grid_ops++;
             }
         }
-        std::fprintf(stderr, "lamg-engine kind %d: %zu ops, %lld grid ops, %lld single-block runs (%lld ops), %lld barriers\n",
-                     kind, B.prog.size(), (long long)grid_ops, (long long)runs, (long long)sb_ops,
+        std::fprintf(stderr, "lamg-engine kind %d groups %d: %zu ops, %lld grid ops, %lld single-block runs (%lld ops), %lld barriers\n",
+                     kind, groups, B.prog.size(), (long long)grid_ops, (long long)runs, (long long)sb_ops,
                      (long long)(grid_ops + runs));
     }
     out.resize(B.prog.size() * 5);
@@ -552,38 +558,6 @@ void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &ou
 // ---------------------------------------------------------------------------
 // Runner
 // ---------------------------------------------------------------------------
-
-template <class T>
-static MKLevel<T> describe(lamg_ctx *h, int l, LevelVecs<T> &v, const T *w) {
-    const SolveLevel &V = h->lv[l];
-    MKLevel<T> d{};
-    d.n = V.n;
-    d.nc = (l + 1 < h->L) ? h->lv[l + 1].n : 0;
-    d.rp = V.rp.get();
-    d.col = V.col.get();
-    d.w = w;
-    d.cb = V.cb_dev.get();
-    d.wrows = V.wrows.get();
-    d.brows = V.brows.get();
-    d.nw = V.nw;
-    d.nb = V.nb;
-    d.pagg = V.pagg.get();
-    d.mptr = V.mptr.get();
-    d.mlist = V.mlist.get();
-    d.wagg = V.wagg.get();
-    d.bagg = V.bagg.get();
-    d.nwagg = V.nwagg;
-    d.nbagg = V.nbagg;
-    d.x = v.x.get();
-    d.b = v.b.get();
-    d.r = v.r.get();
-    d.xs0 = v.xs0.get();
-    d.xs1 = v.xs1.get();
-    d.rs0 = v.rs0.get();
-    d.rs1 = v.rs1.get();
-    d.minv = V.minv.get();
-    return d;
-}
 
 void engine_prepare(lamg_ctx *h) {
     if (h->eng_lv64.get()) return;
@@ -626,9 +600,11 @@ void engine_report(lamg_ctx *h) {
     LAMG_CUDA(cudaMemcpy(t.data(), h->eng_optime.get(), h->eng_optime.bytes(), cudaMemcpyDeviceToHost));
     static const char *names[] = {"sweep", "sweep_run", "resid", "restrict", "zero", "coarse", "prolong",
                                   "recomb_dots", "recomb_apply", "mean_part", "mean_apply", "ir_prep",
-                                  "ir_update", "mean64_part", "mean64_apply", "res64", "norm64", "sweep_smem"};
+                                  "ir_update", "mean64_part", "mean64_apply", "res64", "norm64", "sweep_smem",
+                                  "gmean_part", "gmean_apply", "gmean64_part", "gmean64_apply", "gnorm64",
+                                  "tail_pre", "tail_run"};
     for (int l = 0; l < 128; l++)
-        for (int ty = 0; ty < 18; ty++)
+        for (int ty = 0; ty < 25; ty++)
             for (int sb = 0; sb < 2; sb++) {
                 const int key = (l * 32 + ty) * 2 + sb;
                 if (t[2 * key + 1])
@@ -637,6 +613,16 @@ void engine_report(lamg_ctx *h) {
                                  t[2 * key] * 1e-3 / t[2 * key + 1]);
             }
     LAMG_CUDA(cudaMemset(h->eng_optime.get(), 0, h->eng_optime.bytes()));
+}
+
+template <class T>
+static void set_graphs(EngineArgs<T> &a, lamg_ctx *h) {
+    a.ngraphs = h->ngraphs;
+    a.gptr = h->gptr_d.get();
+    a.iperm0 = h->iperm0.get();
+    a.gid0 = h->gid0.get();
+    a.gsum = h->gsum.get();
+    a.gnorm = h->gnorm.get();
 }
 
 // Run program `kind` once on stream s; returns after the launch is queued.
@@ -657,12 +643,14 @@ void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s) 
         EngineArgs<float> a{(const Op *)slot.get(), 0, len, (const MKLevel<float> *)h->eng_lv32.get(), L0,
                             (float)mu, h->eng_part.get(), nullptr, h->scratch.get(), h->eng_bar.get(),
                             h->eng_err.get(), h->eng_optime.get()};
+        set_graphs(a, h);
         void *args[] = {&a};
         LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<float>, grid, block, args, kEngSmem, s));
     } else {
         EngineArgs<double> a{(const Op *)slot.get(), 0, len, (const MKLevel<double> *)h->eng_lv64.get(), L0, mu,
                              h->eng_part.get(), nullptr, h->scratch.get(), h->eng_bar.get(), h->eng_err.get(),
                              h->eng_optime.get()};
+        set_graphs(a, h);
         void *args[] = {&a};
         LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<double>, grid, block, args, kEngSmem, s));
     }
@@ -744,6 +732,7 @@ int32_t *engine_run_noalloc(lamg_ctx *h, int adaptive, double mu, cudaStream_t s
     EngineArgs<double> a{(const Op *)h->eng_prog[k].get(), 0, h->eng_len[k],
                          (const MKLevel<double> *)h->eng_lv64.get(), L0, mu, part, nullptr, h->scratch.get(),
                          bar, err, nullptr};
+    set_graphs(a, h);
     void *args[] = {&a};
     LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<double>, dim3(h->eng_grid), dim3(kEngThreads), args,
                                           kEngSmem, s));

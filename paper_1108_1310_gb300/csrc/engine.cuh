@@ -1,0 +1,216 @@
+// engine.cuh -- definitions shared by the single- and multi-right-hand-side
+// cycle engines: level descriptors, the op codes of a cycle program, the
+// bounded grid barrier and the fixed-order block reductions.
+#pragma once
+
+#include "solve_rows.cuh"
+
+namespace lamg {
+
+constexpr int kEngThreads = 1024;
+constexpr long long kMaxSpins = 1ll << 23;  // about a second of polling
+
+template <class T>
+struct MKLevel {
+    int32_t n, nc;
+    const int32_t *rp, *col;
+    const T *w;
+    const int32_t *cb;
+    const int32_t *wrows, *brows;
+    int32_t nw, nb;
+    const int32_t *pagg, *mptr, *mlist, *wagg, *bagg;
+    int32_t nwagg, nbagg;
+    T *x, *b, *r, *xs0, *xs1, *rs0, *rs1;
+    const double *minv;
+    // tail colours (tn == 0: none)
+    int32_t tt0, tn, tnc, tnnz;
+    const int32_t *trp, *tcol, *tcb;
+    const T *tw, *tdeg;
+};
+
+enum : int32_t {
+    OP_SWEEP = 0,     // level, colour a (all blocks)
+    OP_SWEEP_RUN,     // level, colours a..b-1 (single block, __syncthreads between colours)
+    OP_RESID,         // r = b - A x; a >= 0: also save x, r into slot a (recombination)
+    OP_RESTRICT,      // b^c = mu P^T r, x^c = 0
+    OP_ZERO,          // x = 0 (coarsest solved by sweeps)
+    OP_COARSE,        // x = M^-1 b (dense coarsest, FP64 arithmetic)
+    OP_PROLONG,       // x += P x^c
+    OP_RECOMB_DOTS,   // partial dot products, theta = a
+    OP_RECOMB_APPLY,  // alpha from the partials, y = x + sum alpha_i (x_i - x)
+    OP_MEAN_PART,     // partial sums of x (cycle precision)
+    OP_MEAN_APPLY,    // x -= mean
+    OP_IR_PREP,       // b32 = (float) r64, x32 = 0
+    OP_IR_UPDATE,     // x64 += (double) x32
+    OP_MEAN64_PART,   // partial sums of x64
+    OP_MEAN64_APPLY,  // x64 -= mean
+    OP_RES64,         // r64 = b64 - A x64 (FP64) and partial sums of r64^2
+    OP_NORM64_FIN,    // out[0] = sum of the partials
+    OP_SWEEP_SMEM,    // level, a = sweeps: whole sweeps from shared memory (single block)
+    // union of several graphs: level-1 projection and norms per graph
+    OP_GMEAN_PART,    // gsum[g] = mean of x over graph g (cycle precision, level 1)
+    OP_GMEAN_APPLY,   // x -= gsum[graph of the row]
+    OP_GMEAN64_PART,  // same on the FP64 iterate
+    OP_GMEAN64_APPLY,
+    OP_GNORM64,       // gnorm[g] = ||r64 on graph g||^2
+    OP_TAIL_PRE,      // tail rows: r_i = b_i + sum over neighbours outside the tail (grid)
+    OP_TAIL_RUN,      // tail colours in order from shared memory (single block)
+};
+
+constexpr int kEngSmem = 200 * 1024;  // dynamic shared memory of the engine block
+
+// bytes the shared-memory sweep needs for a level: rp, col, w, x, b, colour bounds
+template <class T>
+__host__ __device__ __forceinline__ int64_t smem_bytes(int64_t n, int64_t nnz, int64_t ncol) {
+    auto al = [](int64_t b) { return (b + 15) & ~int64_t(15); };
+    return al(4 * (n + 1)) + al(4 * nnz) + al((int64_t)sizeof(T) * nnz) + 2 * al((int64_t)sizeof(T) * n) +
+           al(16 * ncol);
+}
+
+struct Op {
+    int32_t type, level, a, b, sb;
+};
+
+// colour count of a level is carried in the op (b) for the shared-memory sweep
+
+template <class T>
+struct EngineArgs {
+    const Op *prog;
+    int32_t begin, end;
+    const MKLevel<T> *lv;
+    MKLevel<double> L0;     // FP64 finest level (outer refinement / residual)
+    T mu;
+    double *part;           // gridDim * 8 partial sums
+    double *alpha;          // 2 per level
+    double *out;            // results
+    unsigned int *bar;      // barrier: count, generation
+    int32_t *err;
+    unsigned long long *optime;  // optional per (level, op, single-block) time and count
+    // union of several graphs (ngraphs > 1 only)
+    int32_t ngraphs;
+    const int64_t *gptr;     // level-1 natural node range of each graph
+    const int32_t *iperm0;   // natural level-1 id -> permuted row
+    const int32_t *gid0;     // graph of each permuted level-1 row
+    double *gsum, *gnorm;    // per-graph means, ||r64||^2
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier (bounded spin)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err) {
+    __shared__ int bad;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bad = 0;
+        volatile unsigned int *vgen = bar + 1;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if ((++spins & 63) == 0) {
+                    if (*(volatile int32_t *)err) { bad = 1; break; }
+                    if (spins > kMaxSpins) { atomicExch(err, 1); bad = 1; break; }
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return bad == 0;
+}
+
+template <class T>
+__device__ __forceinline__ double block_sum_d(double v) {
+    __shared__ double sh[32];
+    v = warp_allsum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; k++) t += sh[k];
+    __syncthreads();
+    return t;  // in every thread
+}
+
+// sum of the nb block partials at slot k (same order in every block)
+__device__ __forceinline__ double sum_partials(const double *part, int nb, int k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * 8 + k];
+    return block_sum_d<double>(v);
+}
+
+template <class T>
+inline MKLevel<T> describe(lamg_ctx *h, int l, LevelVecs<T> &v, const T *w) {
+    const SolveLevel &V = h->lv[l];
+    MKLevel<T> d{};
+    d.n = V.n;
+    d.nc = (l + 1 < h->L) ? h->lv[l + 1].n : 0;
+    d.rp = V.rp.get();
+    d.col = V.col.get();
+    d.w = w;
+    d.cb = V.cb_dev.get();
+    d.wrows = V.wrows.get();
+    d.brows = V.brows.get();
+    d.nw = V.nw;
+    d.nb = V.nb;
+    d.pagg = V.pagg.get();
+    d.mptr = V.mptr.get();
+    d.mlist = V.mlist.get();
+    d.wagg = V.wagg.get();
+    d.bagg = V.bagg.get();
+    d.nwagg = V.nwagg;
+    d.nbagg = V.nbagg;
+    d.x = v.x.get();
+    d.b = v.b.get();
+    d.r = v.r.get();
+    d.xs0 = v.xs0.get();
+    d.xs1 = v.xs1.get();
+    d.rs0 = v.rs0.get();
+    d.rs1 = v.rs1.get();
+    d.minv = V.minv.get();
+    d.tt0 = V.tt0;
+    d.tn = V.tn;
+    d.tnc = V.tnc;
+    d.tnnz = (int32_t)V.tnnz;
+    d.trp = V.trp.get();
+    d.tcol = V.tcol.get();
+    d.tcb = V.tcb.get();
+    if constexpr (sizeof(T) == 8) {
+        d.tw = (const T *)V.tw64.get();
+        d.tdeg = (const T *)V.tdeg64.get();
+    } else {
+        d.tw = (const T *)V.tw32.get();
+        d.tdeg = (const T *)V.tdeg32.get();
+    }
+    return d;
+}
+
+// shared memory of the tail run: x, s, d (T each), trp, tcb, and (when it fits)
+// the tail block's local CSR
+template <class T>
+__host__ __device__ __forceinline__ int64_t tail_smem_base(int64_t tn, int64_t tnc) {
+    auto al = [](int64_t b) { return (b + 15) & ~int64_t(15); };
+    return 3 * al((int64_t)sizeof(T) * tn) + al(4 * (tn + 1)) + al(4 * (tnc + 1));
+}
+template <class T>
+__host__ __device__ __forceinline__ int64_t tail_smem_csr(int64_t tnnz) {
+    auto al = [](int64_t b) { return (b + 15) & ~int64_t(15); };
+    return al(4 * tnnz) + al((int64_t)sizeof(T) * tnnz);
+}
+
+}  // namespace lamg

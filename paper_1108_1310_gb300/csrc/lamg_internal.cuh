@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -138,6 +139,15 @@ struct SolveLevel {
     DBuf<int32_t> mptr, mlist;     // members of each coarse id (permuted fine ids)
     DBuf<int32_t> wagg, bagg;      // coarse ids whose member lists are warp / block tier
     int32_t nwagg = 0, nbagg = 0;
+    // tail colours (power-law levels: many colours of a few long hub rows at the
+    // end of the colour order): rows tt0 .. n-1, colours tc0 .. ncolours-1.  The
+    // sweep splits each tail row into its part outside the tail (fixed while the
+    // tail colours run) and its part inside (trp/tcol local CSR, tw weights).
+    int32_t tc0 = -1, tt0 = 0, tn = 0, tnc = 0;
+    int64_t tnnz = 0;
+    DBuf<int32_t> trp, tcol, tcb;  // local CSR of the tail block, tail colour bounds (local rows)
+    DBuf<double> tw64, tdeg64;     // weights and full weighted degrees of tail rows
+    DBuf<float> tw32, tdeg32;
     // coarsest level
     int32_t dense = 0;
     DBuf<double> minv;             // (A + 11^T/n)^-1, n x n, if dense
@@ -147,6 +157,22 @@ struct SolveLevel {
 template <class T>
 struct LevelVecs {
     DBuf<T> x, b, r, xs0, xs1, rs0, rs1;
+};
+
+// Workspace of batched solves: level vectors of n x ld interleaved columns
+// (ld = 4 * groups), their descriptors, programs and engine scratch.
+struct BatchState {
+    int32_t groups = 0, ld = 0, grid = 0;
+    std::vector<LevelVecs<double>> v64;
+    std::vector<LevelVecs<float>> v32;
+    DBuf<double> r64;              // FP64 outer residual, n x ld (permuted)
+    DBuf<double> out;              // per-column results, 4 x ld
+    DBuf<char> lv64, lv32;         // level descriptors (MKLevel)
+    DBuf<double> part;             // grid x 8 x ld partial sums
+    DBuf<unsigned int> bar;
+    DBuf<int32_t> err;
+    DBuf<int32_t> prog[6];         // (FP64 step, FP32-IR step, residual only) x adaptive
+    int32_t len[6] = {0, 0, 0, 0, 0, 0};
 };
 
 struct Hierarchy;
@@ -183,6 +209,14 @@ struct lamg_ctx {
     int64_t prof_count = 0;
     int64_t prof_bytes = 0;
     lamg_stats last{};
+    std::unique_ptr<lamg::BatchState> mr;   // batched-solve workspace (lazily built)
+    // block-diagonal union of several graphs (ngraphs == 1: one connected graph)
+    int32_t ngraphs = 1;
+    std::vector<int64_t> gptr;              // host: level-1 node range of each graph
+    lamg::DBuf<int64_t> gptr_d;
+    lamg::DBuf<int32_t> iperm0;             // natural level-1 id -> permuted row
+    lamg::DBuf<int32_t> gid0, gidnat;       // graph of each permuted / natural level-1 row
+    lamg::DBuf<double> gsum, gnorm, gstat;  // per-graph means, ||r||^2, and b statistics (3 per graph)
 };
 
 namespace lamg {
@@ -191,7 +225,7 @@ namespace lamg {
 void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32_t *col,
                      const void *w, int32_t w_is_fp32, cudaStream_t s);
 void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
-                    int32_t w_is_fp32, cudaStream_t s);
+                    int32_t w_is_fp32, cudaStream_t s, int32_t ngraphs = 1, const int64_t *gptr = nullptr);
 
 // single-block threshold of the cycle engine (n + nnz of a level)
 constexpr int64_t kSBWork = 16384;
@@ -201,16 +235,18 @@ void engine_prepare(lamg_ctx *h);
 void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s);
 bool engine_failed(lamg_ctx *h, cudaStream_t s);
 void engine_report(lamg_ctx *h);
-void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out);
+void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out, int groups = 0);
 bool engine_noalloc_ready(lamg_ctx *h, int adaptive);
 int32_t *engine_run_noalloc(lamg_ctx *h, int adaptive, double mu, cudaStream_t s);
 
 // solve.cu
 void build_solve_layout(lamg_ctx *h, cudaStream_t s);
+void build_graph_maps(lamg_ctx *h, cudaStream_t s);
 void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_precision p,
                   cudaStream_t s, lamg_stats *st);
 void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X, int64_t ld,
                           double tol, lamg_precision p, cudaStream_t s, lamg_stats *st);
+void prepare_solve(lamg_ctx *h);
 void cycle_device(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s);
 void cycle_device_noalloc(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s);
 void adjoint_device(lamg_ctx *h, const double *x, const double *g, double *lambda,

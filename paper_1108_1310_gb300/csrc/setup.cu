@@ -342,8 +342,37 @@ __global__ void k_uf_roots(int32_t *parent, int64_t n, unsigned long long *roots
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(roots, c);
 }
 
+// graph of node u in a union: the g with gptr[g] <= u < gptr[g+1]
+__device__ __forceinline__ int32_t graph_of(const int64_t *__restrict__ gptr, int32_t G, int64_t u) {
+    int32_t lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (gptr[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// every entry must stay inside its row's graph
+__global__ void k_graph_cross(int64_t n, int64_t nnz, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const int64_t *__restrict__ gptr, int32_t G, int32_t *flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnz) return;
+    const int64_t u = row_of(rp, n, i);
+    if (graph_of(gptr, G, u) != graph_of(gptr, G, col[i])) atomicOr(flags, VF_ARG);
+}
+
+__global__ void k_graph_ids(int64_t n, const int64_t *__restrict__ gptr, int32_t G, int32_t *__restrict__ gid) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) gid[u] = graph_of(gptr, G, u);
+}
+
+void graph_ids(int64_t n, const int64_t *gptr_dev, int32_t G, int32_t *gid, cudaStream_t s) {
+    k_graph_ids<<<ceil_div(n, 256), 256, 0, s>>>(n, gptr_dev, G, gid);
+    LAMG_CHECK_LAUNCH();
+}
+
 void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
-                    int32_t w_is_fp32, cudaStream_t s) {
+                    int32_t w_is_fp32, cudaStream_t s, int32_t ngraphs, const int64_t *gptr) {
     int64_t rp_n[2];
     LAMG_CUDA(cudaMemcpyAsync(&rp_n[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     LAMG_CUDA(cudaMemcpyAsync(&rp_n[1], row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -382,8 +411,19 @@ void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const
     }
     k_uf_roots<<<ceil_div(n, 256), 256, 0, s>>>(parent.get(), n, roots.get());
     LAMG_CHECK_LAUNCH();
+    if (ngraphs > 1 && nnz) {
+        // a union: no entry may join two graphs; then #components == #graphs iff each is connected
+        Tmp<int64_t> gp(ngraphs + 1, s);
+        LAMG_CUDA(cudaMemcpyAsync(gp.get(), gptr, sizeof(int64_t) * (ngraphs + 1), cudaMemcpyHostToDevice, s));
+        k_graph_cross<<<ceil_div(nnz, 256), 256, 0, s>>>(n, nnz, row_ptr, col, gp.get(), ngraphs, flags.get());
+        LAMG_CHECK_LAUNCH();
+        LAMG_REQUIRE(!(read_scalar(flags.get(), s) & VF_ARG), LAMG_ERR_ARG, "an edge joins two graphs of the union");
+    }
     unsigned long long r = read_scalar(roots.get(), s);
-    LAMG_REQUIRE(r == 1, LAMG_ERR_DISCONNECTED, "graph is not connected");
+    if (ngraphs > 1)
+        LAMG_REQUIRE(r == (unsigned long long)ngraphs, LAMG_ERR_DISCONNECTED, "a graph of the union is not connected");
+    else
+        LAMG_REQUIRE(r == 1, LAMG_ERR_DISCONNECTED, "graph is not connected");
 }
 
 // ---------------------------------------------------------------------------
@@ -723,6 +763,9 @@ __device__ __forceinline__ void tv_update(int32_t u, const int32_t *__restrict__
                                           const double *__restrict__ w, const double *__restrict__ diag, int32_t K,
                                           double *__restrict__ X) {
     const int32_t s = rp[u], e = rp[u + 1];
+    // an isolated node (a whole graph of a union, coarsened to one node) keeps its TVs;
+    // such a row has no entries, so it is always in the thread tier
+    if (M == M_THR && e == s) return;
     double acc[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) acc[k] = 0.0;

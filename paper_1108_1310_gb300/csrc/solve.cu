@@ -13,6 +13,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
+#include <vector>
 
 #include "solve_rows.cuh"
 
@@ -107,8 +109,11 @@ __global__ void k_pagg(const int32_t *__restrict__ perm, const int32_t *__restri
 // inverse is formed by Gauss-Jordan elimination of [M | I] without pivoting
 // (valid for SPD M), one all-SM launch per pivot, double-buffered so that
 // every launch reads the previous step only.
+// With several components K (a union of graphs), M = A + sum_K 1_K 1_K^T / n_K:
+// comp[i] is the component of row i and inv[k] = 1 / n_k (comp == NULL: one).
 __global__ void k_dense_assemble(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                 const double *__restrict__ w, double *__restrict__ G) {
+                                 const double *__restrict__ w, double *__restrict__ G,
+                                 const int32_t *__restrict__ comp, const double *__restrict__ inv) {
     // G is n x 2n, row-major: [M | I]
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)n * 2 * n) return;
@@ -117,7 +122,7 @@ __global__ void k_dense_assemble(int32_t n, const int32_t *__restrict__ rp, cons
     if (j >= n) {
         v = (j - n == i) ? 1.0 : 0.0;
     } else {
-        v = 1.0 / (double)n;
+        v = comp ? (comp[i] == comp[j] ? inv[comp[i]] : 0.0) : 1.0 / (double)n;
         if (i == j) {
             double d = 0.0;
             for (int32_t e = rp[i]; e < rp[i + 1]; e++) d += w[e];
@@ -152,6 +157,78 @@ __global__ void k_dense_extract(int32_t n, const double *__restrict__ G, double 
     if (q >= (int64_t)n * n) return;
     const int32_t i = (int32_t)(q / n), j = (int32_t)(q % n);
     Minv[q] = G[(int64_t)i * 2 * n + n + j];
+}
+
+// Tail colours of a level: the longest suffix of colours that each hold at most
+// kTailRows rows (and together at most kTailMax rows), when it has at least
+// kTailMinColours colours.  On power-law levels these are the hubs, which
+// need many colours among themselves.  Builds the tail block's local CSR
+// (entries whose column is also a tail row) and the full weighted degrees.
+constexpr int32_t kTailRows = 64, kTailMax = 4096, kTailMinColours = 4;
+
+static void build_tail(SolveLevel &V, int ncol, cudaStream_t s) {
+    V.tc0 = -1;
+    V.tn = 0;
+    const int32_t n = V.n;
+    if (ncol < kTailMinColours + 1) return;
+    auto rows = [&](int c) { return V.cb[4 * c + 3] - V.cb[4 * c]; };
+    int c0 = ncol;
+    while (c0 > 1 && rows(c0 - 1) <= kTailRows && n - V.cb[4 * (c0 - 1)] <= kTailMax) c0--;
+    if (ncol - c0 < kTailMinColours) return;
+    const int32_t t0 = V.cb[4 * c0], tn = n - t0;
+    std::vector<int32_t> hrp(tn + 1);
+    LAMG_CUDA(cudaMemcpyAsync(hrp.data(), V.rp.get() + t0, sizeof(int32_t) * (tn + 1), cudaMemcpyDeviceToHost, s));
+    LAMG_CUDA(cudaStreamSynchronize(s));
+    const int64_t e0 = hrp[0], ne = (int64_t)hrp[tn] - e0;
+    std::vector<int32_t> hcol(ne);
+    std::vector<double> hw(ne);
+    if (ne) {
+        LAMG_CUDA(cudaMemcpyAsync(hcol.data(), V.col.get() + e0, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, s));
+        LAMG_CUDA(cudaMemcpyAsync(hw.data(), V.w64.get() + e0, sizeof(double) * ne, cudaMemcpyDeviceToHost, s));
+        LAMG_CUDA(cudaStreamSynchronize(s));
+    }
+    std::vector<int32_t> trp(tn + 1, 0), tcol, tcb(ncol - c0 + 1);
+    std::vector<double> tw, deg(tn);
+    std::vector<float> tw32, deg32(tn);
+    for (int32_t i = 0; i < tn; i++) {
+        double d = 0.0;
+        float d32 = 0.f;
+        for (int64_t k = hrp[i] - e0; k < hrp[i + 1] - e0; k++) {
+            d += hw[k];
+            d32 += (float)hw[k];
+            if (hcol[k] >= t0) {
+                tcol.push_back(hcol[k] - t0);
+                tw.push_back(hw[k]);
+                tw32.push_back((float)hw[k]);
+            }
+        }
+        deg[i] = d;
+        deg32[i] = d32;
+        trp[i + 1] = (int32_t)tcol.size();
+    }
+    for (int c = c0; c <= ncol; c++) tcb[c - c0] = (c < ncol ? V.cb[4 * c] : n) - t0;
+    V.tc0 = c0;
+    V.tt0 = t0;
+    V.tn = tn;
+    V.tnc = ncol - c0;
+    V.tnnz = (int64_t)tcol.size();
+    V.trp.alloc(tn + 1);
+    V.tcb.alloc(tcb.size());
+    V.tcol.alloc(tcol.size());
+    V.tw64.alloc(tw.size());
+    V.tw32.alloc(tw32.size());
+    V.tdeg64.alloc(tn);
+    V.tdeg32.alloc(tn);
+    LAMG_CUDA(cudaMemcpyAsync(V.trp.get(), trp.data(), sizeof(int32_t) * (tn + 1), cudaMemcpyHostToDevice, s));
+    LAMG_CUDA(cudaMemcpyAsync(V.tcb.get(), tcb.data(), sizeof(int32_t) * tcb.size(), cudaMemcpyHostToDevice, s));
+    if (!tcol.empty()) {
+        LAMG_CUDA(cudaMemcpyAsync(V.tcol.get(), tcol.data(), sizeof(int32_t) * tcol.size(), cudaMemcpyHostToDevice, s));
+        LAMG_CUDA(cudaMemcpyAsync(V.tw64.get(), tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice, s));
+        LAMG_CUDA(cudaMemcpyAsync(V.tw32.get(), tw32.data(), sizeof(float) * tw32.size(), cudaMemcpyHostToDevice, s));
+    }
+    LAMG_CUDA(cudaMemcpyAsync(V.tdeg64.get(), deg.data(), sizeof(double) * tn, cudaMemcpyHostToDevice, s));
+    LAMG_CUDA(cudaMemcpyAsync(V.tdeg32.get(), deg32.data(), sizeof(float) * tn, cudaMemcpyHostToDevice, s));
+    LAMG_CUDA(cudaStreamSynchronize(s));
 }
 
 void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
@@ -227,6 +304,7 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
                 }
             }
         }
+        build_tail(V, S.ncolours, s);
         Tmp<uint8_t> f(n, s);
         V.wrows.alloc(n);
         V.brows.alloc(n);
@@ -276,7 +354,36 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         Tmp<int32_t> err(1, s);
         LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
         const int64_t tot = (int64_t)n * 2 * n;
-        k_dense_assemble<<<ceil_div(tot, 256), 256, 0, s>>>(n, C.rp.get(), C.col.get(), C.w64.get(), G.get());
+        // connected components of the coarsest graph (host BFS; n <= dense_max)
+        std::vector<int32_t> hrp(n + 1), hcol(C.nnz), comp(n, -1);
+        LAMG_CUDA(cudaMemcpyAsync(hrp.data(), C.rp.get(), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+        if (C.nnz)
+            LAMG_CUDA(cudaMemcpyAsync(hcol.data(), C.col.get(), sizeof(int32_t) * C.nnz, cudaMemcpyDeviceToHost, s));
+        LAMG_CUDA(cudaStreamSynchronize(s));
+        int32_t ncomp = 0;
+        std::vector<int32_t> queue(n);
+        std::vector<double> inv;
+        for (int32_t s0 = 0; s0 < n; s0++) {
+            if (comp[s0] >= 0) continue;
+            int32_t head = 0, tail = 0;
+            comp[s0] = ncomp;
+            queue[tail++] = s0;
+            while (head < tail) {
+                const int32_t u = queue[head++];
+                for (int32_t e = hrp[u]; e < hrp[u + 1]; e++)
+                    if (comp[hcol[e]] < 0) { comp[hcol[e]] = ncomp; queue[tail++] = hcol[e]; }
+            }
+            inv.push_back(1.0 / (double)tail);
+            ncomp++;
+        }
+        Tmp<int32_t> dcomp(ncomp > 1 ? n : 0, s);
+        Tmp<double> dinv(ncomp > 1 ? ncomp : 0, s);
+        if (ncomp > 1) {
+            LAMG_CUDA(cudaMemcpyAsync(dcomp.get(), comp.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            LAMG_CUDA(cudaMemcpyAsync(dinv.get(), inv.data(), sizeof(double) * ncomp, cudaMemcpyHostToDevice, s));
+        }
+        k_dense_assemble<<<ceil_div(tot, 256), 256, 0, s>>>(n, C.rp.get(), C.col.get(), C.w64.get(), G.get(),
+                                                            ncomp > 1 ? dcomp.get() : nullptr, dinv.get());
         LAMG_CHECK_LAUNCH();
         double *a = G.get(), *bb = H.get();
         for (int32_t k = 0; k < n; k++) {
@@ -349,6 +456,66 @@ __global__ void k_scatter_perm(int32_t n, const int32_t *__restrict__ perm, cons
 }
 
 // ---------------------------------------------------------------------------
+// Union of several graphs: level-1 maps for the per-graph projection and norms
+// ---------------------------------------------------------------------------
+
+__global__ void k_invert_perm(int32_t n, const int32_t *__restrict__ perm, int32_t *__restrict__ iperm) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) iperm[perm[i]] = i;
+}
+
+__global__ void k_gather_i32(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ src,
+                             int32_t *__restrict__ dst) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[perm[i]];
+}
+
+void graph_ids(int64_t n, const int64_t *gptr_dev, int32_t G, int32_t *gid, cudaStream_t s);
+
+void build_graph_maps(lamg_ctx *h, cudaStream_t s) {
+    const int32_t n = h->lv[0].n, G = h->ngraphs;
+    h->gptr_d.alloc(G + 1);
+    LAMG_CUDA(cudaMemcpyAsync(h->gptr_d.get(), h->gptr.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, s));
+    h->gidnat.alloc(n);
+    graph_ids(n, h->gptr_d.get(), G, h->gidnat.get(), s);
+    h->iperm0.alloc(n);
+    k_invert_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, h->lv[0].perm.get(), h->iperm0.get());
+    LAMG_CHECK_LAUNCH();
+    h->gid0.alloc(n);
+    k_gather_i32<<<ceil_div(n, 256), 256, 0, s>>>(n, h->lv[0].perm.get(), h->gidnat.get(), h->gid0.get());
+    LAMG_CHECK_LAUNCH();
+    h->gsum.alloc(G);
+    h->gnorm.alloc(G);
+    h->gstat.alloc(3 * (size_t)G);
+    LAMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// Per graph g (one block per graph, fixed order): over natural ids u in
+// [gptr[g], gptr[g+1]) of v[map ? map[u] : u]: out[g] = sum, out[G+g] = sum |.|,
+// out[2G+g] = sum of squares.
+__global__ void __launch_bounds__(1024) k_graph_stats(int32_t G, const int64_t *__restrict__ gptr,
+                                                      const int32_t *__restrict__ map, const double *__restrict__ v,
+                                                      double *__restrict__ out) {
+    for (int32_t g = blockIdx.x; g < G; g += gridDim.x) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int64_t u = gptr[g] + threadIdx.x; u < gptr[g + 1]; u += blockDim.x) {
+            const double t = v[map ? map[u] : u];
+            a += t;
+            b += fabs(t);
+            c += t * t;
+        }
+        a = block_sum(a);
+        b = block_sum(b);
+        c = block_sum(c);
+        if (threadIdx.x == 0) {
+            out[g] = a;
+            out[G + g] = b;
+            out[2 * G + g] = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Solve drivers
 // ---------------------------------------------------------------------------
 
@@ -375,6 +542,8 @@ static void prepare(lamg_ctx *h) {
     if (!h->host_pinned) LAMG_CUDA(cudaMallocHost((void **)&h->host_pinned, 16 * sizeof(double)));
     engine_prepare(h);
 }
+
+void prepare_solve(lamg_ctx *h) { prepare(h); }
 
 // Engine launch of one step with optional CUDA-event timing of the launch.
 static void run_step(lamg_ctx *h, int kind, int adaptive, cudaStream_t s) {
@@ -453,6 +622,26 @@ static double resnorm64(lamg_ctx *h, cudaStream_t s) {
     return std::sqrt(read_scalar(h->scratch.get() + SC_NORM, s));
 }
 
+// per-graph sum, sum |.|, sum of squares of a level-1 vector (map: natural -> stored index)
+static void graph_stats(lamg_ctx *h, const double *v, const int32_t *map, cudaStream_t s, std::vector<double> &out) {
+    const int32_t G = h->ngraphs;
+    k_graph_stats<<<std::min(G, 4096), 1024, 0, s>>>(G, h->gptr_d.get(), map, v, h->gstat.get());
+    LAMG_CHECK_LAUNCH();
+    out.resize(3 * (size_t)G);
+    LAMG_CUDA(cudaMemcpyAsync(out.data(), h->gstat.get(), sizeof(double) * 3 * G, cudaMemcpyDeviceToHost, s));
+    LAMG_CUDA(cudaStreamSynchronize(s));
+}
+
+__global__ void k_center_graphs(int32_t n, const double *__restrict__ g, double *__restrict__ out,
+                                const int32_t *__restrict__ gid, const int64_t *__restrict__ gptr,
+                                const double *__restrict__ sums) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int32_t k = gid[i];
+        out[i] = g[i] - sums[k] / (double)(gptr[k + 1] - gptr[k]);
+    }
+}
+
 void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_precision p, cudaStream_t s,
                   lamg_stats *st) {
     auto t0 = std::chrono::steady_clock::now();
@@ -464,22 +653,52 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
     LAMG_CHECK_LAUNCH();
     k_gather_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, V0.perm.get(), x, xb);
     LAMG_CHECK_LAUNCH();
+    const int32_t G = h->ngraphs;
     double sb, ab, bn;
-    rhs_norms(h, bb, s, sb, ab, bn);
-    LAMG_REQUIRE(std::fabs(sb) <= 1e-10 * (ab > 0 ? ab : 1.0), LAMG_ERR_RHS_NOT_ZERO_SUM,
-                 "right-hand side is not zero-sum");
+    std::vector<double> gbn(G), grn(G), gst;
+    if (G > 1) {
+        // a union of graphs: b must be zero-sum on every graph; each graph has its own ||b_g||
+        graph_stats(h, bb, h->iperm0.get(), s, gst);
+        bn = 0.0;
+        for (int32_t g = 0; g < G; g++) {
+            LAMG_REQUIRE(std::fabs(gst[g]) <= 1e-10 * (gst[G + g] > 0 ? gst[G + g] : 1.0),
+                         LAMG_ERR_RHS_NOT_ZERO_SUM, "right-hand side is not zero-sum on graph " + std::to_string(g));
+            gbn[g] = std::sqrt(gst[2 * G + g]);
+            bn += gst[2 * G + g];
+        }
+        bn = std::sqrt(bn);
+    } else {
+        rhs_norms(h, bb, s, sb, ab, bn);
+        LAMG_REQUIRE(std::fabs(sb) <= 1e-10 * (ab > 0 ? ab : 1.0), LAMG_ERR_RHS_NOT_ZERO_SUM,
+                     "right-hand side is not zero-sum");
+    }
     const double r0 = resnorm64(h, s);
     double rn = r0;
+    if (G > 1) {
+        graph_stats(h, h->r64.get(), h->iperm0.get(), s, gst);
+        for (int32_t g = 0; g < G; g++) grn[g] = std::sqrt(gst[2 * G + g]);
+    }
+    // stopping test: ||r|| <= tol ||b||, on every graph of a union
+    auto pending = [&]() {
+        if (G == 1) return rn > tol * bn;
+        for (int32_t g = 0; g < G; g++)
+            if (!(grn[g] <= tol * gbn[g])) return true;
+        return false;
+    };
     const int adaptive = h->opt.adaptive;
     const int kind = p == LAMG_FP64 ? 0 : 1;
     const int per_step = p == LAMG_FP64 ? 1 : std::max(1, h->opt.ir_inner);
     int steps = 0, cycles = 0;
-    while (rn > tol * bn && cycles < h->opt.max_cycles) {
+    std::vector<double> gn2(G);
+    while (pending() && cycles < h->opt.max_cycles) {
         run_step(h, kind, adaptive, s);
         LAMG_CUDA(cudaMemcpyAsync(h->host_pinned, h->scratch.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (G > 1)
+            LAMG_CUDA(cudaMemcpyAsync(gn2.data(), h->gnorm.get(), sizeof(double) * G, cudaMemcpyDeviceToHost, s));
         LAMG_CUDA(cudaStreamSynchronize(s));
         after_step(h, kind, s);
         rn = std::sqrt(*h->host_pinned);
+        for (int32_t g = 0; g < G && G > 1; g++) grn[g] = std::sqrt(gn2[g]);
         steps++;
         cycles += per_step;
         if (!(rn == rn)) break;  // NaN: stop
@@ -494,10 +713,14 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
     L.cycles = cycles;
     L.outer_steps = steps;
     L.rel_res = bn > 0 ? rn / bn : 0.0;
+    if (G > 1) {
+        L.rel_res = 0.0;
+        for (int32_t g = 0; g < G; g++) L.rel_res = std::max(L.rel_res, gbn[g] > 0 ? grn[g] / gbn[g] : 0.0);
+    }
     L.acf = (cycles > 0 && r0 > 0 && rn > 0) ? std::pow(rn / r0, 1.0 / cycles) : 0.0;
     L.t_setup_s = h->t_setup_s;
     L.t_solve_s = std::chrono::duration<double>(t1 - t0).count();
-    L.status = (rn <= tol * bn) ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
+    L.status = (rn == rn && !pending()) ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
     if (st) *st = L;
     LAMG_REQUIRE(rn == rn, LAMG_ERR_NOT_CONVERGED, "solve produced NaN");
     if (L.status != LAMG_OK) throw Error{LAMG_ERR_NOT_CONVERGED, "max_cycles reached before tol"};
@@ -565,9 +788,18 @@ void adjoint_device(lamg_ctx *h, const double *x, const double *g, double *lambd
     const int32_t n = h->lv[0].n;
     Tmp<double> gz(n, s);
     double *out = h->scratch.get() + SC_NORM + 8;
-    reduce_to(g, n, 0, h->scratch.get() + SC_PART, out, s);
-    k_center<<<ceil_div(n, 256), 256, 0, s>>>(n, g, gz.get(), out);
-    LAMG_CHECK_LAUNCH();
+    if (h->ngraphs > 1) {
+        // project g to zero mean on every graph of the union
+        std::vector<double> gst;
+        graph_stats(h, g, nullptr, s, gst);
+        k_center_graphs<<<ceil_div(n, 256), 256, 0, s>>>(n, g, gz.get(), h->gidnat.get(), h->gptr_d.get(),
+                                                         h->gstat.get());
+        LAMG_CHECK_LAUNCH();
+    } else {
+        reduce_to(g, n, 0, h->scratch.get() + SC_PART, out, s);
+        k_center<<<ceil_div(n, 256), 256, 0, s>>>(n, g, gz.get(), out);
+        LAMG_CHECK_LAUNCH();
+    }
     LAMG_CUDA(cudaMemsetAsync(lambda, 0, sizeof(double) * n, s));
     solve_device(h, gz.get(), lambda, tol, p, s, st);
     if (dw && m > 0) {
@@ -575,11 +807,6 @@ void adjoint_device(lamg_ctx *h, const double *x, const double *g, double *lambd
         LAMG_CHECK_LAUNCH();
     }
     LAMG_CUDA(cudaStreamSynchronize(s));
-}
-
-void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X, int64_t ld, double tol,
-                          lamg_precision p, cudaStream_t s, lamg_stats *st) {
-    throw Error{LAMG_ERR_ARG, "lamg_solve_batched: not built yet"};
 }
 
 void release_solve(lamg_ctx *h) {

@@ -81,14 +81,16 @@ __device__ __forceinline__ void row_dot(int32_t s, int32_t e, const int32_t *__r
     }
 }
 
-// x_i = (b_i + sum_v w_iv x_v) / sum_v w_iv
+// x_i = (b_i + sum_v w_iv x_v) / sum_v w_iv; a row without entries (an isolated
+// node of a union of graphs) is left unchanged
 template <int M, class T>
 __device__ __forceinline__ void gs_row(int32_t i, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                        const T *__restrict__ w, const T *__restrict__ b, T *__restrict__ x) {
     T acc = T(0), d = T(0);
-    row_dot<M, T>(rp[i], rp[i + 1], col, w, x, acc, d);
+    const int32_t s = rp[i], e = rp[i + 1];
+    row_dot<M, T>(s, e, col, w, x, acc, d);
     reduce2<M>(acc, d);
-    if (slane<M>() == 0) x[i] = (b[i] + acc) / d;
+    if (slane<M>() == 0 && e > s) x[i] = (b[i] + acc) / d;
 }
 
 // r_i = b_i - (A x)_i = b_i + sum_v w_iv (x_v - x_i)   (differences: no cancellation)

@@ -67,6 +67,7 @@ def _load():
         "lamg_default_options": (None, [P]),
         "lamg_last_error": (C.c_char_p, []),
         "lamg_setup": (I32, [I64, P, P, P, I32, P, P, P]),
+        "lamg_setup_graphs": (I32, [I32, P, I64, P, P, P, I32, P, P, P]),
         "lamg_solve": (I32, [P, P, P, D, I32, P, P]),
         "lamg_solve_host": (I32, [P, P, P, D, I32, P, P]),
         "lamg_solve_batched": (I32, [P, I32, P, P, I64, D, I32, P, P]),
@@ -152,6 +153,22 @@ def lamg_setup(n: int, row_ptr, col, w, opt: lamg_options | None = None, stream=
     return h
 
 
+def lamg_setup_graphs(gptr, row_ptr, col, w, opt: lamg_options | None = None, stream=None):
+    """Hierarchy of a block-diagonal union of graphs; gptr: host int64 node ranges."""
+    _dev(row_ptr, torch.int64, "row_ptr")
+    _dev(col, torch.int32, "col")
+    if w.dtype not in (torch.float64, torch.float32):
+        raise TypeError("w must be float64 or float32")
+    _dev(w, w.dtype, "w")
+    gp = np.ascontiguousarray(gptr, dtype=np.int64)
+    h = C.c_void_p()
+    st = _lib.lamg_setup_graphs(int(len(gp) - 1), _ptr(gp), int(gp[-1]), _ptr(row_ptr), _ptr(col), _ptr(w),
+                                int(w.dtype == torch.float32), C.byref(opt) if opt is not None else None,
+                                _stream(stream), C.byref(h))
+    _check(st, "lamg_setup_graphs")
+    return h
+
+
 def lamg_solve(h, b, x, tol: float = 1e-8, precision: int = LAMG_FP64, stream=None,
                allow_not_converged: bool = False) -> lamg_stats:
     _dev(b, torch.float64, "b")
@@ -171,15 +188,21 @@ def lamg_solve_host(h, b: np.ndarray, x: np.ndarray, tol: float = 1e-8, precisio
     return s
 
 
-def lamg_solve_batched(h, B, X, tol: float = 1e-8, precision: int = LAMG_FP64, stream=None):
-    """B, X: (n, nrhs) row-interleaved FP64 device tensors."""
-    _dev(B, torch.float64, "B")
-    _dev(X, torch.float64, "X")
+def lamg_solve_batched(h, B, X, tol: float = 1e-8, precision: int = LAMG_FP64, stream=None,
+                       allow_not_converged: bool = False):
+    """B, X: (n, nrhs) FP64 device tensors with unit column stride (row-interleaved,
+    ld = stride(0) >= nrhs).  Returns one lamg_stats per column."""
+    for t, name in ((B, "B"), (X, "X")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2
+                and t.stride(1) == 1):
+            raise TypeError(f"{name} must be a CUDA float64 (n, nrhs) tensor with unit column stride")
+    if B.shape != X.shape or B.stride(0) != X.stride(0):
+        raise TypeError("B and X must have the same shape and row stride")
     nrhs = B.shape[1]
     stats = (lamg_stats * nrhs)()
     st = _lib.lamg_solve_batched(h, int(nrhs), _ptr(B), _ptr(X), int(B.stride(0)), float(tol),
                                  int(precision), _stream(stream), stats)
-    _check(st, "lamg_solve_batched")
+    _check(st, "lamg_solve_batched", (LAMG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return list(stats)
 
 
@@ -263,23 +286,31 @@ def lamg_launch_count() -> int:
 class Solver:
     """Owns one hierarchy.  ``Solver(graph_csr_on_device)`` then ``solve(b)``."""
 
-    def __init__(self, n, row_ptr, col, w, stream=None, **opts):
+    def __init__(self, n, row_ptr, col, w, stream=None, gptr=None, **opts):
         self.n = int(n)
         self.opt = lamg_default_options(**opts)
-        self.h = lamg_setup(n, row_ptr, col, w, self.opt, stream)
+        if gptr is None:
+            self.h = lamg_setup(n, row_ptr, col, w, self.opt, stream)
+        else:
+            self.h = lamg_setup_graphs(gptr, row_ptr, col, w, self.opt, stream)
         self.device = row_ptr.device
 
     @classmethod
-    def from_graph(cls, g, device="cuda", w_dtype=torch.float64, **opts):
+    def from_graph(cls, g, device="cuda", w_dtype=torch.float64, gptr=None, **opts):
         rp = torch.as_tensor(g.rp, dtype=torch.int64, device=device)
         col = torch.as_tensor(g.col, dtype=torch.int32, device=device)
         w = torch.as_tensor(g.w, device=device).to(w_dtype)
-        return cls(g.n, rp, col, w, **opts)
+        return cls(g.n, rp, col, w, gptr=gptr, **opts)
 
     def solve(self, b, x0=None, tol=1e-8, precision=LAMG_FP64, stream=None, allow_not_converged=False):
         x = torch.zeros_like(b) if x0 is None else x0.clone()
         st = lamg_solve(self.h, b, x, tol, precision, stream, allow_not_converged)
         return x, st
+
+    def solve_batched(self, B, X0=None, tol=1e-8, precision=LAMG_FP64, stream=None, allow_not_converged=False):
+        X = torch.zeros_like(B) if X0 is None else X0.clone()
+        st = lamg_solve_batched(self.h, B, X, tol, precision, stream, allow_not_converged)
+        return X, st
 
     def level_info(self, level):
         return lamg_level_info(self.h, level)

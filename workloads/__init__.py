@@ -239,6 +239,39 @@ def knn_gmm(n: int = 500_000, dim: int = 16, k: int = 10, ncomp: int = 10, seed:
     return g2, lab, pts
 
 
+def block_union(graphs) -> tuple[Graph, np.ndarray]:
+    """Block-diagonal union of graphs: graph g's nodes are renumbered to
+    gptr[g] .. gptr[g+1]-1.  Returns (union graph, gptr int64[G+1])."""
+    gptr = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        gptr[k + 1] = gptr[k] + g.n
+    rp = [np.zeros(1, dtype=np.int64)]
+    off = 0
+    for g in graphs:
+        rp.append(g.rp[1:] + off)
+        off += int(g.rp[-1])
+    col = np.concatenate([g.col.astype(np.int64) + gptr[k] for k, g in enumerate(graphs)]).astype(np.int32)
+    w = np.concatenate([g.w for g in graphs])
+    return Graph(int(gptr[-1]), np.concatenate(rp), col, w, f"union{len(graphs)}"), gptr
+
+
+def er_batch(count: int, n_lo: int, n_hi: int, mean_deg: float = 8.0, seed: int = 7):
+    """`count` Erdos-Renyi graphs (largest components) with n uniform in [n_lo, n_hi],
+    as one block-diagonal union: returns (union graph, gptr)."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(n_lo, n_hi + 1, count)
+    return block_union([erdos_renyi(int(m), mean_deg, seed=int(seed * 100003 + k)) for k, m in enumerate(sizes)])
+
+
+def zero_sum_rhs_graphs(gptr, seed: int) -> np.ndarray:
+    """Gaussian right-hand side with the mean removed on every graph's node range."""
+    rng = np.random.default_rng(seed)
+    b = rng.normal(size=int(gptr[-1]))
+    for g in range(len(gptr) - 1):
+        b[gptr[g]:gptr[g + 1]] -= b[gptr[g]:gptr[g + 1]].mean()
+    return b
+
+
 def zero_sum_rhs(n: int, seed: int, count: int | None = None) -> np.ndarray:
     """Gaussian right-hand side(s) with the mean removed (Sec. 1: b must be zero-sum)."""
     rng = np.random.default_rng(seed)
