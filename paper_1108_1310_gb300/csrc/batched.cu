@@ -51,25 +51,7 @@ __device__ __forceinline__ void reduce_n(T (&v)[N]) {
 #pragma unroll
         for (int k = 0; k < N; k++) v[k] = warp_allsum(v[k]);
     }
-    if (M == M_BLK) {
-        __shared__ T sh[N][32];
-#pragma unroll
-        for (int k = 0; k < N; k++) v[k] = warp_allsum(v[k]);
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-            for (int k = 0; k < N; k++) sh[k][threadIdx.x >> 5] = v[k];
-        }
-        __syncthreads();
-        const int nw = (int)(blockDim.x >> 5);
-#pragma unroll
-        for (int k = 0; k < N; k++) {
-            T t = T(0);
-            for (int q = 0; q < nw; q++) t += sh[k][q];
-            v[k] = t;
-        }
-        __syncthreads();
-    }
+    if (M == M_BLK) block_sum_n<T, N>(v);
 }
 
 // ---------------------------------------------------------------------------

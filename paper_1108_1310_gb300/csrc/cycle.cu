@@ -145,31 +145,29 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             break;
         }
         case OP_RECOMB_DOTS: {
-            double g00 = 0, g01 = 0, g11 = 0, h0 = 0, h1 = 0;
+            // in the cycle precision per thread and block; block partials in FP64
+            T v[5] = {T(0), T(0), T(0), T(0), T(0)};  // G00, G01, G11, h0, h1
             for (int64_t i = tid; i < L.n; i += nthr) {
-                const double ri = (double)L.r[i];
-                const double d0 = ri - (double)L.rs0[i];
-                g00 += d0 * d0;
-                h0 += ri * d0;
+                const T ri = L.r[i];
+                const T d0 = ri - L.rs0[i];
+                v[0] += d0 * d0;
+                v[3] += ri * d0;
                 if (op.a == 2) {
-                    const double d1 = ri - (double)L.rs1[i];
-                    g01 += d0 * d1;
-                    g11 += d1 * d1;
-                    h1 += ri * d1;
+                    const T d1 = ri - L.rs1[i];
+                    v[1] += d0 * d1;
+                    v[2] += d1 * d1;
+                    v[4] += ri * d1;
                 }
             }
-            const double v[5] = {g00, g01, g11, h0, h1};
-            for (int k = 0; k < 5; k++) {
-                const double t = block_sum_d<double>(v[k]);
-                if (threadIdx.x == 0) a.part[(int64_t)bid * 8 + k] = t;
-            }
+            block_sum_n<T, 5>(v);
+            if (threadIdx.x < 5) a.part[(int64_t)bid * 8 + threadIdx.x] = (double)v[threadIdx.x];
             break;
         }
         case OP_RECOMB_APPLY: {
             // Eq. (3.13): alpha minimises ||b - A y||_2; normal equations of size theta
-            const double G00 = sum_partials(a.part, nb, 0), G01 = sum_partials(a.part, nb, 1);
-            const double G11 = sum_partials(a.part, nb, 2), h0 = sum_partials(a.part, nb, 3);
-            const double h1 = sum_partials(a.part, nb, 4);
+            double G[5];
+            sum_partials_n<5>(a.part, nb, 0, G);
+            const double G00 = G[0], G01 = G[1], G11 = G[2], h0 = G[3], h1 = G[4];
             double a0 = 0.0, a1 = 0.0;
             if (op.a == 1) {
                 if (G00 > 0.0) a0 = h0 / G00;
@@ -182,24 +180,25 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
                     a0 = h0 / G00;
                 }
             }
+            const T ta0 = (T)a0, ta1 = (T)a1;
             for (int64_t i = tid; i < L.n; i += nthr) {
-                const double xi = (double)L.x[i];
-                double y = xi + a0 * ((double)L.xs0[i] - xi);
-                if (op.a == 2) y += a1 * ((double)L.xs1[i] - xi);
-                L.x[i] = (T)y;
+                const T xi = L.x[i];
+                T y = xi + ta0 * (L.xs0[i] - xi);
+                if (op.a == 2) y += ta1 * (L.xs1[i] - xi);
+                L.x[i] = y;
             }
             break;
         }
         case OP_MEAN_PART: {
-            double v = 0.0;
-            for (int64_t i = tid; i < L.n; i += nthr) v += (double)L.x[i];
-            v = block_sum_d<double>(v);
-            if (threadIdx.x == 0) a.part[(int64_t)bid * 8] = v;
+            T v = T(0);
+            for (int64_t i = tid; i < L.n; i += nthr) v += L.x[i];
+            v = block_sum<T>(v);
+            if (threadIdx.x == 0) a.part[(int64_t)bid * 8] = (double)v;
             break;
         }
         case OP_MEAN_APPLY: {
-            const double m = sum_partials(a.part, nb, 0) / (double)L.n;
-            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] = (T)((double)L.x[i] - m);
+            const T m = (T)(sum_partials(a.part, nb, 0) / (double)L.n);
+            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] -= m;
             break;
         }
         case OP_IR_PREP:
@@ -245,13 +244,17 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             for (int32_t g = bid; g < a.ngraphs; g += nb) {
                 const int64_t s0 = a.gptr[g], e0 = a.gptr[g + 1];
                 double v = 0.0;
-                for (int64_t u = s0 + threadIdx.x; u < e0; u += blockDim.x) {
-                    const int32_t i = a.iperm0[u];
-                    if (op.type == OP_GMEAN_PART) v += (double)L.x[i];
-                    else if (op.type == OP_GMEAN64_PART) v += a.L0.x[i];
-                    else v += a.L0.r[i] * a.L0.r[i];
+                if (op.type == OP_GMEAN_PART) {
+                    T t = T(0);
+                    for (int64_t u = s0 + threadIdx.x; u < e0; u += blockDim.x) t += L.x[a.iperm0[u]];
+                    v = (double)block_sum<T>(t);
+                } else {
+                    for (int64_t u = s0 + threadIdx.x; u < e0; u += blockDim.x) {
+                        const int32_t i = a.iperm0[u];
+                        v += op.type == OP_GMEAN64_PART ? a.L0.x[i] : a.L0.r[i] * a.L0.r[i];
+                    }
+                    v = block_sum<double>(v);
                 }
-                v = block_sum_d<double>(v);
                 if (threadIdx.x == 0) {
                     if (op.type == OP_GNORM64) a.gnorm[g] = v;
                     else a.gsum[g] = v / (double)(e0 - s0);
@@ -259,7 +262,7 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             }
             break;
         case OP_GMEAN_APPLY:
-            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] = (T)((double)L.x[i] - a.gsum[a.gid0[i]]);
+            for (int64_t i = tid; i < L.n; i += nthr) L.x[i] -= (T)a.gsum[a.gid0[i]];
             break;
         case OP_GMEAN64_APPLY:
             for (int64_t i = tid; i < a.L0.n; i += nthr) a.L0.x[i] -= a.gsum[a.gid0[i]];
@@ -280,7 +283,9 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             break;
         }
         case OP_TAIL_RUN: {
-            // single block: x_i = (r_i + sum over tail neighbours) / a_ii, colour by colour
+            // single block: x_i = (r_i + sum over tail neighbours) / a_ii, colour by colour.
+            // Each colour's rows are cut into chunks of kTailChunk local entries spread over
+            // all warps; the chunk sums of a row are then added in order (deterministic).
             extern __shared__ __align__(16) unsigned char smem[];
             auto al = [](int64_t v) { return (v + 15) & ~int64_t(15); };
             const int32_t tn = L.tn, tnc = L.tnc, t0 = L.tt0;
@@ -289,7 +294,9 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             T *ss = (T *)p; p += al((int64_t)sizeof(T) * tn);
             T *sd = (T *)p; p += al((int64_t)sizeof(T) * tn);
             int32_t *srp = (int32_t *)p; p += al(4 * (int64_t)(tn + 1));
+            int32_t *srq = (int32_t *)p; p += al(4 * (int64_t)(tn + 1));
             int32_t *scb = (int32_t *)p; p += al(4 * (int64_t)(tnc + 1));
+            T *cpart = (T *)p; p += al((int64_t)sizeof(T) * L.tmaxq);
             const int32_t *tcol = L.tcol;
             const T *tw = L.tw;
             if (op.a) {  // the local CSR fits: stage it too
@@ -304,16 +311,31 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
                 ss[k] = L.r[t0 + k];
                 sd[k] = L.tdeg[k];
             }
-            for (int32_t k = threadIdx.x; k <= tn; k += blockDim.x) srp[k] = L.trp[k];
+            for (int32_t k = threadIdx.x; k <= tn; k += blockDim.x) { srp[k] = L.trp[k]; srq[k] = L.trq[k]; }
             for (int32_t k = threadIdx.x; k <= tnc; k += blockDim.x) scb[k] = L.tcb[k];
             __syncthreads();
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
             for (int32_t c = 0; c < tnc; c++) {
-                for (int32_t li = scb[c] + warp; li < scb[c + 1]; li += nw) {
+                const int32_t R0 = scb[c], R1 = scb[c + 1], Q0 = srq[R0], Q1 = srq[R1];
+                for (int32_t q = Q0 + warp; q < Q1; q += nw) {
+                    int32_t lo = R0, hi = R1 - 1;   // last row of the colour whose first chunk is <= q
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi + 1) >> 1;
+                        if (srq[mid] <= q) lo = mid; else hi = mid - 1;
+                    }
+                    const int32_t k0 = srp[lo] + (q - srq[lo]) * kTailChunk;
+                    const int32_t k1 = min(k0 + kTailChunk, srp[lo + 1]);
                     T acc = T(0);
-                    for (int32_t k = srp[li] + lane; k < srp[li + 1]; k += 32) acc += tw[k] * sx[tcol[k]];
+#pragma unroll 4
+                    for (int32_t k = k0 + lane; k < k1; k += 32) acc += tw[k] * sx[tcol[k]];
                     acc = warp_allsum(acc);
-                    if (lane == 0 && sd[li] != T(0)) sx[li] = (ss[li] + acc) / sd[li];
+                    if (lane == 0) cpart[q - Q0] = acc;
+                }
+                __syncthreads();
+                for (int32_t li = R0 + threadIdx.x; li < R1; li += blockDim.x) {
+                    T acc = T(0);
+                    for (int32_t q = srq[li]; q < srq[li + 1]; q++) acc += cpart[q - Q0];
+                    if (sd[li] != T(0)) sx[li] = (ss[li] + acc) / sd[li];
                 }
                 __syncthreads();
             }
@@ -341,9 +363,10 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             for (int rep = 0; rep < op.a; rep++)
                 for (int32_t c = 0; c < nc; c++) {
                     const int32_t t0 = scb[4 * c], t1 = scb[4 * c + 1], t2 = scb[4 * c + 2], t3 = scb[4 * c + 3];
+                    // long rows: one warp each (shared-memory gathers are short; rows of a
+                    // colour proceed in parallel instead of one block-wide row at a time)
                     for (int32_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) gs_row<M_THR, T>(i, srp, scol, sw, sbv, sx);
-                    for (int32_t i = t1 + warp; i < t2; i += nwarp) gs_row<M_WARP, T>(i, srp, scol, sw, sbv, sx);
-                    for (int32_t i = t2; i < t3; i++) gs_row<M_BLK, T>(i, srp, scol, sw, sbv, sx);
+                    for (int32_t i = t1 + warp; i < t3; i += nwarp) gs_row<M_WARP, T>(i, srp, scol, sw, sbv, sx);
                     __syncthreads();
                 }
             for (int32_t k = threadIdx.x; k < n; k += blockDim.x) L.x[k] = sx[k];
@@ -443,7 +466,10 @@ struct Builder {
             for (int c = 0; c < nc; c++) emit(OP_SWEEP, l, c, c + 1, false);
             return;
         }
-        const int cend = V.tn > 0 ? V.tc0 : nc;   // colours before the tail
+        const int64_t tbase = V.tn > 0 ? (prec == 0 ? tail_smem_base<double>(V.tn, V.tnc, V.tmaxq)
+                                                    : tail_smem_base<float>(V.tn, V.tnc, V.tmaxq)) : 0;
+        const bool tail = V.tn > 0 && tbase <= kEngSmem;
+        const int cend = tail ? V.tc0 : nc;   // colours before the tail
         const std::vector<int32_t> &seg = V.seg[prec];
         for (size_t q = 0; q < seg.size(); q += 3) {
             const int c0 = seg[q], c1 = std::min((int)seg[q + 1], cend);
@@ -451,11 +477,10 @@ struct Builder {
             if (seg[q + 2]) emit(OP_SWEEP_RUN, l, c0, c1, true);
             else emit(OP_SWEEP, l, c0, c0 + 1, false);
         }
-        if (V.tn > 0) {
-            const int64_t base = prec == 0 ? tail_smem_base<double>(V.tn, V.tnc) : tail_smem_base<float>(V.tn, V.tnc);
+        if (tail) {
             const int64_t csr = prec == 0 ? tail_smem_csr<double>(V.tnnz) : tail_smem_csr<float>(V.tnnz);
             emit(OP_TAIL_PRE, l, 0, 0, false);
-            emit(OP_TAIL_RUN, l, base + csr <= kEngSmem ? 1 : 0, 0, true);
+            emit(OP_TAIL_RUN, l, tbase + csr <= kEngSmem ? 1 : 0, 0, true);
         }
     }
     void coarsest(int l) {

@@ -23,8 +23,8 @@ struct MKLevel {
     T *x, *b, *r, *xs0, *xs1, *rs0, *rs1;
     const double *minv;
     // tail colours (tn == 0: none)
-    int32_t tt0, tn, tnc, tnnz;
-    const int32_t *trp, *tcol, *tcb;
+    int32_t tt0, tn, tnc, tnnz, tmaxq;
+    const int32_t *trp, *tcol, *tcb, *trq;
     const T *tw, *tdeg;
 };
 
@@ -133,25 +133,72 @@ __device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err) {
     return bad == 0;
 }
 
-template <class T>
-__device__ __forceinline__ double block_sum_d(double v) {
-    __shared__ double sh[32];
-    v = warp_allsum(v);
+// Block sums of N values of type A, result in every thread.  The cross-warp
+// step runs in warp 0 alone: with FP64 (1/64 of the FP32 rate on this GPU)
+// a sum done by every thread would cost 32 adds per thread.
+template <class A, int N>
+__device__ __forceinline__ void block_sum_n(A (&v)[N]) {
+    __shared__ A sh[N][32];
+    __shared__ A res[N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int k = 0; k < N; k++) v[k] = warp_allsum(v[k]);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k++) sh[k][warp] = v[k];
+    }
     __syncthreads();
-    double t = 0.0;
-    const int nw = (int)(blockDim.x >> 5);
-    for (int k = 0; k < nw; k++) t += sh[k];
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            A t = lane < nw ? sh[k][lane] : A(0);
+            t = warp_allsum(t);
+            if (lane == 0) res[k] = t;
+        }
+    }
     __syncthreads();
-    return t;  // in every thread
+#pragma unroll
+    for (int k = 0; k < N; k++) v[k] = res[k];
+    __syncthreads();
 }
 
-// sum of the nb block partials at slot k (same order in every block)
+template <class A>
+__device__ __forceinline__ A block_sum(A v) {
+    A t[1] = {v};
+    block_sum_n<A, 1>(t);
+    return t[0];
+}
+
+template <class T>
+__device__ __forceinline__ double block_sum_d(double v) { return block_sum<double>(v); }
+
+// out[k] = sum of the nb block partials at slots k0 .. k0+N-1 (warp 0 sums, fixed
+// order; the result is broadcast to every thread)
+template <int N>
+__device__ __forceinline__ void sum_partials_n(const double *part, int nb, int k0, double (&out)[N]) {
+    __shared__ double res[N];
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            double t = 0.0;
+            for (int b = lane; b < nb; b += 32) t += part[(int64_t)b * 8 + k0 + k];
+            t = warp_allsum(t);
+            if (lane == 0) res[k] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; k++) out[k] = res[k];
+    __syncthreads();
+}
+
 __device__ __forceinline__ double sum_partials(const double *part, int nb, int k) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)b * 8 + k];
-    return block_sum_d<double>(v);
+    double o[1];
+    sum_partials_n<1>(part, nb, k, o);
+    return o[0];
 }
 
 template <class T>
@@ -190,6 +237,8 @@ inline MKLevel<T> describe(lamg_ctx *h, int l, LevelVecs<T> &v, const T *w) {
     d.trp = V.trp.get();
     d.tcol = V.tcol.get();
     d.tcb = V.tcb.get();
+    d.trq = V.trq.get();
+    d.tmaxq = V.tmaxq;
     if constexpr (sizeof(T) == 8) {
         d.tw = (const T *)V.tw64.get();
         d.tdeg = (const T *)V.tdeg64.get();
@@ -200,12 +249,12 @@ inline MKLevel<T> describe(lamg_ctx *h, int l, LevelVecs<T> &v, const T *w) {
     return d;
 }
 
-// shared memory of the tail run: x, s, d (T each), trp, tcb, and (when it fits)
-// the tail block's local CSR
+// shared memory of the tail run: x, s, d (T each), trp, tcb, trq, the chunk
+// partial sums of one colour, and (when it fits) the tail block's local CSR
 template <class T>
-__host__ __device__ __forceinline__ int64_t tail_smem_base(int64_t tn, int64_t tnc) {
+__host__ __device__ __forceinline__ int64_t tail_smem_base(int64_t tn, int64_t tnc, int64_t tmaxq) {
     auto al = [](int64_t b) { return (b + 15) & ~int64_t(15); };
-    return 3 * al((int64_t)sizeof(T) * tn) + al(4 * (tn + 1)) + al(4 * (tnc + 1));
+    return 3 * al((int64_t)sizeof(T) * tn) + 2 * al(4 * (tn + 1)) + al(4 * (tnc + 1)) + al((int64_t)sizeof(T) * tmaxq);
 }
 template <class T>
 __host__ __device__ __forceinline__ int64_t tail_smem_csr(int64_t tnnz) {

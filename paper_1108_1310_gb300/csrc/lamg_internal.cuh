@@ -61,6 +61,7 @@ int64_t launch_count();
 constexpr int kLongRow = 32;
 constexpr int kHugeRow = 512;
 constexpr int kHugeSolve = 512;
+constexpr int kTailChunk = 128;   // entries of a tail row summed by one warp in a tail colour step
 constexpr int kBlk = 1024;
 
 // ---------------------------------------------------------------------------
@@ -146,6 +147,8 @@ struct SolveLevel {
     int32_t tc0 = -1, tt0 = 0, tn = 0, tnc = 0;
     int64_t tnnz = 0;
     DBuf<int32_t> trp, tcol, tcb;  // local CSR of the tail block, tail colour bounds (local rows)
+    DBuf<int32_t> trq;             // per local row: first chunk (kTailChunk entries) of its local row
+    int32_t tmaxq = 0;             // most chunks in one tail colour
     DBuf<double> tw64, tdeg64;     // weights and full weighted degrees of tail rows
     DBuf<float> tw32, tdeg32;
     // coarsest level

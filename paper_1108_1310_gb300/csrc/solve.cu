@@ -207,6 +207,14 @@ static void build_tail(SolveLevel &V, int ncol, cudaStream_t s) {
         trp[i + 1] = (int32_t)tcol.size();
     }
     for (int c = c0; c <= ncol; c++) tcb[c - c0] = (c < ncol ? V.cb[4 * c] : n) - t0;
+    // chunks of kTailChunk local entries: a tail colour step spreads its rows' chunks over all warps
+    std::vector<int32_t> trq(tn + 1, 0);
+    for (int32_t i = 0; i < tn; i++) trq[i + 1] = trq[i] + (trp[i + 1] - trp[i] + kTailChunk - 1) / kTailChunk;
+    int32_t maxq = 0;
+    for (int c = 0; c + 1 < (int)tcb.size(); c++) maxq = std::max(maxq, trq[tcb[c + 1]] - trq[tcb[c]]);
+    V.tmaxq = maxq;
+    V.trq.alloc(tn + 1);
+    LAMG_CUDA(cudaMemcpyAsync(V.trq.get(), trq.data(), sizeof(int32_t) * (tn + 1), cudaMemcpyHostToDevice, s));
     V.tc0 = c0;
     V.tt0 = t0;
     V.tn = tn;

@@ -26,19 +26,26 @@ __device__ __forceinline__ T warp_allsum(T v) {
     return v;
 }
 
-// block sum of two values, result in every thread of the block
+// block sum of two values, result in every thread of the block (the cross-warp
+// step in warp 0 only: FP64 adds are expensive on this GPU)
 template <class T>
 __device__ __forceinline__ void block_allsum2(T &a, T &b) {
-    __shared__ T sa[32], sb[32];
+    __shared__ T sa[32], sb[32], res[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     a = warp_allsum(a);
     b = warp_allsum(b);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = a; sb[threadIdx.x >> 5] = b; }
+    if (lane == 0) { sa[warp] = a; sb[warp] = b; }
     __syncthreads();
-    a = T(0);
-    b = T(0);
-    const int nw = (int)(blockDim.x >> 5);
-    for (int k = 0; k < nw; k++) { a += sa[k]; b += sb[k]; }
+    if (warp == 0) {
+        T ta = lane < nw ? sa[lane] : T(0), tb = lane < nw ? sb[lane] : T(0);
+        ta = warp_allsum(ta);
+        tb = warp_allsum(tb);
+        if (lane == 0) { res[0] = ta; res[1] = tb; }
+    }
+    __syncthreads();
+    a = res[0];
+    b = res[1];
     __syncthreads();
 }
 
