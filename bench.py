@@ -35,6 +35,10 @@ WORKLOADS = {
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
 }
 TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10}
+# DRAM bytes (read + write) of one engine launch from one ncu capture of this
+# workload (profiles/k_engine_chung_lu1m_fp32ir.md); must be reset to None
+# whenever the engine kernel changes.
+NCU_TRAFFIC = {}
 # batched forms (many right-hand sides on one hierarchy; many graphs as one union)
 BATCHED = {
     "rgg2m_b64": "64 zero-sum Gaussian RHS on a 2M-node 2-D RGG (mean degree 12, w = exp(-d^2/r^2), FP32); "
@@ -406,7 +410,7 @@ def main():
         avg = prof_ms / prof_cnt
         achieved = prof_bytes / (avg / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "cycle engine (one launch = one refinement step: ir_inner FP32 cycles + FP64 residual)",
+                "traffic": NCU_TRAFFIC.get((args.workload, prec_name)), "kernel": "cycle engine (one launch = one refinement step: ir_inner FP32 cycles + FP64 residual)",
                 "bytes_per_launch": prof_bytes, "avg_ms": avg, "launches": prof_cnt,
                 "peak_kind": f"{peak_kind} hbm_gbs"}
 

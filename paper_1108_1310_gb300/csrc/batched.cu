@@ -516,6 +516,7 @@ template <class T>
 __global__ void __launch_bounds__(kEngThreads, 1) k_engine4(MRArgs<T> a) {
     __shared__ MRShared S;
     int32_t pc = a.begin;
+    unsigned int epoch = 0;
     while (pc < a.end) {
         const Op op = a.prog[pc];
         if (op.sb) {
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine4(MRArgs<T> a) {
             exec_op4<T>(a, S, op, blockIdx.x, gridDim.x);
             pc++;
         }
-        if (!grid_sync(a.bar, a.err)) return;
+        if (!grid_sync(a.bar, a.err, epoch)) return;
     }
 }
 
@@ -671,6 +672,7 @@ static void batch_run(lamg_ctx *h, int kind, int adaptive, cudaStream_t s) {
     MKLevel<double> L0 = describe<double>(h, 0, M.v64[0], h->lv[0].w64.get());
     L0.r = M.r64.get();
     const double mu = adaptive ? 1.0 : h->opt.mu_flat;
+    LAMG_CUDA(cudaMemsetAsync(M.bar.get(), 0, 2 * sizeof(unsigned int), s));  // the barrier counts from 0
     if (kind == 1) {
         MRArgs<float> a{(const Op *)M.prog[slot].get(), 0, M.len[slot], (const MKLevel<float> *)M.lv32.get(), L0,
                         (float)mu, M.ld, M.groups, lg, M.part.get(), M.bar.get(), M.err.get()};

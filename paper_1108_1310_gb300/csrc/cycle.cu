@@ -380,6 +380,7 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
 template <class T>
 __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
     int32_t pc = a.begin;
+    unsigned int epoch = 0;
     while (pc < a.end) {
         const Op op = a.prog[pc];
         const bool timed = a.optime && blockIdx.x == 0 && threadIdx.x == 0;
@@ -400,7 +401,7 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
             exec_op<T>(a, op, blockIdx.x, gridDim.x);
             pc++;
         }
-        if (!grid_sync(a.bar, a.err)) return;
+        if (!grid_sync(a.bar, a.err, epoch)) return;
         if (timed) {
             const int key = (op.level * 32 + op.type) * 2 + (op.sb ? 1 : 0);
             a.optime[2 * key] += gtimer() - t0;
@@ -434,9 +435,7 @@ struct Builder {
     bool level_sb(int l) const {
         const SolveLevel &V = h->lv[l];
         if (groups) return (V.nnz + V.n) * groups <= kSBWork;
-        const int nc = (int)V.cb.size() / 4;
-        const int64_t need = prec == 0 ? smem_bytes<double>(V.n, V.nnz, nc) : smem_bytes<float>(V.n, V.nnz, nc);
-        return V.nnz + V.n <= kSBWork && need <= kEngSmem;
+        return V.nnz + V.n <= sb_work(prec);
     }
     void emit(int type, int level, int a, int b, bool sb) { prog.push_back(Op{type, level, a, b, sb ? 1 : 0}); }
 
@@ -664,6 +663,7 @@ void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s) 
     MKLevel<double> L0 = describe<double>(h, 0, h->v64[0], h->lv[0].w64.get());
     L0.r = h->r64.get();
     const dim3 grid(h->eng_grid), block(kEngThreads);
+    LAMG_CUDA(cudaMemsetAsync(h->eng_bar.get(), 0, 2 * sizeof(unsigned int), s));  // the barrier counts from 0
     if (kind == 1) {
         EngineArgs<float> a{(const Op *)slot.get(), 0, len, (const MKLevel<float> *)h->eng_lv32.get(), L0,
                             (float)mu, h->eng_part.get(), nullptr, h->scratch.get(), h->eng_bar.get(),

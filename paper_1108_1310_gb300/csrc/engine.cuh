@@ -8,7 +8,7 @@
 namespace lamg {
 
 constexpr int kEngThreads = 1024;
-constexpr long long kMaxSpins = 1ll << 23;  // about a second of polling
+constexpr long long kMaxSpins = 1ll << 21;  // one to two seconds of polling
 
 template <class T>
 struct MKLevel {
@@ -104,27 +104,32 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // grid barrier (bounded spin)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err) {
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Counting grid barrier: bar[0] counts every block's arrivals over the whole
+// launch and must be zero when the launch starts (the host clears it before
+// each launch).  Barrier number e (1, 2, ...) completes when bar[0] reaches
+// e * gridDim.x, so no block resets anything and a single atomic per block
+// and barrier suffices; thread 0 polls with acquire loads.  The spin is
+// bounded: after kMaxSpins polls (or when another block has given up) it sets
+// the error word and every block returns.
+__device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err, unsigned int &epoch) {
     __shared__ int bad;
     __syncthreads();
     if (threadIdx.x == 0) {
         bad = 0;
-        volatile unsigned int *vgen = bar + 1;
-        const unsigned int gen = *vgen;
+        const unsigned int target = (++epoch) * gridDim.x;
         __threadfence();
-        const unsigned int arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if ((++spins & 63) == 0) {
-                    if (*(volatile int32_t *)err) { bad = 1; break; }
-                    if (spins > kMaxSpins) { atomicExch(err, 1); bad = 1; break; }
-                }
-                __nanosleep(32);
+        atomicAdd(bar, 1u);
+        long long spins = 0;
+        while (ld_acquire_gpu(bar) < target) {
+            if ((++spins & 255) == 0) {
+                if (*(volatile int32_t *)err) { bad = 1; break; }
+                if (spins > kMaxSpins) { atomicExch(err, 1); bad = 1; break; }
             }
         }
         __threadfence();

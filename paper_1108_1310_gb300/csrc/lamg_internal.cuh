@@ -230,7 +230,14 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
 void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
                     int32_t w_is_fp32, cudaStream_t s, int32_t ngraphs = 1, const int64_t *gptr = nullptr);
 
-// single-block threshold of the cycle engine (n + nnz of a level)
+// Single-block thresholds of the cycle engine: a level whose n + nnz is at most
+// sb_work(prec) runs every op on one block (no grid barrier); a colour of at
+// most tail_work(prec) entries joins a single-block run.  One SM streams FP32
+// rows from L2 faster than a grid-wide phase completes, up to a few hundred
+// KB; FP64 arithmetic on one SM is slow (1/64 rate), so its limits are lower.
+// LAMG_SB_WORK32/64 and LAMG_TAIL_WORK32/64 override them (tuning aid).
+int64_t sb_work(int prec);    // prec 0 = FP64, 1 = FP32
+int64_t tail_work(int prec);
 constexpr int64_t kSBWork = 16384;
 
 // cycle.cu

@@ -635,11 +635,13 @@ __global__ void __launch_bounds__(kBlk) k_jp_finish(const int32_t *__restrict__ 
                                                    int32_t *__restrict__ act0, int32_t *__restrict__ act1,
                                                    unsigned long long *__restrict__ forb, int32_t W,
                                                    int32_t *__restrict__ colour, int32_t *__restrict__ rounds_out) {
-    __shared__ int32_t na, nn;
+    __shared__ int32_t na, nn, ns;
+    __shared__ int32_t sl[kBlk];   // nodes selected this round (at most one per thread and pass)
     for (int32_t i = threadIdx.x; i < r; i += kBlk) { ptr[i] = iptr[i]; icol[i] = -1; act0[i] = i; }
     if (threadIdx.x == 0) na = r;
     __syncthreads();
     int32_t *act = act0, *nxt = act1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int32_t round = 0; round <= r; round++) {
         const int32_t m = na;
         if (m == 0) {
@@ -655,29 +657,37 @@ __global__ void __launch_bounds__(kBlk) k_jp_finish(const int32_t *__restrict__ 
         }
         if (threadIdx.x == 0) nn = 0;
         __syncthreads();
-        for (int32_t t = threadIdx.x; t < m; t += kBlk) {
-            const int32_t i = act[t];
-            if (!sel[i]) continue;
-            int32_t c = -1;
-            for (int32_t wd = 0; wd < W && c < 0; wd++) {
-                const unsigned long long mk = forb[(int64_t)i * W + wd];
-                if (mk != ~0ull) c = wd * 64 + __ffsll((long long)~mk) - 1;
+        // colour the selected nodes and queue the rest; then spread each selected
+        // node's mask updates over a warp (hubs have long induced lists).  The
+        // selected nodes are handled in passes of at most kBlk.
+        for (int32_t base = 0; base < m; base += kBlk) {
+            if (threadIdx.x == 0) ns = 0;
+            __syncthreads();
+            const int32_t t = base + threadIdx.x;
+            if (t < m) {
+                const int32_t i = act[t];
+                if (sel[i]) {
+                    int32_t c = -1;
+                    for (int32_t wd = 0; wd < W && c < 0; wd++) {
+                        const unsigned long long mk = forb[(int64_t)i * W + wd];
+                        if (mk != ~0ull) c = wd * 64 + __ffsll((long long)~mk) - 1;
+                    }
+                    icol[i] = c;
+                    colour[R[i]] = c;
+                    sl[atomicAdd(&ns, 1)] = i;
+                } else {
+                    nxt[atomicAdd(&nn, 1)] = i;
+                }
             }
-            icol[i] = c;
-            colour[R[i]] = c;
-        }
-        __syncthreads();
-        for (int32_t t = threadIdx.x; t < m; t += kBlk) {
-            const int32_t i = act[t];
-            if (!sel[i]) {
-                nxt[atomicAdd(&nn, 1)] = i;
-                continue;
+            __syncthreads();
+            for (int32_t k = warp; k < ns; k += kBlk / 32) {
+                const int32_t i = sl[k];
+                const int32_t c = icol[i];
+                for (int32_t q = iptr[i] + lane; q < iptr[i + 1]; q += 32)
+                    atomicOr(&forb[(int64_t)inb[q] * W + (c >> 6)], 1ull << (c & 63));
             }
-            const int32_t c = icol[i];
-            for (int32_t q = iptr[i]; q < iptr[i + 1]; q++)
-                atomicOr(&forb[(int64_t)inb[q] * W + (c >> 6)], 1ull << (c & 63));
+            __syncthreads();
         }
-        __syncthreads();
         if (threadIdx.x == 0) na = nn;
         int32_t *tp = act; act = nxt; nxt = tp;
         __syncthreads();
@@ -811,6 +821,75 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweep_tail(int32_t c0, int32_t c1, 
         for (int32_t i = t1 + warp; i < t2; i += kBlk / 32) tv_update<M_WARP>(order[i], rp, col, w, diag, K, X);
         for (int32_t i = t2; i < t3; i++) tv_update<M_BLK>(order[i], rp, col, w, diag, K, X);
         __syncthreads();
+    }
+}
+
+// ---- All colours of nu TV sweeps in one cooperative launch.  plan = triples
+// (c0, c1, single): single runs (small colours) go to block 0 alone with
+// __syncthreads between colours; other colours are spread over every block,
+// with a bounded grid barrier after each.  The row updates and their order
+// within a colour are those of the per-colour launches (bit-identical).
+constexpr long long kTvMaxSpins = 1ll << 23;
+
+__device__ __forceinline__ bool tv_grid_sync(unsigned int *bar, int32_t *err) {
+    __shared__ int bad;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bad = 0;
+        volatile unsigned int *vgen = bar + 1;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if ((++spins & 63) == 0) {
+                    if (*(volatile int32_t *)err) { bad = 1; break; }
+                    if (spins > kTvMaxSpins) { atomicExch(err, 1); bad = 1; break; }
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return bad == 0;
+}
+
+__global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const int32_t *__restrict__ plan,
+                                                         int32_t nplan, const int32_t *__restrict__ cb,
+                                                         const int32_t *__restrict__ order,
+                                                         const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                         const double *__restrict__ w, const double *__restrict__ diag,
+                                                         int32_t K, double *__restrict__ X, unsigned int *bar,
+                                                         int32_t *err) {
+    const int warp = threadIdx.x >> 5;
+    const int64_t nthr = (int64_t)gridDim.x * kBlk, tid = (int64_t)blockIdx.x * kBlk + threadIdx.x;
+    const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    for (int32_t sw = 0; sw < nsweeps; sw++) {
+        for (int32_t q = 0; q < nplan; q++) {
+            const int32_t c0 = plan[3 * q], c1 = plan[3 * q + 1], single = plan[3 * q + 2];
+            if (single) {
+                if (blockIdx.x == 0) {
+                    for (int32_t c = c0; c < c1; c++) {
+                        const int32_t t0 = cb[4 * c], t1 = cb[4 * c + 1], t2 = cb[4 * c + 2], t3 = cb[4 * c + 3];
+                        for (int32_t i = t0 + threadIdx.x; i < t1; i += kBlk) tv_update<M_THR>(order[i], rp, col, w, diag, K, X);
+                        for (int32_t i = t1 + warp; i < t2; i += kBlk / 32) tv_update<M_WARP>(order[i], rp, col, w, diag, K, X);
+                        for (int32_t i = t2; i < t3; i++) tv_update<M_BLK>(order[i], rp, col, w, diag, K, X);
+                        __syncthreads();
+                    }
+                }
+            } else {
+                const int32_t t0 = cb[4 * c0], t1 = cb[4 * c0 + 1], t2 = cb[4 * c0 + 2], t3 = cb[4 * c0 + 3];
+                for (int64_t i = t0 + tid; i < t1; i += nthr) tv_update<M_THR>(order[i], rp, col, w, diag, K, X);
+                for (int64_t i = t1 + wid; i < t2; i += nwarp) tv_update<M_WARP>(order[i], rp, col, w, diag, K, X);
+                for (int64_t i = t2 + blockIdx.x; i < t3; i += gridDim.x) tv_update<M_BLK>(order[i], rp, col, w, diag, K, X);
+            }
+            if (!tv_grid_sync(bar, err)) return;
+        }
     }
 }
 
@@ -1272,6 +1351,47 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, c
     auto small = [&](int c) {
         return L.cb[4 * c + 3] == L.cb[4 * c + 2] && (int64_t)ent[c] * K <= kTailWork;
     };
+    if (!test && o.nu_tv > 0) {
+        // every sweep in one cooperative launch (the energy test, when on, needs the host between sweeps)
+        std::vector<int32_t> plan;
+        for (int c = 0; c < L.ncolours;) {
+            if (small(c)) {
+                int c1 = c;
+                while (c1 < L.ncolours && small(c1)) c1++;
+                plan.insert(plan.end(), {c, c1, 1});
+                c = c1;
+            } else {
+                plan.insert(plan.end(), {c, c + 1, 0});
+                c++;
+            }
+        }
+        Tmp<int32_t> dplan(plan.size(), s);
+        Tmp<unsigned int> bar(2, s);
+        Tmp<int32_t> err(1, s);
+        LAMG_CUDA(cudaMemcpyAsync(dplan.get(), plan.data(), sizeof(int32_t) * plan.size(), cudaMemcpyHostToDevice, s));
+        LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
+        LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
+        static int grid = 0;
+        if (!grid) {
+            int dev = 0, sms = 0, per = 0;
+            LAMG_CUDA(cudaGetDevice(&dev));
+            LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tv_sweeps_coop, kBlk, 0));
+            LAMG_REQUIRE(per >= 1, LAMG_ERR_CUDA, "TV sweep kernel cannot be resident");
+            grid = sms;
+        }
+        int32_t nsw = o.nu_tv, npl = (int32_t)(plan.size() / 3);
+        const int32_t *pp = dplan.get(), *cbp = L.cb_dev.get(), *rpp = L.rp.get(), *colp = L.col.get();
+        const double *wp = L.w.get();
+        unsigned int *barp = bar.get();
+        int32_t *errp = err.get();
+        int32_t Kv = K;
+        void *args[] = {&nsw, &pp, &npl, &cbp, &ord, &rpp, &colp, &wp, &diag, &Kv, &X, &barp, &errp};
+        LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_tv_sweeps_coop, dim3(grid), dim3(kBlk), args, 0, s));
+        note_launch();
+        LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "TV sweep: grid barrier timed out");
+        return INFINITY;
+    }
     for (int sw = 1; sw <= o.nu_tv; sw++) {
         for (int c = 0; c < L.ncolours;) {
             if (small(c)) {

@@ -12,6 +12,7 @@
 // cooperative kernel per cycle or refinement step.
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -25,6 +26,20 @@ constexpr int kRedBlocks = 608;     // 152 SMs x 4 blocks for reductions
 constexpr int kRedThreads = 256;
 constexpr int64_t kTailWork32 = 2048;   // entries of a colour that the single-block sweep takes (FP32)
 constexpr int64_t kTailWork64 = 512;    // same for FP64 (one SM's FP64 rate is low on this GPU)
+constexpr int64_t kSBWork32 = 16384, kSBWork64 = 16384;
+
+static int64_t env_or(const char *name, int64_t dflt) {
+    const char *e = std::getenv(name);
+    return (e && *e) ? std::atoll(e) : dflt;
+}
+int64_t sb_work(int prec) {
+    static const int64_t v32 = env_or("LAMG_SB_WORK32", kSBWork32), v64 = env_or("LAMG_SB_WORK64", kSBWork64);
+    return prec == 1 ? v32 : v64;
+}
+int64_t tail_work(int prec) {
+    static const int64_t v32 = env_or("LAMG_TAIL_WORK32", kTailWork32), v64 = env_or("LAMG_TAIL_WORK64", kTailWork64);
+    return prec == 1 ? v32 : v64;
+}
 
 // scratch layout (doubles)
 enum {
@@ -296,7 +311,7 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
             LAMG_CUDA(cudaMemcpyAsync(hrp.data(), V.rp.get(), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
             LAMG_CUDA(cudaStreamSynchronize(s));
             for (int p = 0; p < 2; p++) {
-                const int64_t lim = p == 0 ? kTailWork64 : kTailWork32;
+                const int64_t lim = tail_work(p);
                 auto small = [&](int c) { return (int64_t)hrp[V.cb[4 * c + 3]] - hrp[V.cb[4 * c]] <= lim; };
                 V.seg[p].clear();
                 for (int c = 0; c < S.ncolours;) {
