@@ -48,8 +48,6 @@ struct PhaseTimer {
 constexpr unsigned kFull = 0xffffffffu;
 enum { ST_U = 0, ST_S = 1, ST_A = 2, ST_D = 3 };
 enum { M_THR = 0, M_WARP = 1, M_BLK = 2 };
-constexpr int kJPBatch = 4;          // JP rounds issued between host checks
-constexpr int kJPFinish = 65536;     // remaining nodes at or below which JP finishes on the induced graph
 
 // ---------------------------------------------------------------------------
 // splitmix64 (Steele, Lea & Flood 2014): first output of the generator seeded
@@ -102,6 +100,24 @@ __device__ __forceinline__ double canon_reduce(double p) {
     if (threadIdx.x < 32) {
         double v = warp_tree(red[threadIdx.x]);
         if (threadIdx.x == 0) red[32] = v;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <int M>
+__device__ __forceinline__ int32_t reduce_sum_i32(int32_t v) {
+    if (M == M_THR) return v;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (M == M_WARP) return v;
+    __shared__ int32_t red[33];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int32_t t = red[threadIdx.x];
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+        if (threadIdx.x == 0) red[32] = t;
     }
     __syncthreads();
     return red[32];
@@ -495,25 +511,6 @@ __device__ __forceinline__ bool beats(int32_t du, uint64_t pu, int32_t u, int32_
     return pu > pv || (pu == pv && u < v);
 }
 
-// u is selected in this round iff it is uncoloured and beats every uncoloured neighbour
-template <int M>
-__device__ __forceinline__ bool jp_is_max(int32_t u, const int32_t *__restrict__ rp,
-                                          const int32_t *__restrict__ col,
-                                          const int32_t *__restrict__ colour, uint64_t key) {
-    if (colour[u] >= 0) return false;  // same value in every thread of the tier
-    const uint64_t pu = splitmix64(key + (uint64_t)u);
-    const int32_t du = rp[u + 1] - rp[u];
-    bool is_max = true;
-    for (int32_t i = rp[u] + tlane<M>(); i < rp[u + 1]; i += tstride<M>()) {
-        const int32_t v = col[i];
-        if (colour[v] < 0 && beats(rp[v + 1] - rp[v], splitmix64(key + (uint64_t)v), v, du, pu, u)) {
-            is_max = false;
-            break;
-        }
-    }
-    return reduce_all<M>(is_max);
-}
-
 // smallest colour not used by any neighbour, searched in windows of 64
 template <int M>
 __device__ __forceinline__ int32_t jp_free_colour(int32_t u, const int32_t *__restrict__ rp,
@@ -530,184 +527,143 @@ __device__ __forceinline__ int32_t jp_free_colour(int32_t u, const int32_t *__re
     }
 }
 
-template <int M>
-__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_jp_select(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
-                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            const int32_t *__restrict__ colour, uint64_t key,
-                            uint8_t *__restrict__ sel, const int32_t *__restrict__ remaining,
-                            int32_t *__restrict__ rounds) {
-    if (M == M_THR && blockIdx.x == 0 && threadIdx.x == 0 && *remaining > 0) atomicAdd(rounds, 1);
-    int32_t u;
-    if (!get_row<M>(n, list, nlist, u)) return;
-    if (M == M_THR && rp[u + 1] - rp[u] > kLongRow) return;
-    const bool r = jp_is_max<M>(u, rp, col, colour, key);
-    if (tlane<M>() == 0) sel[u] = r ? 1 : 0;
-}
 
-template <int M>
-__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_jp_assign(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
-                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            const uint8_t *__restrict__ sel, int32_t *__restrict__ colour,
-                            int32_t *__restrict__ remaining) {
-    int32_t u;
-    if (!get_row<M>(n, list, nlist, u)) return;
-    if (M == M_THR && rp[u + 1] - rp[u] > kLongRow) return;
-    if (!sel[u]) return;
-    const int32_t c = jp_free_colour<M>(u, rp, col, colour);
-    if (tlane<M>() == 0) {
-        colour[u] = c;
-        atomicSub(remaining, 1);
-    }
-}
+constexpr long long kCoopMaxSpins = 1ll << 21;  // one to two seconds of polling
 
-// ---- Last rounds on the subgraph induced by the r <= kJPFinish remaining nodes.
-// R = remaining nodes (increasing id), pos[u] = index of u in R or -1.
-// Keys for the exact priority order of the remaining nodes (LSD passes: the
-// list is already in increasing id; a stable sort by ~hash then by ~degree
-// yields decreasing (degree, hash), ties by increasing id).
-__global__ void k_jp_hashkey(const int32_t *__restrict__ R, const int32_t *__restrict__ idx, int32_t r,
-                             uint64_t key, uint64_t *__restrict__ k) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < r) k[i] = ~splitmix64(key + (uint64_t)R[idx[i]]);
-}
-
-__global__ void k_jp_degkey(const int32_t *__restrict__ R, const int32_t *__restrict__ idx, int32_t r,
-                            const int32_t *__restrict__ rp, uint64_t *__restrict__ k) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < r) {
-        const int32_t u = R[idx[i]];
-        k[i] = (uint64_t)(0x7fffffff - (rp[u + 1] - rp[u]));
-    }
-}
-
-__global__ void k_jp_rank_from_order(const int32_t *__restrict__ idx, int32_t r, int32_t *__restrict__ rank) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < r) rank[idx[i]] = i;
-}
-
-// one warp per remaining node: count its remaining neighbours (fill = 0) or
-// write (key = i * r + rank of the neighbour, value = neighbour index) and
-// set the forbidden bits of its already coloured neighbours (fill = 1).
-__global__ void k_jp_induced(const int32_t *__restrict__ R, int32_t r, const int32_t *__restrict__ rp,
-                             const int32_t *__restrict__ col, const int32_t *__restrict__ pos,
-                             const int32_t *__restrict__ rank, const int32_t *__restrict__ colour, int fill,
-                             int32_t *__restrict__ cnt, const int32_t *__restrict__ iptr,
-                             uint64_t *__restrict__ ikey, int32_t *__restrict__ ival,
-                             unsigned long long *__restrict__ forb, int32_t W) {
-    const int32_t i = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= r) return;
-    const int32_t u = R[i];
-    int32_t run = 0;
-    for (int32_t base = rp[u]; base < rp[u + 1]; base += 32) {
-        const int32_t e = base + lane;
-        int32_t j = -1;
-        if (e < rp[u + 1]) {
-            const int32_t v = col[e];
-            j = pos[v];
-            if (fill && j < 0) {
-                const int32_t c = colour[v];
-                if (c >= 0) atomicOr(&forb[(int64_t)i * W + (c >> 6)], 1ull << (c & 63));
+// Counting grid barrier of the cooperative setup kernels: bar[0] counts the
+// arrivals of the whole launch (zeroed before it); barrier e completes at
+// e * gridDim.x.  Bounded spin: on expiry (or when another block gave up) the
+// error word is set and every block returns.
+__device__ __forceinline__ bool coop_sync(unsigned int *bar, int32_t *err, unsigned int &epoch) {
+    __shared__ int bad;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bad = 0;
+        const unsigned int target = (++epoch) * gridDim.x;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        long long spins = 0;
+        while (true) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if ((++spins & 255) == 0) {
+                if (*(volatile int32_t *)err) { bad = 1; break; }
+                if (spins > kCoopMaxSpins) { atomicExch(err, 1); bad = 1; break; }
             }
         }
-        const unsigned m = __ballot_sync(kFull, j >= 0);
-        if (fill && j >= 0) {
-            const int32_t o = iptr[i] + run + __popc(m & ((1u << lane) - 1u));
-            ikey[o] = (uint64_t)i * (uint64_t)r + (uint64_t)rank[j];
-            ival[o] = j;
-        }
-        run += __popc(m);
+        __threadfence();
     }
-    if (!fill && lane == 0) cnt[i] = run;
+    __syncthreads();
+    return bad == 0;
 }
 
-// JP rounds on the induced graph in one block.  A node is selected iff the
-// first uncoloured entry of its neighbour list (sorted by decreasing priority)
-// has lower priority than itself, which is exactly "beats every uncoloured
-// neighbour".  The pointer into the list only moves forward.  Colours come
-// from the forbidden masks (coloured neighbours, set as they get coloured).
-// The active list is compacted every round (its order does not affect any
-// decision: selection, colour choice and mask updates are order-free).
-__global__ void __launch_bounds__(kBlk) k_jp_finish(const int32_t *__restrict__ R, int32_t r,
-                                                   const int32_t *__restrict__ rank, const int32_t *__restrict__ iptr,
-                                                   const int32_t *__restrict__ inb, int32_t *__restrict__ ptr,
-                                                   int32_t *__restrict__ icol, uint8_t *__restrict__ sel,
-                                                   int32_t *__restrict__ act0, int32_t *__restrict__ act1,
-                                                   unsigned long long *__restrict__ forb, int32_t W,
-                                                   int32_t *__restrict__ colour, int32_t *__restrict__ rounds_out) {
-    __shared__ int32_t na, nn, ns;
-    __shared__ int32_t sl[kBlk];   // nodes selected this round (at most one per thread and pass)
-    for (int32_t i = threadIdx.x; i < r; i += kBlk) { ptr[i] = iptr[i]; icol[i] = -1; act0[i] = i; }
-    if (threadIdx.x == 0) na = r;
-    __syncthreads();
-    int32_t *act = act0, *nxt = act1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int32_t round = 0; round <= r; round++) {
-        const int32_t m = na;
-        if (m == 0) {
-            if (threadIdx.x == 0) *rounds_out = round;
+// ---- Jones-Plassmann by wait counts.  wait[u] = number of neighbours that
+// beat u (higher priority).  Round r colours every node whose count is zero
+// -- exactly the uncoloured nodes that beat all their uncoloured neighbours,
+// i.e. the JP selection of that round -- with the smallest colour unused by
+// its (already coloured) higher-priority neighbours; then each such node
+// decrements the counts of the neighbours it beats, and a count reaching zero
+// puts that neighbour in the next round's frontier.  Every edge is examined a
+// constant number of times instead of once per round.  Frontiers are kept per
+// row tier (lst: [parity][tier], cnt: [parity][tier]); their order (atomic
+// appends) changes no decision.  out[0] = rounds.
+__global__ void k_jp_prio(int32_t n, const int32_t *__restrict__ rp, uint64_t key, int32_t *__restrict__ deg,
+                          uint64_t *__restrict__ hsh) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    deg[u] = rp[u + 1] - rp[u];
+    hsh[u] = splitmix64(key + (uint64_t)u);
+}
+
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_jp_wait(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+                                                                    const int32_t *__restrict__ rp,
+                                                                    const int32_t *__restrict__ col,
+                                                                    const int32_t *__restrict__ deg,
+                                                                    const uint64_t *__restrict__ hsh,
+                                                                    int32_t *__restrict__ wait) {
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
+    if (M == M_THR && rp[u + 1] - rp[u] > kLongRow) return;
+    const int32_t du = deg[u];
+    const uint64_t pu = hsh[u];
+    int32_t c = 0;
+    for (int32_t i = rp[u] + tlane<M>(); i < rp[u + 1]; i += tstride<M>()) {
+        const int32_t v = col[i];
+        c += beats(deg[v], hsh[v], v, du, pu, u) ? 1 : 0;
+    }
+    c = reduce_sum_i32<M>(c);
+    if (tlane<M>() == 0) wait[u] = c;
+}
+
+// frontier flags: rows of tier `tier` with no waiting count
+__global__ void k_jp_ready(const int32_t *__restrict__ rp, int64_t n, int tier, const int32_t *__restrict__ wait,
+                           uint8_t *__restrict__ f) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    f[u] = (wait[u] == 0 && row_tier(rp[u + 1] - rp[u]) == tier) ? 1 : 0;
+}
+
+// decrement the counts of the neighbours that u beats; append those that reach zero
+template <int M>
+__device__ __forceinline__ void jp_release(int32_t u, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                           const int32_t *__restrict__ deg, const uint64_t *__restrict__ hsh,
+                                           int32_t *__restrict__ wait, int32_t *nlst, int64_t cap, int32_t *nxt) {
+    const int32_t du = deg[u];
+    const uint64_t pu = hsh[u];
+    for (int32_t i = rp[u] + tlane<M>(); i < rp[u + 1]; i += tstride<M>()) {
+        const int32_t v = col[i];
+        if (!beats(du, pu, u, deg[v], hsh[v], v)) continue;
+        if (atomicSub(&wait[v], 1) == 1) {
+            const int t = row_tier(deg[v]);
+            nlst[(int64_t)t * cap + atomicAdd(&nxt[t], 1)] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                const int32_t *__restrict__ deg, const uint64_t *__restrict__ hsh,
+                                                int32_t *__restrict__ wait, int32_t *__restrict__ colour, int32_t *lst,
+                                                int64_t cap, int32_t *cnt, int32_t *out, unsigned int *bar,
+                                                int32_t *err) {
+    const int64_t nthr = (int64_t)gridDim.x * kBlk, tid = (int64_t)blockIdx.x * kBlk + threadIdx.x;
+    const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    const int lane = threadIdx.x & 31;
+    unsigned int epoch = 0;
+    for (int32_t r = 0;; r++) {
+        const volatile int32_t *cur = cnt + (r & 1) * 3;
+        int32_t *nxt = cnt + ((r + 1) & 1) * 3;
+        const int32_t c0 = cur[0], c1 = cur[1], c2 = cur[2];
+        if (c0 + c1 + c2 == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = r;
             return;
         }
-        for (int32_t t = threadIdx.x; t < m; t += kBlk) {
-            const int32_t i = act[t];
-            int32_t p = ptr[i];
-            while (p < iptr[i + 1] && icol[inb[p]] >= 0) p++;
-            ptr[i] = p;
-            sel[i] = (p == iptr[i + 1] || rank[inb[p]] > rank[i]) ? 1 : 0;
+        const int32_t *L0 = lst + (int64_t)(r & 1) * 3 * cap, *L1 = L0 + cap, *L2 = L1 + cap;
+        int32_t *N = lst + (int64_t)((r + 1) & 1) * 3 * cap;
+        // colour the frontier: its higher-priority neighbours are all coloured
+        for (int64_t i = tid; i < c0; i += nthr) {
+            const int32_t u = L0[i];
+            colour[u] = jp_free_colour<M_THR>(u, rp, col, colour);
         }
-        if (threadIdx.x == 0) nn = 0;
-        __syncthreads();
-        // colour the selected nodes and queue the rest; then spread each selected
-        // node's mask updates over a warp (hubs have long induced lists).  The
-        // selected nodes are handled in passes of at most kBlk.
-        for (int32_t base = 0; base < m; base += kBlk) {
-            if (threadIdx.x == 0) ns = 0;
-            __syncthreads();
-            const int32_t t = base + threadIdx.x;
-            if (t < m) {
-                const int32_t i = act[t];
-                if (sel[i]) {
-                    int32_t c = -1;
-                    for (int32_t wd = 0; wd < W && c < 0; wd++) {
-                        const unsigned long long mk = forb[(int64_t)i * W + wd];
-                        if (mk != ~0ull) c = wd * 64 + __ffsll((long long)~mk) - 1;
-                    }
-                    icol[i] = c;
-                    colour[R[i]] = c;
-                    sl[atomicAdd(&ns, 1)] = i;
-                } else {
-                    nxt[atomicAdd(&nn, 1)] = i;
-                }
-            }
-            __syncthreads();
-            for (int32_t k = warp; k < ns; k += kBlk / 32) {
-                const int32_t i = sl[k];
-                const int32_t c = icol[i];
-                for (int32_t q = iptr[i] + lane; q < iptr[i + 1]; q += 32)
-                    atomicOr(&forb[(int64_t)inb[q] * W + (c >> 6)], 1ull << (c & 63));
-            }
-            __syncthreads();
+        for (int64_t i = wid; i < c1; i += nwarp) {
+            const int32_t u = L1[i];
+            const int32_t c = jp_free_colour<M_WARP>(u, rp, col, colour);
+            if (lane == 0) colour[u] = c;
         }
-        if (threadIdx.x == 0) na = nn;
-        int32_t *tp = act; act = nxt; nxt = tp;
-        __syncthreads();
+        for (int64_t i = blockIdx.x; i < c2; i += gridDim.x) {
+            const int32_t u = L2[i];
+            const int32_t c = jp_free_colour<M_BLK>(u, rp, col, colour);
+            if (threadIdx.x == 0) colour[u] = c;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) { nxt[0] = 0; nxt[1] = 0; nxt[2] = 0; }
+        if (!coop_sync(bar, err, epoch)) return;
+        // release the neighbours they beat
+        for (int64_t i = tid; i < c0; i += nthr) jp_release<M_THR>(L0[i], rp, col, deg, hsh, wait, N, cap, nxt);
+        for (int64_t i = wid; i < c1; i += nwarp) jp_release<M_WARP>(L1[i], rp, col, deg, hsh, wait, N, cap, nxt);
+        for (int64_t i = blockIdx.x; i < c2; i += gridDim.x) jp_release<M_BLK>(L2[i], rp, col, deg, hsh, wait, N, cap, nxt);
+        if (!coop_sync(bar, err, epoch)) return;
     }
-    if (threadIdx.x == 0) *rounds_out = -1;  // not reached: every round colours a node
-}
-
-__global__ void k_iota32(int32_t *__restrict__ a, int32_t n) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = i;
-}
-
-__global__ void k_uncoloured(const int32_t *__restrict__ colour, int32_t n, uint8_t *__restrict__ f) {
-    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u < n) f[u] = colour[u] < 0 ? 1 : 0;
-}
-
-__global__ void k_pos_scatter(const int32_t *__restrict__ R, int32_t r, int32_t *__restrict__ pos) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < r) pos[R[i]] = i;
 }
 
 __global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
@@ -829,36 +785,6 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweep_tail(int32_t c0, int32_t c1, 
 // __syncthreads between colours; other colours are spread over every block,
 // with a bounded grid barrier after each.  The row updates and their order
 // within a colour are those of the per-colour launches (bit-identical).
-constexpr long long kTvMaxSpins = 1ll << 23;
-
-__device__ __forceinline__ bool tv_grid_sync(unsigned int *bar, int32_t *err) {
-    __shared__ int bad;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        bad = 0;
-        volatile unsigned int *vgen = bar + 1;
-        const unsigned int gen = *vgen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if ((++spins & 63) == 0) {
-                    if (*(volatile int32_t *)err) { bad = 1; break; }
-                    if (spins > kTvMaxSpins) { atomicExch(err, 1); bad = 1; break; }
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return bad == 0;
-}
-
 __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const int32_t *__restrict__ plan,
                                                          int32_t nplan, const int32_t *__restrict__ cb,
                                                          const int32_t *__restrict__ order,
@@ -869,6 +795,7 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const 
     const int warp = threadIdx.x >> 5;
     const int64_t nthr = (int64_t)gridDim.x * kBlk, tid = (int64_t)blockIdx.x * kBlk + threadIdx.x;
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    unsigned int epoch = 0;
     for (int32_t sw = 0; sw < nsweeps; sw++) {
         for (int32_t q = 0; q < nplan; q++) {
             const int32_t c0 = plan[3 * q], c1 = plan[3 * q + 1], single = plan[3 * q + 2];
@@ -888,7 +815,7 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const 
                 for (int64_t i = t1 + wid; i < t2; i += nwarp) tv_update<M_WARP>(order[i], rp, col, w, diag, K, X);
                 for (int64_t i = t2 + blockIdx.x; i < t3; i += gridDim.x) tv_update<M_BLK>(order[i], rp, col, w, diag, K, X);
             }
-            if (!tv_grid_sync(bar, err)) return;
+            if (!coop_sync(bar, err, epoch)) return;
         }
     }
 }
@@ -1217,78 +1144,59 @@ static void build_tiers(const int32_t *rp, int32_t n, Tiers &t, cudaStream_t s) 
 static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s) {
     const int32_t n = L.n;
     L.colour.alloc(n);
-    Tmp<uint8_t> sel(n, s);
-    Tmp<int32_t> ctr(2, s);  // remaining, rounds
     k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, -1);
     LAMG_CHECK_LAUNCH();
-    const int32_t init[2] = {n, 0};
-    LAMG_CUDA(cudaMemcpyAsync(ctr.get(), init, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     const uint64_t key = colour_key(h->opt.seed, level);
-    int32_t *remaining = ctr.get(), *rounds = ctr.get() + 1;
-    int32_t left = n;
-    for (int batch = 0; left > kJPFinish; batch++) {
-        LAMG_REQUIRE(batch < 1000000, LAMG_ERR_CUDA, "colouring did not terminate");
-        for (int r = 0; r < kJPBatch; r++) {
-            LAUNCH3(k_jp_select, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
-                    L.col.get(), L.colour.get(), key, sel.get(), remaining, rounds);
-            LAUNCH3(k_jp_assign, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
-                    L.col.get(), sel.get(), L.colour.get(), remaining);
+    PhaseTimer ct(s);
+    ct.level = level;
+    int32_t batch_rounds = 0;
+    const int32_t fin_rounds = 0;
+    {
+    // wait counts, the first frontier, then all rounds in one cooperative launch
+    Tmp<int32_t> deg(n, s), wait(n, s);
+    Tmp<uint64_t> hsh(n, s);
+    k_jp_prio<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), key, deg.get(), hsh.get());
+    LAMG_CHECK_LAUNCH();
+    LAUNCH3(k_jp_wait, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
+            deg.get(), hsh.get(), wait.get());
+    const int64_t cap = n;
+    Tmp<int32_t> lst(6 * (size_t)cap, s), fcnt(6, s), out(1, s), err(1, s);
+    Tmp<unsigned int> bar(2, s);
+    int32_t c6[6] = {0, 0, 0, 0, 0, 0};
+    {
+        Tmp<uint8_t> f(n, s);
+        for (int t = 0; t < 3; t++) {
+            k_jp_ready<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), n, t, wait.get(), f.get());
+            LAMG_CHECK_LAUNCH();
+            c6[t] = (int32_t)compact_indices(f.get(), lst.get() + t * cap, n, s);
         }
-        left = read_scalar(remaining, s);
     }
-    const int32_t batch_rounds = read_scalar(rounds, s);
-    int32_t fin_rounds = 0;
-    if (left > 0) {
-        const int32_t r = left;
-        Tmp<int32_t> R(n, s), pos(n, s), rank(r, s), cnt(r + 1, s), iptr(r + 1, s), ptr(r, s), icol(r, s);
-        Tmp<uint8_t> uncol(n, s), fsel(r, s);
-        k_uncoloured<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, uncol.get());
-        LAMG_CHECK_LAUNCH();
-        const int32_t rr = (int32_t)compact_indices(uncol.get(), R.get(), n, s);
-        LAMG_REQUIRE(rr == r, LAMG_ERR_CUDA, "colouring: remaining count mismatch");
-        const int32_t maxc = reduce_max_i32(L.colour.get(), n, s);
-        const int32_t W = (maxc + 1 + r + 63) / 64 + 1;
-        Tmp<unsigned long long> forb((size_t)r * W, s);
-        LAMG_CUDA(cudaMemsetAsync(forb.get(), 0, sizeof(unsigned long long) * (size_t)r * W, s));
-        k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(pos.get(), n, -1);
-        LAMG_CHECK_LAUNCH();
-        k_pos_scatter<<<ceil_div(r, 256), 256, 0, s>>>(R.get(), r, pos.get());
-        LAMG_CHECK_LAUNCH();
-        {
-            // exact priority order of the remaining nodes by two stable passes
-            Tmp<uint64_t> pk(r, s), pkt(r, s);
-            Tmp<int32_t> idx(r, s), idt(r, s);
-            k_iota32<<<ceil_div(r, 256), 256, 0, s>>>(idx.get(), r);
-            LAMG_CHECK_LAUNCH();
-            k_jp_hashkey<<<ceil_div(r, 256), 256, 0, s>>>(R.get(), idx.get(), r, key, pk.get());
-            LAMG_CHECK_LAUNCH();
-            radix_sort_pairs<uint64_t, int32_t>(pk.get(), idx.get(), pkt.get(), idt.get(), r, 64, s);
-            k_jp_degkey<<<ceil_div(r, 256), 256, 0, s>>>(R.get(), idx.get(), r, L.rp.get(), pk.get());
-            LAMG_CHECK_LAUNCH();
-            radix_sort_pairs<uint64_t, int32_t>(pk.get(), idx.get(), pkt.get(), idt.get(), r, 31, s);
-            k_jp_rank_from_order<<<ceil_div(r, 256), 256, 0, s>>>(idx.get(), r, rank.get());
-            LAMG_CHECK_LAUNCH();
-        }
-        k_jp_induced<<<ceil_div((int64_t)r * 32, 256), 256, 0, s>>>(R.get(), r, L.rp.get(), L.col.get(), pos.get(),
-                                                                   rank.get(), L.colour.get(), 0, cnt.get(), nullptr,
-                                                                   nullptr, nullptr, forb.get(), W);
-        LAMG_CHECK_LAUNCH();
-        LAMG_CUDA(cudaMemsetAsync(cnt.get() + r, 0, sizeof(int32_t), s));
-        exclusive_scan_i32(cnt.get(), iptr.get(), r + 1, s);
-        const int32_t ne = read_scalar(iptr.get() + r, s);
-        Tmp<uint64_t> ikey(ne, s), iktmp(ne, s);
-        Tmp<int32_t> inb(ne, s), ivtmp(ne, s), act0(r, s), act1(r, s);
-        k_jp_induced<<<ceil_div((int64_t)r * 32, 256), 256, 0, s>>>(R.get(), r, L.rp.get(), L.col.get(), pos.get(),
-                                                                   rank.get(), L.colour.get(), 1, nullptr, iptr.get(),
-                                                                   ikey.get(), inb.get(), forb.get(), W);
-        LAMG_CHECK_LAUNCH();
-        radix_sort_pairs<uint64_t, int32_t>(ikey.get(), inb.get(), iktmp.get(), ivtmp.get(), ne,
-                                            bits_for((uint64_t)r * (uint64_t)r - 1), s);
-        k_jp_finish<<<1, kBlk, 0, s>>>(R.get(), r, rank.get(), iptr.get(), inb.get(), ptr.get(), icol.get(),
-                                       fsel.get(), act0.get(), act1.get(), forb.get(), W, L.colour.get(), rounds);
-        LAMG_CHECK_LAUNCH();
-        fin_rounds = read_scalar(rounds, s);
-        LAMG_REQUIRE(fin_rounds >= 0, LAMG_ERR_CUDA, "colouring: finish kernel failed");
+    LAMG_CUDA(cudaMemcpyAsync(fcnt.get(), c6, sizeof(c6), cudaMemcpyHostToDevice, s));
+    LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
+    LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, sms = 0, per = 0;
+        LAMG_CUDA(cudaGetDevice(&dev));
+        LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jp_dag, kBlk, 0));
+        LAMG_REQUIRE(per >= 1, LAMG_ERR_CUDA, "colouring kernel cannot be resident");
+        grid = sms;
+    }
+    {
+        const int32_t *rpp = L.rp.get(), *colp = L.col.get(), *dp = deg.get();
+        const uint64_t *hp = hsh.get();
+        int32_t *wp = wait.get(), *colour = L.colour.get(), *lp = lst.get(), *cp = fcnt.get(), *op = out.get(),
+                *ep = err.get();
+        int64_t capv = cap;
+        unsigned int *bp = bar.get();
+        void *args[] = {&rpp, &colp, &dp, &hp, &wp, &colour, &lp, &capv, &cp, &op, &bp, &ep};
+        LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_jp_dag, dim3(grid), dim3(kBlk), args, 0, s));
+        note_launch();
+    }
+    LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "colouring: grid barrier timed out");
+    batch_rounds = read_scalar(out.get(), s);
+    ct.mark("jp_rounds");
     }
     L.jp_rounds = batch_rounds + fin_rounds;
     L.ncolours = reduce_max_i32(L.colour.get(), n, s) + 1;
@@ -1381,6 +1289,15 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, c
             grid = sms;
         }
         int32_t nsw = o.nu_tv, npl = (int32_t)(plan.size() / 3);
+        if (const char *e = std::getenv("LAMG_TIMING"); e && e[0] == '1') {
+            int singles = 0, maxdeg = 0;
+            for (int32_t q = 0; q < npl; q++) singles += plan[3 * q + 2];
+            std::vector<int32_t> hrp(n + 1);
+            LAMG_CUDA(cudaMemcpy(hrp.data(), L.rp.get(), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+            for (int32_t u = 0; u < n; u++) maxdeg = std::max(maxdeg, hrp[u + 1] - hrp[u]);
+            std::fprintf(stderr, "lamg-timing level %d tv plan: %d phases (%d single-block runs), K %d, max degree %d\n",
+                         level, npl, singles, K, maxdeg);
+        }
         const int32_t *pp = dplan.get(), *cbp = L.cb_dev.get(), *rpp = L.rp.get(), *colp = L.col.get();
         const double *wp = L.w.get();
         unsigned int *barp = bar.get();
