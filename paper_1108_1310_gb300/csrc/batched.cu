@@ -239,7 +239,7 @@ template <class T>
 __device__ __forceinline__ void sweep_colour4(const MRArgs<T> &a, const MKLevel<T> &L, int c, int bid, int nb) {
     const int32_t t0 = L.cb[4 * c], t1 = L.cb[4 * c + 1], t2 = L.cb[4 * c + 2], t3 = L.cb[4 * c + 3];
     const int G = a.groups, lg = a.lg, ld = a.ld;
-    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     for (int64_t q = (int64_t)t0 * G + tid; q < (int64_t)t1 * G; q += nthr)
         gs_row4<M_THR, T>((int32_t)(q >> lg), (int)(q & (G - 1)), L, ld);
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
@@ -253,7 +253,7 @@ template <class T, class U>
 __device__ __forceinline__ void residual4(const MRArgs<U> &a, const MKLevel<T> &L, const T *b, const T *x, T *r,
                                           T *xs, T *rs, int bid, int nb) {
     const int G = a.groups, lg = a.lg, ld = a.ld;
-    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     for (int64_t q = tid; q < (int64_t)L.n * G; q += nthr) {
         const int32_t i = (int32_t)(q >> lg);
         if (L.rp[i + 1] - L.rp[i] > kLongRow) continue;
@@ -268,7 +268,7 @@ __device__ __forceinline__ void residual4(const MRArgs<U> &a, const MKLevel<T> &
 
 template <class T>
 __device__ void exec_op4(const MRArgs<T> &a, MRShared &S, const Op &op, int bid, int nb) {
-    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     const int G = a.groups, lg = a.lg, ld = a.ld;
     const int g = (int)(tid & (G - 1));
     const MKLevel<T> &L = a.lv[op.level];

@@ -31,7 +31,7 @@ namespace lamg {
 template <class T>
 __device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid, int nb) {
     const int32_t t0 = L.cb[4 * c], t1 = L.cb[4 * c + 1], t2 = L.cb[4 * c + 2], t3 = L.cb[4 * c + 3];
-    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     for (int64_t i = t0 + tid; i < t1; i += nthr) gs_row<M_THR, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
     for (int64_t i = t1 + wid; i < t2; i += nwarp) gs_row<M_WARP, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
@@ -41,7 +41,7 @@ __device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid
 template <class T>
 __device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const T *x, T *r, T *xs, T *rs, int bid,
                                          int nb) {
-    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     for (int64_t i = tid; i < L.n; i += nthr) {
         const int32_t ii = (int32_t)i;
         if (L.rp[ii + 1] - L.rp[ii] > kLongRow) continue;
@@ -63,7 +63,7 @@ __device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const 
 
 template <class T>
 __device__ __forceinline__ void restrict_op(const MKLevel<T> &F, const MKLevel<T> &C, T mu, int bid, int nb) {
-    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     for (int64_t J = tid; J < C.n; J += nthr) {
         const int32_t jj = (int32_t)J;
         C.x[jj] = T(0);
@@ -104,7 +104,7 @@ __device__ __forceinline__ void tail_pre_row(int32_t i, const MKLevel<T> &L) {
 
 template <class T>
 __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
-    const int64_t nthr = (int64_t)nb * blockDim.x, tid = (int64_t)bid * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     const MKLevel<T> &L = a.lv[op.level];
     switch (op.type) {
         case OP_SWEEP:

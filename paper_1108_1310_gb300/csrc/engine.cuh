@@ -104,6 +104,14 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // grid barrier (bounded spin)
 // ---------------------------------------------------------------------------
 
+// Thread index of a grid-wide op executed by nb blocks (this one is bid) that
+// deals work out in chunks of 32 consecutive items, consecutive chunks going to
+// consecutive blocks: a warp's items stay contiguous (coalesced) while even a
+// small op spreads over every SM.  (tid >> 5) is the matching warp index.
+__device__ __forceinline__ int64_t spread_tid(int bid, int nb) {
+    return ((int64_t)(threadIdx.x >> 5) * nb + bid) * 32 + (threadIdx.x & 31);
+}
+
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

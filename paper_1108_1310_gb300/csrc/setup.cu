@@ -14,6 +14,7 @@
 //    warp reduces its 32 partials by the same halving tree, then warp 0
 //    reduces the 32 warp results by it again.
 // Kernels are therefore templated on the row tier M (thread / warp / block).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -627,7 +628,9 @@ __global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp,
                                                 int32_t *__restrict__ wait, int32_t *__restrict__ colour, int32_t *lst,
                                                 int64_t cap, int32_t *cnt, int32_t *out, unsigned int *bar,
                                                 int32_t *err) {
-    const int64_t nthr = (int64_t)gridDim.x * kBlk, tid = (int64_t)blockIdx.x * kBlk + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * kBlk;
+    // chunks of 32 items, consecutive chunks on consecutive blocks (spread over every SM)
+    const int64_t tid = ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
     const int lane = threadIdx.x & 31;
     unsigned int epoch = 0;
@@ -791,13 +794,18 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const 
                                                          const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                                          const double *__restrict__ w, const double *__restrict__ diag,
                                                          int32_t K, double *__restrict__ X, unsigned int *bar,
-                                                         int32_t *err) {
-    const int warp = threadIdx.x >> 5;
-    const int64_t nthr = (int64_t)gridDim.x * kBlk, tid = (int64_t)blockIdx.x * kBlk + threadIdx.x;
+                                                         int32_t *err, double *__restrict__ gsum,
+                                                         unsigned long long *__restrict__ ptime) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nthr = (int64_t)gridDim.x * kBlk;
+    // chunks of 32 items, consecutive chunks on consecutive blocks (spread over every SM)
+    const int64_t tid = ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
     unsigned int epoch = 0;
     for (int32_t sw = 0; sw < nsweeps; sw++) {
         for (int32_t q = 0; q < nplan; q++) {
+            unsigned long long t_start = 0;
+            if (ptime && blockIdx.x == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
             const int32_t c0 = plan[3 * q], c1 = plan[3 * q + 1], single = plan[3 * q + 2];
             if (single) {
                 if (blockIdx.x == 0) {
@@ -813,9 +821,51 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const 
                 const int32_t t0 = cb[4 * c0], t1 = cb[4 * c0 + 1], t2 = cb[4 * c0 + 2], t3 = cb[4 * c0 + 3];
                 for (int64_t i = t0 + tid; i < t1; i += nthr) tv_update<M_THR>(order[i], rp, col, w, diag, K, X);
                 for (int64_t i = t1 + wid; i < t2; i += nwarp) tv_update<M_WARP>(order[i], rp, col, w, diag, K, X);
-                for (int64_t i = t2 + blockIdx.x; i < t3; i += gridDim.x) tv_update<M_BLK>(order[i], rp, col, w, diag, K, X);
+                // Block-tier rows (hubs): the 1024 lane partials of the canonical order
+                // come in 32 groups of 32 lanes; each group is one warp's work item
+                // anywhere on the GPU (its lane partials, then the group's tree), so a
+                // hub's FP64 work spreads over many SMs.  After a barrier one warp per
+                // row adds the 32 group sums by the same tree (R1 order, bit-identical).
+                const int32_t nbr = t3 - t2;
+                if (nbr > 0) {
+                    for (int64_t it = wid; it < (int64_t)nbr * 32; it += nwarp) {
+                        const int32_t r = (int32_t)(it >> 5), g = (int32_t)(it & 31);
+                        const int32_t u = order[t2 + r];
+                        double acc[16];
+#pragma unroll
+                        for (int k = 0; k < 16; k++) acc[k] = 0.0;
+                        for (int32_t j = rp[u] + 32 * g + lane; j < rp[u + 1]; j += kBlk) {
+                            const double wj = w[j];
+                            const double *xv = X + (int64_t)col[j] * K;
+#pragma unroll
+                            for (int k = 0; k < 16; k++)
+                                if (k < K) acc[k] = acc[k] + wj * xv[k];
+                        }
+#pragma unroll
+                        for (int k = 0; k < 16; k++) {
+                            if (k < K) {
+                                const double t = warp_tree(acc[k]);
+                                if (lane == 0) gsum[((int64_t)r * 32 + g) * K + k] = t;
+                            }
+                        }
+                    }
+                    if (!coop_sync(bar, err, epoch)) return;
+                    for (int64_t r = wid; r < nbr; r += nwarp) {
+                        const int32_t u = order[t2 + r];
+                        const double du = diag[u];
+                        for (int k = 0; k < K; k++) {
+                            const double t = warp_tree(gsum[((int64_t)r * 32 + lane) * K + k]);
+                            if (lane == 0) X[(int64_t)u * K + k] = t / du;
+                        }
+                    }
+                }
             }
             if (!coop_sync(bar, err, epoch)) return;
+            if (ptime && blockIdx.x == 0 && threadIdx.x == 0) {
+                unsigned long long t_end;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+                ptime[q] += t_end - t_start;
+            }
         }
     }
 }
@@ -1273,6 +1323,10 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, c
                 c++;
             }
         }
+        int32_t maxbr = 0;
+        for (size_t q = 0; q < plan.size(); q += 3)
+            if (!plan[q + 2]) maxbr = std::max(maxbr, L.cb[4 * plan[q] + 3] - L.cb[4 * plan[q] + 2]);
+        Tmp<double> gsum((size_t)maxbr * 32 * K, s);
         Tmp<int32_t> dplan(plan.size(), s);
         Tmp<unsigned int> bar(2, s);
         Tmp<int32_t> err(1, s);
@@ -1303,10 +1357,32 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, c
         unsigned int *barp = bar.get();
         int32_t *errp = err.get();
         int32_t Kv = K;
-        void *args[] = {&nsw, &pp, &npl, &cbp, &ord, &rpp, &colp, &wp, &diag, &Kv, &X, &barp, &errp};
+        double *gp = gsum.get();
+        const char *te = std::getenv("LAMG_TIMING");
+        const bool tprof = te && te[0] == '2';   // per-phase times (development aid)
+        Tmp<unsigned long long> ptime(tprof ? npl : 0, s);
+        if (tprof) LAMG_CUDA(cudaMemsetAsync(ptime.get(), 0, sizeof(unsigned long long) * npl, s));
+        unsigned long long *tp = ptime.get();
+        void *args[] = {&nsw, &pp, &npl, &cbp, &ord, &rpp, &colp, &wp, &diag, &Kv, &X, &barp, &errp, &gp, &tp};
         LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_tv_sweeps_coop, dim3(grid), dim3(kBlk), args, 0, s));
         note_launch();
         LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "TV sweep: grid barrier timed out");
+        if (tprof) {
+            std::vector<unsigned long long> ht(npl);
+            LAMG_CUDA(cudaMemcpy(ht.data(), ptime.get(), sizeof(unsigned long long) * npl, cudaMemcpyDeviceToHost));
+            std::vector<int> idx(npl);
+            for (int q = 0; q < npl; q++) idx[q] = q;
+            std::sort(idx.begin(), idx.end(), [&](int a, int b) { return ht[a] > ht[b]; });
+            unsigned long long tot = 0;
+            for (auto v : ht) tot += v;
+            std::fprintf(stderr, "lamg-tvphase level %d total %.3f ms over %d phases\n", level, tot * 1e-6, npl);
+            for (int k = 0; k < std::min(npl, 12); k++) {
+                const int q = idx[k], c = plan[3 * q];
+                std::fprintf(stderr, "lamg-tvphase level %d colour %d single %d: %.1f us; rows thr %d warp %d blk %d, entries %d\n",
+                             level, c, plan[3 * q + 2], ht[q] * 1e-3, L.cb[4 * c + 1] - L.cb[4 * c],
+                             L.cb[4 * c + 2] - L.cb[4 * c + 1], L.cb[4 * c + 3] - L.cb[4 * c + 2], ent[c]);
+            }
+        }
         return INFINITY;
     }
     for (int sw = 1; sw <= o.nu_tv; sw++) {
