@@ -315,22 +315,55 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             for (int32_t k = threadIdx.x; k <= tnc; k += blockDim.x) scb[k] = L.tcb[k];
             __syncthreads();
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+            // entry range [k0, k1) of chunk q of the colour with rows [R0, R1)
+            auto chunk = [&](int32_t q, int32_t R0, int32_t R1, int32_t &k0, int32_t &k1) {
+                int32_t lo = R0, hi = R1 - 1;   // last row of the colour whose first chunk is <= q
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi + 1) >> 1;
+                    if (srq[mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                k0 = srp[lo] + (q - srq[lo]) * kTailChunk;
+                k1 = min(k0 + kTailChunk, srp[lo + 1]);
+            };
+            // the entries (column, weight) of this warp's first chunk of the next colour are
+            // loaded while the current colour finishes (they do not depend on x)
+            constexpr int kPer = kTailChunk / 32;
+            int32_t pc[kPer];
+            T pw[kPer];
+            int32_t pk0 = 0, pk1 = 0;
+            auto prefetch = [&](int32_t c) {
+                pk0 = pk1 = 0;
+                if (c >= tnc) return;
+                const int32_t R0 = scb[c], R1 = scb[c + 1], q = srq[R0] + warp;
+                if (q >= srq[R1]) return;
+                chunk(q, R0, R1, pk0, pk1);
+#pragma unroll
+                for (int m = 0; m < kPer; m++) {
+                    const int32_t k = pk0 + lane + 32 * m;
+                    pc[m] = k < pk1 ? tcol[k] : 0;
+                    pw[m] = k < pk1 ? tw[k] : T(0);
+                }
+            };
+            prefetch(0);
             for (int32_t c = 0; c < tnc; c++) {
                 const int32_t R0 = scb[c], R1 = scb[c + 1], Q0 = srq[R0], Q1 = srq[R1];
-                for (int32_t q = Q0 + warp; q < Q1; q += nw) {
-                    int32_t lo = R0, hi = R1 - 1;   // last row of the colour whose first chunk is <= q
-                    while (lo < hi) {
-                        const int32_t mid = (lo + hi + 1) >> 1;
-                        if (srq[mid] <= q) lo = mid; else hi = mid - 1;
-                    }
-                    const int32_t k0 = srp[lo] + (q - srq[lo]) * kTailChunk;
-                    const int32_t k1 = min(k0 + kTailChunk, srp[lo + 1]);
+                if (Q0 + warp < Q1) {   // the prefetched first chunk
+                    T acc = T(0);
+#pragma unroll
+                    for (int m = 0; m < kPer; m++) acc += pw[m] * sx[pc[m]];
+                    acc = warp_allsum(acc);
+                    if (lane == 0) cpart[warp] = acc;
+                }
+                for (int32_t q = Q0 + warp + nw; q < Q1; q += nw) {
+                    int32_t k0, k1;
+                    chunk(q, R0, R1, k0, k1);
                     T acc = T(0);
 #pragma unroll 4
                     for (int32_t k = k0 + lane; k < k1; k += 32) acc += tw[k] * sx[tcol[k]];
                     acc = warp_allsum(acc);
                     if (lane == 0) cpart[q - Q0] = acc;
                 }
+                prefetch(c + 1);
                 __syncthreads();
                 for (int32_t li = R0 + threadIdx.x; li < R1; li += blockDim.x) {
                     T acc = T(0);
