@@ -78,7 +78,7 @@ typedef struct {
     int32_t  max_rounds;       /* aggregation stages per level: 8                       */
     int32_t  max_levels;       /* depth limit: 100                                      */
     int32_t  dense_max;        /* largest coarsest level solved by the dense inverse: 1024 */
-    int32_t  coarse_sweeps;    /* GS sweeps when the coarsest level is larger: 20      */
+    int32_t  coarse_sweeps;    /* GS sweeps when the coarsest level is larger: 5       */
     double   mu_flat;          /* flat energy correction (Eq. (3.10), Q = 2): 4/3      */
     uint64_t seed;             /* seed of the counter-based generator: 1               */
     int32_t  adaptive;         /* 1: iterate recombination (Eq. (3.13)); 0: flat mu    */

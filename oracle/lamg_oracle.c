@@ -34,7 +34,7 @@ void orc_default_opts(orc_opts *o) {
     o->max_rounds = 8;
     o->max_levels = 100;
     o->dense_max = 1024;
-    o->coarse_sweeps = 20;
+    o->coarse_sweeps = 5;
     o->mu_flat = 4.0 / 3.0;    /* Eq. (3.10) with Q = 2 */
     o->seed = 1;
 }

@@ -119,7 +119,7 @@ void lamg_default_options(lamg_options *o) {
     o->max_rounds = 8;
     o->max_levels = 100;
     o->dense_max = 1024;
-    o->coarse_sweeps = 20;
+    o->coarse_sweeps = 5;
     o->mu_flat = 4.0 / 3.0;
     o->seed = 1;
     o->adaptive = 1;
