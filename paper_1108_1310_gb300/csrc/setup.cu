@@ -738,7 +738,22 @@ __device__ __forceinline__ void tv_update(int32_t u, const int32_t *__restrict__
     double acc[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) acc[k] = 0.0;
-    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
+    // two entries per step (their loads overlap); each lane still adds its
+    // entries in increasing order, so the canonical partial is unchanged
+    const int32_t st = tstride<M>();
+    int32_t j = s + tlane<M>();
+    for (; j + st < e; j += 2 * st) {
+        const double w0 = w[j], w1 = w[j + st];
+        const double *x0 = X + (int64_t)col[j] * K, *x1 = X + (int64_t)col[j + st] * K;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (k < K) {
+                const double a = x0[k], b = x1[k];
+                acc[k] = acc[k] + w0 * a;
+                acc[k] = acc[k] + w1 * b;
+            }
+    }
+    if (j < e) {
         const double wj = w[j];
         const double *xv = X + (int64_t)col[j] * K;
 #pragma unroll
@@ -834,7 +849,20 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const 
                         double acc[16];
 #pragma unroll
                         for (int k = 0; k < 16; k++) acc[k] = 0.0;
-                        for (int32_t j = rp[u] + 32 * g + lane; j < rp[u + 1]; j += kBlk) {
+                        int32_t j = rp[u] + 32 * g + lane;
+                        const int32_t je = rp[u + 1];
+                        for (; j + kBlk < je; j += 2 * kBlk) {   // two entries per step, same order
+                            const double w0 = w[j], w1 = w[j + kBlk];
+                            const double *x0 = X + (int64_t)col[j] * K, *x1 = X + (int64_t)col[j + kBlk] * K;
+#pragma unroll
+                            for (int k = 0; k < 16; k++)
+                                if (k < K) {
+                                    const double a = x0[k], b = x1[k];
+                                    acc[k] = acc[k] + w0 * a;
+                                    acc[k] = acc[k] + w1 * b;
+                                }
+                        }
+                        if (j < je) {
                             const double wj = w[j];
                             const double *xv = X + (int64_t)col[j] * K;
 #pragma unroll
