@@ -36,9 +36,9 @@ WORKLOADS = {
 }
 TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10}
 # DRAM bytes (read + write) of one engine launch from one ncu capture of this
-# workload (profiles/k_engine_chung_lu1m_fp32ir.md); must be reset to None
+# workload (profiles/k_engine_chung_lu1m_fp32ir.md); must be emptied
 # whenever the engine kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("chung_lu1m", "fp32ir"): 1.452e9}
 # batched forms (many right-hand sides on one hierarchy; many graphs as one union)
 BATCHED = {
     "rgg2m_b64": "64 zero-sum Gaussian RHS on a 2M-node 2-D RGG (mean degree 12, w = exp(-d^2/r^2), FP32); "
