@@ -157,6 +157,21 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def slowest_rank_ms(ms, dist, device):
+    """Max over ranks of a per-rank step time (replicas: the job ends with its slowest rank)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank_step, ms):
+    """Whole-job throughput: every rank processes the same units per step (weak scaling)."""
+    return world * units_per_rank_step / (ms / 1e3)
+
+
 def run_batched(args, L, W, torch, dev, stream, rank, world):
     """One step = setup + solve of every right-hand side / every graph to 1e-8."""
     tol = 1e-8
@@ -340,13 +355,9 @@ def main():
     if dist:
         dist.barrier()
     times = [a.elapsed_time(bb) for a, bb in evs]
-    ms = sum(times) / len(times)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = slowest_rank_ms(sum(times) / len(times), dist, dev)
     cycles = sum(s.cycles for s in stats) / len(stats)
-    value = world * g.m * cycles / (ms / 1e3)
+    value = job_value(world, g.m * cycles, ms)
 
     # plain FP64 on the same workload, same accuracy (context for the IR form)
     fp64 = None
