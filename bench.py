@@ -188,9 +188,17 @@ def run_batched(args, L, W, torch, dev, stream, rank, world):
     opt = L.lamg_default_options(validate=1, max_cycles=2000)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    tuned = {}
+
     def setup():
         if gptr is None:
-            return L.lamg_setup(g.n, rp, col, w, opt, stream)
+            h = L.lamg_setup(g.n, rp, col, w, opt, stream)
+            if R > 1:
+                # column chunk of the batched engine: tuned once on the first hierarchy
+                if "cols" not in tuned:
+                    tuned["cols"], tuned["ms"] = L.lamg_autotune_batched(h, R, L.LAMG_FP32_IR, stream)
+                L.lamg_set_batch_cols(h, tuned["cols"])
+            return h
         return L.lamg_setup_graphs(gptr, rp, col, w, opt, stream)
 
     def solve(h, prec):
@@ -258,6 +266,7 @@ def run_batched(args, L, W, torch, dev, stream, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": BATCHED[args.workload], "n": g.n, "m": g.m,
                    "rhs": R, "graphs": 1 if gptr is None else len(gptr) - 1, "tol": tol,
+                   "batch_cols": tuned.get("cols"), "autotune_ms_16_32_64_128": tuned.get("ms"),
                    "levels": res[-1][2], "cycles_all_columns": cyc, "max_rel_res": res[-1][1],
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
         "fp64_vs_ir": cmp, "e2e": None, "roofline": None, "cpu_baseline": None,

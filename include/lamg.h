@@ -173,6 +173,20 @@ lamg_status lamg_solve_batched(lamg_handle h, int32_t nrhs, const double *B, dou
                                int64_t ld, double tol, lamg_precision precision,
                                lamg_stream stream, lamg_stats *st);
 
+/* lamg_autotune_batched -- picks the column chunk of lamg_solve_batched
+ * (columns per engine run: 16, 32, 64 or 128) for this handle by timing one
+ * refinement step of nrhs columns at each chunk (CUDA events on `stream`),
+ * and keeps the fastest in the handle.  chosen_cols (host, may be NULL)
+ * receives it; ms_host (host double[4], may be NULL) the four step times.
+ * Needs a single-graph handle (LAMG_ERR_ARG otherwise).  Synchronises. */
+lamg_status lamg_autotune_batched(lamg_handle h, int32_t nrhs, lamg_precision precision,
+                                  lamg_stream stream, int32_t *chosen_cols, double *ms_host);
+
+/* lamg_set_batch_cols -- sets the column chunk directly (a value cached from
+ * an earlier lamg_autotune_batched): 0 (the default, 128) or a power of two
+ * in [4, 128]; LAMG_ERR_ARG otherwise. */
+lamg_status lamg_set_batch_cols(lamg_handle h, int32_t cols);
+
 /* lamg_adjoint -- gradient of a scalar loss L(x) of the solution x = A^+ b.
  *  Given g = dL/dx (device FP64[n]) it solves A lambda = g - mean(g) with the
  *  same hierarchy (A is symmetric), so dL/db = lambda, and, for the m edges

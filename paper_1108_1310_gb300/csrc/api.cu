@@ -235,6 +235,21 @@ lamg_status lamg_solve_batched(lamg_handle h, int32_t nrhs, const double *B, dou
     });
 }
 
+lamg_status lamg_autotune_batched(lamg_handle h, int32_t nrhs, lamg_precision precision, lamg_stream stream,
+                                  int32_t *chosen_cols, double *ms_host) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && nrhs >= 1, LAMG_ERR_ARG, "bad autotune arguments");
+        autotune_batched(h, nrhs, precision, (cudaStream_t)stream, chosen_cols, ms_host);
+    });
+}
+
+lamg_status lamg_set_batch_cols(lamg_handle h, int32_t cols) {
+    return guarded([&] {
+        LAMG_REQUIRE(h, LAMG_ERR_ARG, "NULL handle");
+        set_batch_cols(h, cols);
+    });
+}
+
 lamg_status lamg_adjoint(lamg_handle h, const double *x, const double *g, double *lambda,
                          const int32_t *eu, const int32_t *ev, int64_t m, void *dw, int32_t dw_is_fp32,
                          double tol, lamg_precision p, lamg_stream stream, lamg_stats *st) {

@@ -705,6 +705,64 @@ static bool batch_read(lamg_ctx *h, std::vector<double> &out, cudaStream_t s) {
     return e != 0;
 }
 
+// columns per engine run: the tuned value, else the largest
+static int batch_chunk(const lamg_ctx *h) {
+    const int c = h->batch_cols;
+    return (c >= 4 && c <= kMaxCols) ? c : kMaxCols;
+}
+
+void set_batch_cols(lamg_ctx *h, int32_t cols) {
+    LAMG_REQUIRE(cols == 0 || (cols >= 4 && cols <= kMaxCols && (cols & (cols - 1)) == 0), LAMG_ERR_ARG,
+                 "batch columns must be 0 (default) or a power of two in [4, 128]");
+    h->batch_cols = cols;
+}
+
+// Autotuner of the column chunk (columns per engine run) of batched solves:
+// times one refinement step of `nrhs` columns for each candidate chunk of
+// 16, 32, 64 and 128 columns (right-hand side and iterate zero: a step does
+// the same work for any values), keeps the fastest in the handle.
+void autotune_batched(lamg_ctx *h, int32_t nrhs, lamg_precision p, cudaStream_t s, int32_t *chosen,
+                      double *ms_out) {
+    LAMG_REQUIRE(h->ngraphs == 1, LAMG_ERR_ARG, "lamg_autotune_batched: needs a single-graph handle");
+    prepare_solve(h);
+    const int32_t n = h->lv[0].n;
+    const int kind = p == LAMG_FP64 ? 0 : 1;
+    const int cand[4] = {16, 32, 64, 128};
+    cudaEvent_t e0, e1;
+    LAMG_CUDA(cudaEventCreate(&e0));
+    LAMG_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_c = kMaxCols;
+    std::vector<double> rn2;
+    for (int k = 0; k < 4; k++) {
+        const int cw = cand[k];
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; rep++) {   // first pass builds programs and buffers
+            LAMG_CUDA(cudaEventRecord(e0, s));
+            for (int32_t c0 = 0; c0 < nrhs; c0 += cw) {
+                const int R = std::min(cw, nrhs - c0);
+                batch_prepare(h, groups_for(R));
+                BatchState &M = *h->mr;
+                const size_t tot = (size_t)n * M.ld;
+                LAMG_CUDA(cudaMemsetAsync(M.v64[0].x.get(), 0, sizeof(double) * tot, s));
+                LAMG_CUDA(cudaMemsetAsync(M.v64[0].b.get(), 0, sizeof(double) * tot, s));
+                LAMG_CUDA(cudaMemsetAsync(M.r64.get(), 0, sizeof(double) * tot, s));
+                batch_run(h, kind, h->opt.adaptive, s);
+                if (batch_read(h, rn2, s)) throw Error{LAMG_ERR_TIMEOUT, "cycle engine: grid barrier timed out"};
+            }
+            LAMG_CUDA(cudaEventRecord(e1, s));
+            LAMG_CUDA(cudaEventSynchronize(e1));
+            LAMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms_out) ms_out[k] = ms;
+        if (ms < best) { best = ms; best_c = cw; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->batch_cols = best_c;
+    if (chosen) *chosen = best_c;
+}
+
 void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X, int64_t ld, double tol,
                           lamg_precision p, cudaStream_t s, lamg_stats *st) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -718,8 +776,9 @@ void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X,
     const int per_step = p == LAMG_FP64 ? 1 : std::max(1, h->opt.ir_inner);
     std::vector<lamg_stats> stats(nrhs);
     bool all_ok = true;
-    for (int32_t c0 = 0; c0 < nrhs; c0 += kMaxCols) {
-        const int R = std::min(kMaxCols, nrhs - c0);
+    const int chunk = batch_chunk(h);
+    for (int32_t c0 = 0; c0 < nrhs; c0 += chunk) {
+        const int R = std::min(chunk, nrhs - c0);
         batch_prepare(h, groups_for(R));
         BatchState &M = *h->mr;
         const int ldi = M.ld;

@@ -213,6 +213,7 @@ struct lamg_ctx {
     int64_t prof_bytes = 0;
     lamg_stats last{};
     std::unique_ptr<lamg::BatchState> mr;   // batched-solve workspace (lazily built)
+    int32_t batch_cols = 0;                 // columns per batched engine run (0: the largest)
     // block-diagonal union of several graphs (ngraphs == 1: one connected graph)
     int32_t ngraphs = 1;
     std::vector<int64_t> gptr;              // host: level-1 node range of each graph
@@ -256,6 +257,9 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
                   cudaStream_t s, lamg_stats *st);
 void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X, int64_t ld,
                           double tol, lamg_precision p, cudaStream_t s, lamg_stats *st);
+void set_batch_cols(lamg_ctx *h, int32_t cols);
+void autotune_batched(lamg_ctx *h, int32_t nrhs, lamg_precision p, cudaStream_t s, int32_t *chosen,
+                      double *ms_out);
 void prepare_solve(lamg_ctx *h);
 void cycle_device(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s);
 void cycle_device_noalloc(lamg_ctx *h, const double *b, double *x, int32_t adaptive, cudaStream_t s);

@@ -77,6 +77,8 @@ def _load():
         "lamg_level_copy": (I32, [P, I32, I32, P, I64]),
         "lamg_cycle": (I32, [P, P, P, I32, P]),
         "lamg_cycle_noalloc": (I32, [P, P, P, I32, P]),
+        "lamg_autotune_batched": (I32, [P, I32, I32, P, P, P]),
+        "lamg_set_batch_cols": (I32, [P, I32]),
         "lamg_profile": (I32, [P, I32, P, P, P]),
         "lamg_launch_count": (I32, [P]),
     }
@@ -206,6 +208,20 @@ def lamg_solve_batched(h, B, X, tol: float = 1e-8, precision: int = LAMG_FP64, s
     return list(stats)
 
 
+def lamg_autotune_batched(h, nrhs: int, precision: int = LAMG_FP32_IR, stream=None):
+    """Times one refinement step of nrhs columns at column chunks 16/32/64/128 and keeps
+    the fastest in the handle.  Returns (chosen chunk, [ms at 16, 32, 64, 128])."""
+    chosen = C.c_int32(0)
+    ms = (C.c_double * 4)()
+    _check(_lib.lamg_autotune_batched(h, int(nrhs), int(precision), _stream(stream), C.byref(chosen), ms),
+           "lamg_autotune_batched")
+    return chosen.value, list(ms)
+
+
+def lamg_set_batch_cols(h, cols: int):
+    _check(_lib.lamg_set_batch_cols(h, int(cols)), "lamg_set_batch_cols")
+
+
 def lamg_adjoint(h, x, g, lam, eu=None, ev=None, dw=None, tol: float = 1e-8,
                  precision: int = LAMG_FP64, stream=None) -> lamg_stats:
     _dev(x, torch.float64, "x")
@@ -311,6 +327,29 @@ class Solver:
         X = torch.zeros_like(B) if X0 is None else X0.clone()
         st = lamg_solve_batched(self.h, B, X, tol, precision, stream, allow_not_converged)
         return X, st
+
+    def autotune_batched(self, nrhs, precision=LAMG_FP32_IR, cache=None, stream=None):
+        """Column chunk for batched solves of nrhs right-hand sides: looked up in the JSON
+        file `cache` (key: n, level-1 nnz, nrhs, precision), else timed on this handle and
+        stored there.  Returns the chunk in use."""
+        import json
+        info = self.level_info(0)
+        key = f"{self.n}:{info['nnz']}:{int(nrhs)}:{'fp64' if precision == LAMG_FP64 else 'fp32ir'}"
+        table = {}
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        if key in table:
+            lamg_set_batch_cols(self.h, int(table[key]["cols"]))
+            return int(table[key]["cols"])
+        cols, ms = lamg_autotune_batched(self.h, nrhs, precision, stream)
+        if cache is not None:
+            table[key] = {"cols": cols, "ms": dict(zip(["16", "32", "64", "128"], ms))}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return cols
 
     def level_info(self, level):
         return lamg_level_info(self.h, level)

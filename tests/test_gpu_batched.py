@@ -98,3 +98,32 @@ def test_batched_rejects_non_zero_sum_column(L):
     assert e.value.status == L.LAMG_ERR_RHS_NOT_ZERO_SUM
     assert "column 2" in str(e.value)
     s.close()
+
+
+def test_autotune_batched_and_cache(L, tmp_path):
+    g = W.chung_lu(6000, seed=13)
+    s = L.Solver.from_graph(g)
+    B = _rhs(g.n, 64, 11)
+    cache = str(tmp_path / "tune.json")
+    cols = s.autotune_batched(64, precision=L.LAMG_FP32_IR, cache=cache)
+    assert cols in (16, 32, 64, 128)
+    import json
+    table = json.load(open(cache))
+    (key, entry), = table.items()
+    assert entry["cols"] == cols and all(v > 0 for v in entry["ms"].values())
+    X, stats = s.solve_batched(torch.tensor(B, device="cuda"), tol=1e-8, precision=L.LAMG_FP32_IR)
+    assert all(st.rel_res <= 1e-8 for st in stats)
+    # a second handle takes the cached value without timing
+    s2 = L.Solver.from_graph(g)
+    assert s2.autotune_batched(64, precision=L.LAMG_FP32_IR, cache=cache) == cols
+    # every chunk width gives the same solutions within the solve tolerance
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    for c in (16, 128):
+        L.lamg_set_batch_cols(s2.h, c)
+        X2, st2 = s2.solve_batched(torch.tensor(B, device="cuda"), tol=1e-10)
+        xo, _ = h.solve(B[:, 5], tol=1e-12)
+        assert np.linalg.norm(X2.cpu().numpy()[:, 5] - xo) <= 1e-6 * np.linalg.norm(xo)
+    with pytest.raises(L.LamgError):
+        L.lamg_set_batch_cols(s2.h, 12)
+    s.close()
+    s2.close()
