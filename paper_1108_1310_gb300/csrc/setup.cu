@@ -528,6 +528,40 @@ __device__ __forceinline__ int32_t jp_free_colour(int32_t u, const int32_t *__re
     }
 }
 
+// Same result for a block-tier row in one pass: the neighbours' colours below
+// kFreeBits are marked in a shared bitmap, then the first clear bit is found;
+// only when all of them are taken does the windowed search continue above.
+constexpr int kFreeBits = 8192;
+__device__ __forceinline__ int32_t jp_free_colour_blk(int32_t u, const int32_t *__restrict__ rp,
+                                                      const int32_t *__restrict__ col,
+                                                      const int32_t *__restrict__ colour) {
+    __shared__ unsigned int bits[kFreeBits / 32];
+    __shared__ int32_t first;
+    for (int k = threadIdx.x; k < kFreeBits / 32; k += blockDim.x) bits[k] = 0u;
+    if (threadIdx.x == 0) first = kFreeBits;
+    __syncthreads();
+    for (int32_t i = rp[u] + threadIdx.x; i < rp[u + 1]; i += blockDim.x) {
+        const int32_t c = colour[col[i]];
+        if (c >= 0 && c < kFreeBits) atomicOr(&bits[c >> 5], 1u << (c & 31));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kFreeBits / 32; k += blockDim.x)
+        if (bits[k] != ~0u) atomicMin(&first, k * 32 + __ffs(~bits[k]) - 1);
+    __syncthreads();
+    const int32_t f = first;
+    __syncthreads();
+    if (f < kFreeBits) return f;
+    for (int32_t base = kFreeBits;; base += 64) {
+        unsigned long long mask = 0ull;
+        for (int32_t i = rp[u] + threadIdx.x; i < rp[u + 1]; i += blockDim.x) {
+            const int32_t c = colour[col[i]];
+            if (c >= base && c < base + 64) mask |= 1ull << (c - base);
+        }
+        mask = reduce_or64<M_BLK>(mask);
+        if (mask != ~0ull) return base + __ffsll((long long)~mask) - 1;
+    }
+}
+
 
 constexpr long long kCoopMaxSpins = 1ll << 21;  // one to two seconds of polling
 
@@ -656,7 +690,7 @@ __global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp,
         }
         for (int64_t i = blockIdx.x; i < c2; i += gridDim.x) {
             const int32_t u = L2[i];
-            const int32_t c = jp_free_colour<M_BLK>(u, rp, col, colour);
+            const int32_t c = jp_free_colour_blk(u, rp, col, colour);
             if (threadIdx.x == 0) colour[u] = c;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) { nxt[0] = 0; nxt[1] = 0; nxt[2] = 0; }
