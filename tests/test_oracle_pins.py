@@ -516,3 +516,25 @@ def test_adjoint_finite_differences():
         fd = (Lp - Lm) / (2 * hstep)
         an = float(np.dot(lam, dirb))
         assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-8)
+
+
+def test_per_level_pieces_reproduce_the_hierarchy():
+    """The oracle's standalone colouring, edge scores and hub test, applied to a
+    level's own CSR and TVs, give that level's stored results: the full-size GPU
+    test relies on this to check the GPU's levels piece by piece."""
+    g = W.chung_lu(3000, seed=5)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    seed = oracle.default_opts().seed
+    for l in range(h.num_levels):
+        rp, col, w = h.csr(l)
+        n = h.info(l)["n"]
+        key = oracle.splitmix64(oracle.splitmix64(seed) ^ ((2 * l + 1) << 32))
+        assert np.array_equal(oracle.colour(n, rp, col, key)[0], h.colour(l))
+        if h.info(l)["coarsest"]:
+            continue
+        aff, q, score = oracle.edge_scores(n, rp, col, w, h.tv(l))
+        a2, q2, s2 = h.scores(l)
+        assert np.array_equal(aff.view(np.uint64), a2.view(np.uint64))
+        assert np.array_equal(q.view(np.uint64), q2.view(np.uint64))
+        assert np.array_equal(score.view(np.uint64), s2.view(np.uint64))
+        assert np.array_equal(oracle.hubs(n, rp, col, w), h.agg(l)[2])
