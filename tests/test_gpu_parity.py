@@ -36,6 +36,8 @@ def _graph(name):
         # hubs above 4096 entries: block-tier rows in setup and solve
         "hubs": lambda: W.chung_lu(30000, 2.1, 12.0, seed=7, i0=1.0),
         "star6k": lambda: W.star(6000),
+        # every node its own colour: tail-colour sweeps and long single-block runs
+        "complete": lambda: W.complete(200),
     }[name]()
 
 
@@ -49,7 +51,8 @@ def _bits(a):
     return np.ascontiguousarray(a).view(np.uint8)
 
 
-SETUP_GRAPHS = ["five", "path", "star", "grid2d", "grid3d", "chung_lu", "rgg", "er", "grid64", "hubs", "star6k"]
+SETUP_GRAPHS = ["five", "path", "star", "grid2d", "grid3d", "chung_lu", "rgg", "er", "grid64", "hubs", "star6k",
+                "complete"]
 
 
 @pytest.mark.parametrize("gname", SETUP_GRAPHS)
@@ -83,7 +86,7 @@ def test_setup_bit_exact(L, gname):
     s.close()
 
 
-@pytest.mark.parametrize("gname", ["grid2d", "chung_lu", "rgg", "grid3d", "star", "hubs"])
+@pytest.mark.parametrize("gname", ["grid2d", "chung_lu", "rgg", "grid3d", "star", "hubs", "complete"])
 @pytest.mark.parametrize("adaptive", [True, False])
 def test_one_cycle_elementwise(L, gname, adaptive):
     g = _graph(gname)
@@ -104,7 +107,7 @@ def test_one_cycle_elementwise(L, gname, adaptive):
     s.close()
 
 
-@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "five", "path", "star6k"])
+@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "five", "path", "star6k", "complete"])
 def test_solve_fp64_matches_oracle_and_dense(L, gname):
     g = _graph(gname)
     s, h = _both(L, g)
@@ -238,3 +241,19 @@ def test_host_array_solve(L):
     xd, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10)
     assert np.array_equal(x, xd.cpu().numpy())
     s.close()
+
+
+def test_size_limits_rejected_before_any_work(L):
+    # nnz must stay below 2^31 (int32 CSR indices on the device); the check reads
+    # row_ptr[0] and row_ptr[n] only, so no large arrays are needed
+    rp = torch.zeros(3, dtype=torch.int64, device="cuda")
+    rp[2] = 2 ** 31
+    col = torch.zeros(1, dtype=torch.int32, device="cuda")
+    w = torch.ones(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LamgError) as e:
+        L.Solver(2, rp, col, w)
+    assert e.value.status == L.LAMG_ERR_ARG
+    rp[2] = -1
+    with pytest.raises(L.LamgError) as e:
+        L.Solver(2, rp, col, w)
+    assert e.value.status == L.LAMG_ERR_ARG
