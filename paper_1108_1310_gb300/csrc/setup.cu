@@ -1253,6 +1253,17 @@ static void build_tiers(const int32_t *rp, int32_t n, Tiers &t, cudaStream_t s) 
     t.nb = tier_list(rp, n, 2, nullptr, t.b.get(), s);
 }
 
+// Grid of a cooperative setup kernel on the current device: one kBlk-thread
+// block per SM (the kernels' launch bounds guarantee one fits).
+static int coop_grid(const void *kernel, const char *what) {
+    int dev = 0, sms = 0, per = 0;
+    LAMG_CUDA(cudaGetDevice(&dev));
+    LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlk, 0));
+    LAMG_REQUIRE(per >= 1, LAMG_ERR_CUDA, std::string(what) + " cannot be resident");
+    return sms;
+}
+
 static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s) {
     const int32_t n = L.n;
     L.colour.alloc(n);
@@ -1286,15 +1297,7 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
     LAMG_CUDA(cudaMemcpyAsync(fcnt.get(), c6, sizeof(c6), cudaMemcpyHostToDevice, s));
     LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
     LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
-    static int grid = 0;
-    if (!grid) {
-        int dev = 0, sms = 0, per = 0;
-        LAMG_CUDA(cudaGetDevice(&dev));
-        LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jp_dag, kBlk, 0));
-        LAMG_REQUIRE(per >= 1, LAMG_ERR_CUDA, "colouring kernel cannot be resident");
-        grid = sms;
-    }
+    const int grid = coop_grid((const void *)k_jp_dag, "colouring kernel");
     {
         const int32_t *rpp = L.rp.get(), *colp = L.col.get(), *dp = deg.get();
         const uint64_t *hp = hsh.get();
@@ -1395,15 +1398,7 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, c
         LAMG_CUDA(cudaMemcpyAsync(dplan.get(), plan.data(), sizeof(int32_t) * plan.size(), cudaMemcpyHostToDevice, s));
         LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
         LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
-        static int grid = 0;
-        if (!grid) {
-            int dev = 0, sms = 0, per = 0;
-            LAMG_CUDA(cudaGetDevice(&dev));
-            LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tv_sweeps_coop, kBlk, 0));
-            LAMG_REQUIRE(per >= 1, LAMG_ERR_CUDA, "TV sweep kernel cannot be resident");
-            grid = sms;
-        }
+        const int grid = coop_grid((const void *)k_tv_sweeps_coop, "TV sweep kernel");
         int32_t nsw = o.nu_tv, npl = (int32_t)(plan.size() / 3);
         if (const char *e = std::getenv("LAMG_TIMING"); e && e[0] == '1') {
             int singles = 0, maxdeg = 0;
