@@ -252,14 +252,17 @@ lamg_status lamg_cycle(lamg_handle h, const double *b, double *x, int32_t adapti
 lamg_status lamg_cycle_noalloc(lamg_handle h, const double *b, double *x, int32_t adaptive,
                                lamg_stream stream);
 
-/* Average device time, in milliseconds, and count of the finest-level
- * relaxation sweep launches timed with CUDA events while profiling is on
- * (enable = 1 resets the counters; 0 stops recording). */
+/* Profiling of the cycle engine: average device time in milliseconds (CUDA
+ * events on the solve's stream) and count of the engine launches -- one per
+ * FP64 cycle, or per FP32-in-FP64 refinement step -- made while profiling is
+ * on, and the model bytes of one launch (the cycles it runs plus the FP64
+ * residual, update and projection).  enable = 1 resets the counters and
+ * starts recording; 0 stops. */
 lamg_status lamg_profile(lamg_handle h, int32_t enable, double *avg_ms, int64_t *count,
                          int64_t *bytes_per_launch);
 
-/* Number of this library's kernel launches since it was loaded (each kernel
- * of a launched CUDA graph counts once per graph launch). */
+/* Number of this library's kernel launches since it was loaded (a
+ * cooperative engine launch counts once). */
 lamg_status lamg_launch_count(int64_t *count_host);
 
 #ifdef __cplusplus

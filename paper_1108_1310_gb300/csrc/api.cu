@@ -13,17 +13,9 @@ namespace lamg {
 
 static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
-static thread_local int t_capturing = 0;
-static thread_local int64_t t_captured = 0;
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
-void note_launch() {
-    if (t_capturing) t_captured++;
-    else g_launches.fetch_add(1, std::memory_order_relaxed);
-}
-void note_graph_launch(int64_t kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
-void begin_capture_count() { t_capturing = 1; t_captured = 0; }
-int64_t end_capture_count() { t_capturing = 0; return t_captured; }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(); }
 
 template <class F>

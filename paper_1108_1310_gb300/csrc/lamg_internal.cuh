@@ -34,13 +34,8 @@ void set_last_error(const std::string &msg);
         }                                                                                \
     } while (0)
 
-// Every kernel launch is followed by LAMG_CHECK_LAUNCH(), which also counts
-// it (launches issued while a graph is being captured are counted per graph
-// and added each time the graph is launched).
+// Every kernel launch is followed by LAMG_CHECK_LAUNCH(), which also counts it.
 void note_launch();
-void note_graph_launch(int64_t kernels);
-void begin_capture_count();
-int64_t end_capture_count();
 int64_t launch_count();
 
 #define LAMG_CHECK_LAUNCH()                  \
