@@ -252,6 +252,15 @@ lamg_status lamg_cycle(lamg_handle h, const double *b, double *x, int32_t adapti
 lamg_status lamg_cycle_noalloc(lamg_handle h, const double *b, double *x, int32_t adaptive,
                                lamg_stream stream);
 
+/* lamg_barrier_selftest -- diagnostic of the failure path of the cycle
+ * engine's grid barrier (no paper counterpart).  Launches the barrier alone on
+ * the engine's grid.  hold_one_block = 0: every block arrives; returns
+ * LAMG_OK.  hold_one_block = 1: one block never arrives, the others give up
+ * after the bounded wait (one to two seconds), set the error word and return;
+ * the call returns LAMG_ERR_TIMEOUT and the context stays usable.  Nothing
+ * faults or hangs.  Synchronises `stream`. */
+lamg_status lamg_barrier_selftest(int32_t hold_one_block, lamg_stream stream);
+
 /* Profiling of the cycle engine: average device time in milliseconds (CUDA
  * events on the solve's stream) and count of the engine launches -- one per
  * FP64 cycle, or per FP32-in-FP64 refinement step -- made while profiling is

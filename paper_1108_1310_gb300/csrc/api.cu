@@ -324,6 +324,13 @@ lamg_status lamg_cycle_noalloc(lamg_handle h, const double *b, double *x, int32_
     });
 }
 
+lamg_status lamg_barrier_selftest(int32_t hold_one_block, lamg_stream stream) {
+    return guarded([&] {
+        const int32_t e = barrier_selftest(hold_one_block, (cudaStream_t)stream);
+        LAMG_REQUIRE(e == 0, LAMG_ERR_TIMEOUT, "grid barrier: wait ran out (a block never arrived)");
+    });
+}
+
 lamg_status lamg_profile(lamg_handle h, int32_t enable, double *avg_ms, int64_t *count, int64_t *bytes) {
     return guarded([&] {
         LAMG_REQUIRE(h, LAMG_ERR_ARG, "NULL handle");

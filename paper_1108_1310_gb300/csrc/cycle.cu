@@ -443,6 +443,15 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
     }
 }
 
+// Self-test of the grid barrier's bounded wait: every block except `held`
+// (-1: none) enters one barrier.  With a block held back the others give up
+// after kMaxSpins polls, set the error word and return; nothing faults.
+__global__ void __launch_bounds__(kEngThreads) k_barrier_probe(unsigned int *bar, int32_t *err, int32_t held) {
+    unsigned int epoch = 0;
+    if ((int32_t)blockIdx.x == held) return;
+    grid_sync(bar, err, epoch);
+}
+
 // ||r64||^2 from the per-block partials written by OP_NORM64_FIN
 __global__ void k_engine_norm(const double *part, int nb, double *out) {
     double v = 0.0;
@@ -796,6 +805,26 @@ int32_t *engine_run_noalloc(lamg_ctx *h, int adaptive, double mu, cudaStream_t s
                                           kEngSmem, s));
     note_launch();
     return err;
+}
+
+// Runs k_barrier_probe on the engine's grid; returns the error word.
+int32_t barrier_selftest(int32_t hold_one, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    LAMG_CUDA(cudaGetDevice(&dev));
+    LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_barrier_probe, kEngThreads, 0));
+    LAMG_REQUIRE(per >= 1, LAMG_ERR_CUDA, "barrier probe cannot be resident");
+    Tmp<unsigned int> bar(2, s);
+    Tmp<int32_t> err(1, s);
+    LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
+    LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
+    unsigned int *bp = bar.get();
+    int32_t *ep = err.get();
+    int32_t held = hold_one ? 0 : -1;
+    void *args[] = {&bp, &ep, &held};
+    LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_barrier_probe, dim3(sms), dim3(kEngThreads), args, 0, s));
+    note_launch();
+    return read_scalar(err.get(), s);
 }
 
 int64_t engine_program_ops(lamg_ctx *h, int kind, int adaptive) {

@@ -243,6 +243,7 @@ bool engine_failed(lamg_ctx *h, cudaStream_t s);
 void engine_report(lamg_ctx *h);
 void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out, int groups = 0);
 bool engine_noalloc_ready(lamg_ctx *h, int adaptive);
+int32_t barrier_selftest(int32_t hold_one, cudaStream_t s);
 int32_t *engine_run_noalloc(lamg_ctx *h, int adaptive, double mu, cudaStream_t s);
 
 // solve.cu

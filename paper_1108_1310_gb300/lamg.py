@@ -79,6 +79,7 @@ def _load():
         "lamg_cycle_noalloc": (I32, [P, P, P, I32, P]),
         "lamg_autotune_batched": (I32, [P, I32, I32, P, P, P]),
         "lamg_set_batch_cols": (I32, [P, I32]),
+        "lamg_barrier_selftest": (I32, [I32, P]),
         "lamg_profile": (I32, [P, I32, P, P, P]),
         "lamg_launch_count": (I32, [P]),
     }
@@ -279,6 +280,11 @@ def lamg_cycle_noalloc(h, b, x, adaptive: bool = True, stream=None):
     _dev(b, torch.float64, "b")
     _dev(x, torch.float64, "x")
     _check(_lib.lamg_cycle_noalloc(h, _ptr(b), _ptr(x), int(adaptive), _stream(stream)), "lamg_cycle_noalloc")
+
+
+def lamg_barrier_selftest(hold_one_block: bool, stream=None) -> int:
+    """Status of the grid barrier's bounded wait (LAMG_ERR_TIMEOUT when a block is held back)."""
+    return int(_lib.lamg_barrier_selftest(int(bool(hold_one_block)), _stream(stream)))
 
 
 def lamg_profile(h, enable: bool):
