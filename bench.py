@@ -40,6 +40,11 @@ TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10}
 # whenever the engine kernel changes.
 NCU_TRAFFIC = {("chung_lu1m", "fp32ir"): 1.452e9}
 # batched forms (many right-hand sides on one hierarchy; many graphs as one union)
+ADJOINT = {
+    "knn500k_adjoint": "kNN graph n=500k, k=10, 16-D Gaussian-mixture points, Gaussian weights FP32, all components "
+                       "as one union; semi-supervised solve (1% labelled sources, zero-sum per component) to 1e-8 "
+                       "plus the adjoint: lambda and dL/dw for every edge",
+}
 BATCHED = {
     "rgg2m_b64": "64 zero-sum Gaussian RHS on a 2M-node 2-D RGG (mean degree 12, w = exp(-d^2/r^2), FP32); "
                  "FP32 cycles in FP64 IR to 1e-8, lamg_solve_batched",
@@ -172,6 +177,104 @@ def job_value(world, units_per_rank_step, ms):
     return world * units_per_rank_step / (ms / 1e3)
 
 
+def run_adjoint(args, L, W, torch, dev, stream, rank, world):
+    """One step = setup + forward solve + adjoint (lambda and the gradient for every edge), FP32 in FP64 IR."""
+    tol = 1e-8
+    # all 500k points: the kNN graph of a 10-cluster mixture falls into components,
+    # solved together as one block-diagonal union (lamg_setup_graphs)
+    g, gptr, _, _ = W.knn_gmm(500_000, dim=16, k=10, seed=6, device=str(dev), components=True)
+    rng = np.random.default_rng(6)
+    perm = rng.permutation(g.n)
+    lab, held = perm[: g.n // 100], perm[g.n // 100: g.n // 100 + g.n // 20]
+    y = rng.integers(0, 2, g.n).astype(np.float64)
+    b_host = np.zeros(g.n)
+    labelled = np.zeros(g.n, dtype=bool)
+    labelled[lab] = True
+    for c in range(len(gptr) - 1):   # zero-sum sources on every component
+        idx = np.arange(gptr[c], gptr[c + 1])[labelled[gptr[c]:gptr[c + 1]]]
+        if idx.size >= 2:
+            b_host[idx] = y[idx] - y[idx].mean()
+    gx_host = np.zeros(g.n)
+    gx_host[held] = 1.0
+    eu, ev, _ = g.edges()
+    rp = torch.tensor(g.rp, device=dev)
+    col = torch.tensor(g.col, device=dev)
+    w = torch.tensor(g.w, device=dev).to(torch.float32)
+    b = torch.tensor(b_host, device=dev)
+    gx = torch.tensor(gx_host, device=dev)
+    eut = torch.tensor(eu, device=dev)
+    evt = torch.tensor(ev, device=dev)
+    x = torch.zeros_like(b)
+    lam = torch.zeros_like(b)
+    dw = torch.zeros(eu.size, dtype=torch.float64, device=dev)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(prec=L.LAMG_FP32_IR):
+        h = L.lamg_setup_graphs(gptr, rp, col, w, opt, stream)
+        x.zero_()
+        st = L.lamg_solve(h, b, x, tol, prec, stream)
+        sa = L.lamg_adjoint(h, x, gx, lam, eut, evt, dw, tol=tol, precision=prec, stream=stream)
+        L.lamg_free(h)
+        return st, sa
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    times, res = [], []
+    launches0 = L.lamg_launch_count()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res.append(step())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            flush.fill_(1.0)
+    launches = L.lamg_launch_count() - launches0
+    ms = slowest_rank_ms(sum(times) / len(times), None, dev)
+    cyc = sum(r[0].cycles + r[1].cycles for r in res) / len(res)
+    # forward and adjoint solves timed alone on one hierarchy, FP32 IR and plain FP64
+    h = L.lamg_setup_graphs(gptr, rp, col, w, opt, stream)
+    cmp = {}
+    for name, prec in (("fp32ir", L.LAMG_FP32_IR), ("fp64", L.LAMG_FP64)):
+        for what in ("forward", "adjoint"):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            if what == "adjoint":
+                L.lamg_solve(h, b, x, tol, prec, stream)
+            e0.record(stream)
+            if what == "forward":
+                st = L.lamg_solve(h, b, x, tol, prec, stream)
+            else:
+                st = L.lamg_adjoint(h, x, gx, lam, eut, evt, dw, tol=tol, precision=prec, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cmp[f"{what}_ms_{name}"] = e0.elapsed_time(e1)
+            cmp[f"{what}_cycles_{name}"] = st.cycles
+            cmp[f"{what}_rel_res_{name}"] = st.rel_res
+    L.lamg_free(h)
+    line = {
+        "metric": "edges*cycles/s (LAMG setup + solve to tol)",
+        "value": job_value(world, g.m * cyc, ms), "unit": "edges*cycles/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": ADJOINT[args.workload], "n": g.n, "m": g.m, "tol": tol,
+                   "graphs": len(gptr) - 1,
+                   "levels": res[-1][0].levels, "cycles_forward_plus_adjoint": cyc,
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
+        "fp64_vs_ir": cmp, "e2e": None, "roofline": None, "cpu_baseline": None,
+        "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_batched(args, L, W, torch, dev, stream, rank, world):
     """One step = setup + solve of every right-hand side / every graph to 1e-8."""
     tol = 1e-8
@@ -282,7 +385,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu")
-    ap.add_argument("--workload", default="chung_lu1m", choices=list(WORKLOADS) + list(BATCHED))
+    ap.add_argument("--workload", default="chung_lu1m", choices=list(WORKLOADS) + list(BATCHED) + list(ADJOINT))
     ap.add_argument("--precision", default=None, choices=["fp32ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -309,6 +412,8 @@ def main():
 
     if args.workload in BATCHED:
         return run_batched(args, L, W, torch, dev, stream, rank, world)
+    if args.workload in ADJOINT:
+        return run_adjoint(args, L, W, torch, dev, stream, rank, world)
     gname, pdef, desc = WORKLOADS[args.workload]
     prec_name = args.precision or pdef
     prec = L.LAMG_FP32_IR if prec_name == "fp32ir" else L.LAMG_FP64

@@ -205,7 +205,7 @@ def erdos_renyi(n: int, mean_deg: float = 8.0, seed: int = 5) -> Graph:
 
 
 def knn_gmm(n: int = 500_000, dim: int = 16, k: int = 10, ncomp: int = 10, seed: int = 6,
-            device: str = "cpu", block: int = 4096):
+            device: str = "cpu", block: int = 4096, components: bool = False):
     """k-nearest-neighbour graph (union-symmetrised) on points from a Gaussian
     mixture (means ~ N(0, 3^2 I), unit covariance, equal weights); Gaussian edge
     weights exp(-d^2/sigma^2), sigma = mean k-th neighbour distance, rounded to
@@ -235,6 +235,20 @@ def knn_gmm(n: int = 500_000, dim: int = 16, k: int = 10, ncomp: int = 10, seed:
     w = np.exp(-d2 / (sigma * sigma)).astype(np.float32).astype(np.float64)
     w = np.maximum(w, np.float64(np.finfo(np.float32).tiny))
     g = from_edges(n, lo, hi, w, f"knn{n}")
+    if components:
+        # every connected component, renumbered so that each is a contiguous
+        # node range: (union graph, gptr, labels, points) for lamg_setup_graphs
+        import scipy.sparse as sp
+        import scipy.sparse.csgraph as cg
+        A = sp.csr_matrix((g.w, g.col, g.rp), shape=(n, n))
+        nc, comp = cg.connected_components(A, directed=False)
+        order = np.argsort(comp, kind="stable")
+        inv = np.empty(n, dtype=np.int64)
+        inv[order] = np.arange(n)
+        gu = from_edges(n, inv[lo], inv[hi], w, f"knn{n}_components")
+        gptr = np.zeros(nc + 1, dtype=np.int64)
+        gptr[1:] = np.cumsum(np.bincount(comp, minlength=nc))
+        return gu, gptr, lab[order], pts[order]
     g2 = largest_component(g)
     return g2, lab, pts
 
