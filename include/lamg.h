@@ -141,6 +141,12 @@ lamg_status lamg_setup_graphs(int32_t num_graphs, const int64_t *graph_ptr, int6
                               int32_t w_is_fp32, const lamg_options *opt, lamg_stream stream,
                               lamg_handle *out);
 
+/* lamg_graph_residuals -- per-graph ||b_g - A x_g|| / ||b_g|| of the last
+ * lamg_solve (or lamg_solve_host / lamg_adjoint) on a handle from
+ * lamg_setup_graphs.  rel_res_host: host double[num_graphs].  LAMG_ERR_ARG for
+ * a single-graph handle or before any solve. */
+lamg_status lamg_graph_residuals(lamg_handle h, double *rel_res_host);
+
 /* lamg_solve -- cycles of Sec. 4.2 until ||b - A x||_2 <= tol ||b||_2.
  *  b  device FP64[n], zero-sum (LAMG_ERR_RHS_NOT_ZERO_SUM otherwise)
  *  x  device FP64[n]; in: initial guess, out: the zero-mean iterate

@@ -324,6 +324,15 @@ lamg_status lamg_cycle_noalloc(lamg_handle h, const double *b, double *x, int32_
     });
 }
 
+lamg_status lamg_graph_residuals(lamg_handle h, double *rel_res_host) {
+    return guarded([&] {
+        LAMG_REQUIRE(h && rel_res_host, LAMG_ERR_ARG, "NULL argument");
+        LAMG_REQUIRE(h->ngraphs > 1, LAMG_ERR_ARG, "the handle holds one graph (use lamg_stats.rel_res)");
+        LAMG_REQUIRE((int32_t)h->grel.size() == h->ngraphs, LAMG_ERR_ARG, "no solve has run on this handle");
+        std::memcpy(rel_res_host, h->grel.data(), sizeof(double) * h->ngraphs);
+    });
+}
+
 lamg_status lamg_barrier_selftest(int32_t hold_one_block, lamg_stream stream) {
     return guarded([&] {
         const int32_t e = barrier_selftest(hold_one_block, (cudaStream_t)stream);

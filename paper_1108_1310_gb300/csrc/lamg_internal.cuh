@@ -216,6 +216,7 @@ struct lamg_ctx {
     lamg::DBuf<int32_t> iperm0;             // natural level-1 id -> permuted row
     lamg::DBuf<int32_t> gid0, gidnat;       // graph of each permuted / natural level-1 row
     lamg::DBuf<double> gsum, gnorm, gstat;  // per-graph means, ||r||^2, and b statistics (3 per graph)
+    std::vector<double> grel;               // per-graph ||r_g|| / ||b_g|| of the last solve
 };
 
 namespace lamg {

@@ -738,7 +738,11 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
     L.rel_res = bn > 0 ? rn / bn : 0.0;
     if (G > 1) {
         L.rel_res = 0.0;
-        for (int32_t g = 0; g < G; g++) L.rel_res = std::max(L.rel_res, gbn[g] > 0 ? grn[g] / gbn[g] : 0.0);
+        h->grel.assign(G, 0.0);
+        for (int32_t g = 0; g < G; g++) {
+            h->grel[g] = gbn[g] > 0 ? grn[g] / gbn[g] : 0.0;
+            L.rel_res = std::max(L.rel_res, h->grel[g]);
+        }
     }
     L.acf = (cycles > 0 && r0 > 0 && rn > 0) ? std::pow(rn / r0, 1.0 / cycles) : 0.0;
     L.t_setup_s = h->t_setup_s;

@@ -80,6 +80,7 @@ def _load():
         "lamg_autotune_batched": (I32, [P, I32, I32, P, P, P]),
         "lamg_set_batch_cols": (I32, [P, I32]),
         "lamg_barrier_selftest": (I32, [I32, P]),
+        "lamg_graph_residuals": (I32, [P, P]),
         "lamg_profile": (I32, [P, I32, P, P, P]),
         "lamg_launch_count": (I32, [P]),
     }
@@ -280,6 +281,13 @@ def lamg_cycle_noalloc(h, b, x, adaptive: bool = True, stream=None):
     _dev(b, torch.float64, "b")
     _dev(x, torch.float64, "x")
     _check(_lib.lamg_cycle_noalloc(h, _ptr(b), _ptr(x), int(adaptive), _stream(stream)), "lamg_cycle_noalloc")
+
+
+def lamg_graph_residuals(h, ngraphs: int) -> np.ndarray:
+    """Per-graph relative residuals of the last solve on a many-graphs handle."""
+    out = np.zeros(int(ngraphs))
+    _check(_lib.lamg_graph_residuals(h, _ptr(out)), "lamg_graph_residuals")
+    return out
 
 
 def lamg_barrier_selftest(hold_one_block: bool, stream=None) -> int:

@@ -82,6 +82,8 @@ def test_union_solve_every_graph(L, precision):
     x, st = s.solve(torch.tensor(b, device="cuda"), tol=tol, precision=p)
     xg = x.cpu().numpy()
     assert st.rel_res <= tol
+    rel = L.lamg_graph_residuals(s.h, len(gptr) - 1)
+    assert rel.max() == st.rel_res and (rel <= tol).all()
     xo, _ = h.solve(b, tol=1e-12)
     for g in range(len(gptr) - 1):
         a, e = gptr[g], gptr[g + 1]
