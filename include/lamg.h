@@ -86,6 +86,11 @@ typedef struct {
     int32_t  ir_inner;         /* FP32 cycles per FP64 refinement step: 2               */
     int32_t  validate;         /* 1: check the input graph (symmetry, weights, connectivity) */
     int32_t  keep_setup_data;  /* 1: keep TVs, affinities, energy ratios for inspection */
+    int32_t  project_rhs;      /* 0: a b that is not zero-sum (per graph, per column) is
+                                  rejected with LAMG_ERR_RHS_NOT_ZERO_SUM; 1: the solve
+                                  uses b minus its mean instead (per graph, per column),
+                                  the compatible part of b (Sec. 1), and leaves the
+                                  caller's b unchanged                                    */
 } lamg_options;
 
 typedef struct {
@@ -148,7 +153,9 @@ lamg_status lamg_setup_graphs(int32_t num_graphs, const int64_t *graph_ptr, int6
 lamg_status lamg_graph_residuals(lamg_handle h, double *rel_res_host);
 
 /* lamg_solve -- cycles of Sec. 4.2 until ||b - A x||_2 <= tol ||b||_2.
- *  b  device FP64[n], zero-sum (LAMG_ERR_RHS_NOT_ZERO_SUM otherwise)
+ *  b  device FP64[n], zero-sum (LAMG_ERR_RHS_NOT_ZERO_SUM otherwise, unless
+ *     the options set project_rhs: then b minus its mean is solved for, and
+ *     ||b - mean|| is the norm of the stopping test)
  *  x  device FP64[n]; in: initial guess, out: the zero-mean iterate
  *  precision  LAMG_FP64: FP64 cycles.  LAMG_FP32_IR: FP32 cycles inside FP64
  *             iterative refinement (outer residual, mean projection and the
@@ -170,7 +177,8 @@ lamg_status lamg_solve_host(lamg_handle h, const double *b_host, double *x_host,
  *  B, X  device FP64, row-interleaved: entry (u, j) at [u * ld + j], ld >= nrhs.
  *        X in: initial guesses, out: zero-mean iterates.
  *  Every column of B must be zero-sum (LAMG_ERR_RHS_NOT_ZERO_SUM names the
- *  first one that is not).  Each column has its own recombination
+ *  first one that is not), unless the options set project_rhs: then each
+ *  column's mean is subtracted on the device copy.  Each column has its own recombination
  *  coefficients, mean projection and stopping test; the call returns when all
  *  columns have reached tol (LAMG_ERR_NOT_CONVERGED, X valid, otherwise).
  *  st: host array of nrhs stats (cycles/outer_steps: when that column

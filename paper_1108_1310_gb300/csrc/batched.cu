@@ -560,6 +560,13 @@ __global__ void k_gather4(int32_t n, int32_t ld, int32_t R, const int32_t *__res
     dst[q] = c < R ? src[(int64_t)perm[i] * lds + c] : 0.0;
 }
 
+// b[i * ld + c] -= mean[c] (columns past the batch have mean 0)
+__global__ void k_sub_colmean(int32_t n, int32_t ld, const double *__restrict__ mean, double *__restrict__ b) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * ld) return;
+    b[q] -= mean[q % ld];
+}
+
 __global__ void k_scatter4(int32_t n, int32_t ld, int32_t R, const int32_t *__restrict__ perm,
                            const double *__restrict__ src, int64_t lds, double *__restrict__ dst) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -789,13 +796,24 @@ void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X,
         k_gather4<<<ceil_div(tot, 256), 256, 0, s>>>(n, ldi, R, perm, X + c0, ld, xb);
         LAMG_CHECK_LAUNCH();
         // zero-sum check and ||b|| per column (Sec. 1: b must be compatible)
-        k_colstats<<<M.grid, 1024, 0, s>>>(n, M.groups, bb, M.part.get());
-        LAMG_CHECK_LAUNCH();
-        k_colstats_fin<<<1, 1024, 0, s>>>(M.part.get(), M.grid, ldi, M.out.get());
-        LAMG_CHECK_LAUNCH();
         std::vector<double> cs(3 * (size_t)ldi);
-        LAMG_CUDA(cudaMemcpyAsync(cs.data(), M.out.get(), sizeof(double) * 3 * ldi, cudaMemcpyDeviceToHost, s));
-        LAMG_CUDA(cudaStreamSynchronize(s));
+        auto colstats = [&]() {
+            k_colstats<<<M.grid, 1024, 0, s>>>(n, M.groups, bb, M.part.get());
+            LAMG_CHECK_LAUNCH();
+            k_colstats_fin<<<1, 1024, 0, s>>>(M.part.get(), M.grid, ldi, M.out.get());
+            LAMG_CHECK_LAUNCH();
+            LAMG_CUDA(cudaMemcpyAsync(cs.data(), M.out.get(), sizeof(double) * 3 * ldi, cudaMemcpyDeviceToHost, s));
+            LAMG_CUDA(cudaStreamSynchronize(s));
+        };
+        colstats();
+        if (h->opt.project_rhs) {  // solve for each column minus its mean
+            std::vector<double> mean(ldi, 0.0);
+            for (int c = 0; c < R; c++) mean[c] = cs[c] / (double)n;
+            LAMG_CUDA(cudaMemcpyAsync(M.out.get(), mean.data(), sizeof(double) * ldi, cudaMemcpyHostToDevice, s));
+            k_sub_colmean<<<ceil_div(tot, 256), 256, 0, s>>>(n, ldi, M.out.get(), bb);
+            LAMG_CHECK_LAUNCH();
+            colstats();
+        }
         std::vector<double> bn(R);
         for (int c = 0; c < R; c++) {
             const double sum = cs[c], asum = cs[ldi + c];

@@ -655,7 +655,8 @@ static void graph_stats(lamg_ctx *h, const double *v, const int32_t *map, cudaSt
     LAMG_CUDA(cudaStreamSynchronize(s));
 }
 
-__global__ void k_center_graphs(int32_t n, const double *__restrict__ g, double *__restrict__ out,
+// out may be g (in place): each element is read and written by one thread
+__global__ void k_center_graphs(int32_t n, const double *g, double *out,
                                 const int32_t *__restrict__ gid, const int64_t *__restrict__ gptr,
                                 const double *__restrict__ sums) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -663,6 +664,11 @@ __global__ void k_center_graphs(int32_t n, const double *__restrict__ g, double 
         const int32_t k = gid[i];
         out[i] = g[i] - sums[k] / (double)(gptr[k + 1] - gptr[k]);
     }
+}
+
+__global__ void k_add_const(int32_t n, double *__restrict__ v, double c) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] += c;
 }
 
 void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_precision p, cudaStream_t s,
@@ -682,6 +688,11 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
     if (G > 1) {
         // a union of graphs: b must be zero-sum on every graph; each graph has its own ||b_g||
         graph_stats(h, bb, h->iperm0.get(), s, gst);
+        if (h->opt.project_rhs) {  // solve for b minus its mean on every graph (the device stats start with the sums)
+            k_center_graphs<<<ceil_div(n, 256), 256, 0, s>>>(n, bb, bb, h->gid0.get(), h->gptr_d.get(), h->gstat.get());
+            LAMG_CHECK_LAUNCH();
+            graph_stats(h, bb, h->iperm0.get(), s, gst);
+        }
         bn = 0.0;
         for (int32_t g = 0; g < G; g++) {
             LAMG_REQUIRE(std::fabs(gst[g]) <= 1e-10 * (gst[G + g] > 0 ? gst[G + g] : 1.0),
@@ -692,6 +703,11 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
         bn = std::sqrt(bn);
     } else {
         rhs_norms(h, bb, s, sb, ab, bn);
+        if (h->opt.project_rhs && sb != 0.0) {  // solve for b minus its mean
+            k_add_const<<<ceil_div(n, 256), 256, 0, s>>>(n, bb, -sb / (double)n);
+            LAMG_CHECK_LAUNCH();
+            rhs_norms(h, bb, s, sb, ab, bn);
+        }
         LAMG_REQUIRE(std::fabs(sb) <= 1e-10 * (ab > 0 ? ab : 1.0), LAMG_ERR_RHS_NOT_ZERO_SUM,
                      "right-hand side is not zero-sum");
     }

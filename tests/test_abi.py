@@ -61,6 +61,8 @@ def test_default_options_are_the_papers(lib):
     assert (o.gamma, o.k_finest, o.k_max, o.nu_tv, o.nu1, o.nu2, o.n_coarsest) == (1.5, 4, 10, 3, 1, 2, 150)
     assert (o.q_max, o.hub_factor, o.mu_flat) == (2.5, 8.0, 4.0 / 3.0)
     assert o.adaptive == 1
+    # input checks on, and a b that is not zero-sum rejected rather than projected
+    assert (o.validate, o.project_rhs) == (1, 0)
 
 
 def test_default_options_match_the_oracle(lib):
