@@ -433,6 +433,28 @@ def test_solution_matches_dense_pseudoinverse(gname):
         assert abs(x.sum()) <= 1e-12 * np.abs(x).sum()             # u^T x = 0 (Eq. (1.3b))
 
 
+@pytest.mark.parametrize("gname", ["chung_lu", "grid"])
+def test_solution_matches_cg_at_scale(gname):
+    # Beyond dense sizes the solution is pinned by an independent method: plain
+    # FP64 conjugate gradients on A + 11^T/n, which is SPD for a connected graph
+    # and maps the zero-mean x = A^+ b to b (Eqs. (1.3a)-(1.3b)).  The two share
+    # nothing but the CSR arrays.
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    sp = pytest.importorskip("scipy.sparse")
+    g = {"chung_lu": W.chung_lu(30000, seed=24), "grid": W.grid2d(150, 150)}[gname]
+    n = g.n
+    W_ = sp.csr_matrix((g.w, g.col, g.rp), shape=(n, n))
+    d = np.asarray(W_.sum(axis=1)).ravel()
+    op = sla.LinearOperator((n, n), matvec=lambda v: d * v - W_ @ v + v.sum() / n, dtype=np.float64)
+    b = W.zero_sum_rhs(n, 25)
+    xc, info = sla.cg(op, b, rtol=1e-13, atol=0.0, maxiter=20 * n)
+    assert info == 0
+    h = oracle.Hierarchy(n, g.rp, g.col, g.w)
+    x, hist = h.solve(b, tol=1e-12, max_cycles=400)
+    assert hist[-1] <= 1e-12 * np.linalg.norm(b)
+    assert np.linalg.norm(x - xc) <= 1e-7 * np.linalg.norm(xc)
+
+
 def test_rejects_non_zero_sum_rhs():
     g = W.grid2d(20, 20)
     h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
