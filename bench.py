@@ -6,9 +6,12 @@ refinement), timed with CUDA events.  Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload chung_lu1m|grid256|grid64] [--precision fp32ir|fp64]
 
-Multi-GPU: the solve does not shard (each relaxation sweep would need a halo
-exchange); N GPUs run N independent replicas of the step, no collective on
-the data path; value = all ranks' units / the slowest rank's time.
+Multi-GPU: the solve of one graph does not shard (each relaxation sweep would
+need a halo exchange); N GPUs run N independent replicas of the step.  The
+batched workloads are many independent problems and shard: the right-hand
+sides (rgg2m_b64) or the graphs (er500, balanced by size) are split over the
+ranks.  Either way there is no collective on the data path, and value = all
+ranks' units / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -177,7 +180,40 @@ def job_value(world, units_per_rank_step, ms):
     return world * units_per_rank_step / (ms / 1e3)
 
 
-def run_adjoint(args, L, W, torch, dev, stream, rank, world):
+def total_units(units, dist, device):
+    """Sum over ranks of the units each rank processed (a sharded job: one host-side
+    reduction of the counts after the timed region, nothing on the data path)."""
+    if not dist:
+        return units
+    import torch
+    t = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_block(count, world, rank):
+    """Contiguous share [c0, c1) of `count` independent items (right-hand sides) for
+    one rank; the shares differ in size by at most one."""
+    base, extra = divmod(count, world)
+    c0 = rank * base + min(rank, extra)
+    return c0, c0 + base + (1 if rank < extra else 0)
+
+
+def shard_lpt(loads, world):
+    """Independent problems of the given loads (graph sizes) dealt to `world` ranks,
+    largest first, each to the least-loaded rank so far (ties: lower rank; equal
+    loads: lower index).  Returns each rank's problem indices in increasing order."""
+    order = sorted(range(len(loads)), key=lambda k: (-loads[k], k))
+    total = [0] * world
+    share = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda q: (total[q], q))
+        share[r].append(k)
+        total[r] += loads[k]
+    return [sorted(s) for s in share]
+
+
+def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
     """One step = setup + forward solve + adjoint (lambda and the gradient for every edge), FP32 in FP64 IR."""
     tol = 1e-8
     # all 500k points: the kNN graph of a 10-cluster mixture falls into components,
@@ -223,6 +259,9 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world):
         flush.fill_(1.0)
     torch.cuda.synchronize()
     times, res = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     launches0 = L.lamg_launch_count()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         for _ in range(args.steps):
@@ -235,7 +274,9 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world):
             times.append(e0.elapsed_time(e1))
             flush.fill_(1.0)
     launches = L.lamg_launch_count() - launches0
-    ms = slowest_rank_ms(sum(times) / len(times), None, dev)
+    if dist:
+        dist.barrier()
+    ms = slowest_rank_ms(sum(times) / len(times), dist, dev)
     cyc = sum(r[0].cycles + r[1].cycles for r in res) / len(res)
     # forward and adjoint solves timed alone on one hierarchy, FP32 IR and plain FP64
     h = L.lamg_setup_graphs(gptr, rp, col, w, opt, stream)
@@ -275,14 +316,23 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world):
         print(json.dumps(line))
 
 
-def run_batched(args, L, W, torch, dev, stream, rank, world):
-    """One step = setup + solve of every right-hand side / every graph to 1e-8."""
+def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
+    """One step = setup + solve of every right-hand side / every graph to 1e-8.
+    The job is fixed (64 right-hand sides, 500 graphs) and shards over the ranks
+    with no collective on the data path: rank r takes a contiguous block of the
+    columns (each rank builds the hierarchy of the one matrix), or its share of
+    the graphs balanced by size; value = all ranks' units / the slowest rank."""
     tol = 1e-8
     if args.workload == "rgg2m_b64":
-        g, gptr, R = W.config_graph("rgg2m"), None, 64
-        B = torch.tensor(W.zero_sum_rhs(g.n, 3, count=R), device=dev)
+        g, gptr, R_all = W.config_graph("rgg2m"), None, 64
+        c0, c1 = shard_block(R_all, world, rank)
+        R, G_all, G = c1 - c0, 1, 1
+        Bh = np.ascontiguousarray(W.zero_sum_rhs(g.n, 3, count=R_all)[:, c0:c1])
+        B = torch.tensor(Bh[:, 0].copy() if R == 1 else Bh, device=dev)
     else:
-        (g, gptr), R = W.er_batch(500, 1000, 200_000, seed=7), 1
+        G_all = 500
+        mine = shard_lpt(W.er_batch_sizes(G_all, 1000, 200_000, seed=7).tolist(), world)[rank]
+        (g, gptr), R, R_all, G = W.er_batch(G_all, 1000, 200_000, seed=7, only=mine), 1, 1, len(mine)
         B = torch.tensor(W.zero_sum_rhs_graphs(gptr, 3), device=dev)
     rp = torch.tensor(g.rp, device=dev)
     col = torch.tensor(g.col, device=dev)
@@ -323,6 +373,9 @@ def run_batched(args, L, W, torch, dev, stream, rank, world):
         flush.fill_(1.0)
     torch.cuda.synchronize()
     times, res = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     launches0 = L.lamg_launch_count()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         for _ in range(args.steps):
@@ -335,8 +388,11 @@ def run_batched(args, L, W, torch, dev, stream, rank, world):
             times.append(e0.elapsed_time(e1))
             flush.fill_(1.0)
     launches = L.lamg_launch_count() - launches0
-    ms = sum(times) / len(times)
+    if dist:
+        dist.barrier()
+    ms = slowest_rank_ms(sum(times) / len(times), dist, dev)
     cyc = sum(r[0] for r in res) / len(res)
+    units = total_units(g.m * cyc, dist, dev)     # edges*cycles of all ranks' shares per step
 
     def timed(fn):
         flush.fill_(1.0)
@@ -364,14 +420,14 @@ def run_batched(args, L, W, torch, dev, stream, rank, world):
     L.lamg_free(h)
     line = {
         "metric": "edges*cycles/s (LAMG setup + solve to tol)",
-        "value": world * g.m * cyc / (ms / 1e3), "unit": "edges*cycles/s", "n_gpus": world,
+        "value": units / (ms / 1e3), "unit": "edges*cycles/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": BATCHED[args.workload], "n": g.n, "m": g.m,
-                   "rhs": R, "graphs": 1 if gptr is None else len(gptr) - 1, "tol": tol,
+                   "rhs": R_all, "rhs_rank0": R, "graphs": G_all, "graphs_rank0": G, "tol": tol,
                    "batch_cols": tuned.get("cols"), "autotune_ms_16_32_64_128": tuned.get("ms"),
                    "levels": res[-1][2], "cycles_all_columns": cyc, "max_rel_res": res[-1][1],
-                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"shard{world}"},
         "fp64_vs_ir": cmp, "e2e": None, "roofline": None, "cpu_baseline": None,
         "clocks": clk.summary(), "gpu_launches": launches,
     }
@@ -411,9 +467,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     if args.workload in BATCHED:
-        return run_batched(args, L, W, torch, dev, stream, rank, world)
+        return run_batched(args, L, W, torch, dev, stream, rank, world, dist)
     if args.workload in ADJOINT:
-        return run_adjoint(args, L, W, torch, dev, stream, rank, world)
+        return run_adjoint(args, L, W, torch, dev, stream, rank, world, dist)
     gname, pdef, desc = WORKLOADS[args.workload]
     prec_name = args.precision or pdef
     prec = L.LAMG_FP32_IR if prec_name == "fp32ir" else L.LAMG_FP64

@@ -269,12 +269,18 @@ def block_union(graphs) -> tuple[Graph, np.ndarray]:
     return Graph(int(gptr[-1]), np.concatenate(rp), col, w, f"union{len(graphs)}"), gptr
 
 
-def er_batch(count: int, n_lo: int, n_hi: int, mean_deg: float = 8.0, seed: int = 7):
+def er_batch_sizes(count: int, n_lo: int, n_hi: int, seed: int = 7) -> np.ndarray:
+    """Node counts (before taking the largest component) of the graphs of er_batch."""
+    return np.random.default_rng(seed).integers(n_lo, n_hi + 1, count)
+
+
+def er_batch(count: int, n_lo: int, n_hi: int, mean_deg: float = 8.0, seed: int = 7, only=None):
     """`count` Erdos-Renyi graphs (largest components) with n uniform in [n_lo, n_hi],
-    as one block-diagonal union: returns (union graph, gptr)."""
-    rng = np.random.default_rng(seed)
-    sizes = rng.integers(n_lo, n_hi + 1, count)
-    return block_union([erdos_renyi(int(m), mean_deg, seed=int(seed * 100003 + k)) for k, m in enumerate(sizes)])
+    as one block-diagonal union: returns (union graph, gptr).  Every graph has its
+    own seed, so `only` (graph indices) builds the union of a subset, in that order."""
+    sizes = er_batch_sizes(count, n_lo, n_hi, seed)
+    ks = range(count) if only is None else only
+    return block_union([erdos_renyi(int(sizes[k]), mean_deg, seed=int(seed * 100003 + k)) for k in ks])
 
 
 def zero_sum_rhs_graphs(gptr, seed: int) -> np.ndarray:
