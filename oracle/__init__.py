@@ -42,7 +42,7 @@ class Opts(C.Structure):
                 ("alpha_stall", C.c_double), ("relax_fast_ratio", C.c_double),
                 ("max_rounds", C.c_int32), ("max_levels", C.c_int32),
                 ("dense_max", C.c_int32), ("coarse_sweeps", C.c_int32),
-                ("mu_flat", C.c_double), ("seed", C.c_uint64)]
+                ("mu_flat", C.c_double), ("seed", C.c_uint64), ("agg_rule", C.c_int32)]
 
 
 _P = C.c_void_p

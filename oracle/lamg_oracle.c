@@ -37,6 +37,7 @@ void orc_default_opts(orc_opts *o) {
     o->coarse_sweeps = 5;
     o->mu_flat = 4.0 / 3.0;    /* Eq. (3.10) with Q = 2 */
     o->seed = 1;
+    o->agg_rule = 0;           /* parallel handshake */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -578,7 +579,14 @@ static double relax_tvs(orc_level *L, const orc_opts *o, int32_t level) {
  * Rounds stop when alpha_r <= alpha_max = 0.7/gamma, when a round changes
  * nothing, or after max_rounds.  The round whose alpha_r is closest to
  * alpha_max is selected (ties -> earlier).  Numbering: seeds by ascending node
- * index, the dummy aggregate last. */
+ * index, the dummy aggregate last.
+ *
+ * agg_rule = 1 replaces each round by a stage of the paper's sequential scan
+ * (Sec. 3.4.2): the U nodes in increasing index, each deciding on the states
+ * left by the nodes before it.  u joins the admissible non-A neighbour v with
+ * the largest score (the smallest c_uv among those with q_uv <= 2.5, Sec.
+ * 3.4.5); an undecided v thereby becomes a seed.  At most two stages are run,
+ * as in the paper; the selection and the numbering are the same. */
 static void aggregate(orc_level *L, const orc_opts *o) {
     int64_t n = L->n;
     int32_t *state = L->state;
@@ -608,32 +616,52 @@ static void aggregate(orc_level *L, const orc_opts *o) {
     }
     double amax = 0.7 / o->gamma;
     double best_alpha = INFINITY; int32_t best_round = 0, r;
-    for (r = 1; r <= o->max_rounds; r++) {
-        for (int64_t u = 0; u < n; u++) {
-            best[u] = -1;
-            if (state[u] != ST_U) continue;
-            double bs = -1.0;
-            for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++) {
-                int32_t v = L->col[e];
-                double s = L->score[e];
-                if (s < 0.0 || state[v] == ST_A) continue;
-                if (s > bs || (s == bs && best[u] >= 0 && v < best[u])) { bs = s; best[u] = v; }
-            }
-        }
-        memcpy(nstate, state, sizeof(int32_t) * (size_t)n);
-        memcpy(nseed, seed, sizeof(int32_t) * (size_t)n);
+    const int32_t max_stages = o->agg_rule == 1 ? (o->max_rounds < 2 ? o->max_rounds : 2) : o->max_rounds;
+    for (r = 1; r <= max_stages; r++) {
         int changed = 0;
-        for (int64_t u = 0; u < n; u++) {
-            if (state[u] != ST_U || best[u] < 0) continue;
-            int32_t v = best[u];
-            if (state[v] == ST_S) { nstate[u] = ST_A; nseed[u] = v; changed = 1; }
-            else if (state[v] == ST_U && best[v] == (int32_t)u) {
-                int32_t lo = (int32_t)u < v ? (int32_t)u : v, hi = (int32_t)u < v ? v : (int32_t)u;
-                nstate[lo] = ST_S; nstate[hi] = ST_A; nseed[hi] = lo; changed = 1;
+        if (o->agg_rule == 1) {
+            for (int64_t u = 0; u < n; u++) {
+                if (state[u] != ST_U) continue;
+                int32_t bv = -1;
+                double bs = -1.0;
+                for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++) {
+                    int32_t v = L->col[e];
+                    double s = L->score[e];
+                    if (s < 0.0 || state[v] == ST_A || state[v] == ST_D) continue;
+                    if (s > bs || (s == bs && v < bv)) { bs = s; bv = v; }
+                }
+                if (bv < 0) continue;
+                if (state[bv] == ST_U) state[bv] = ST_S;
+                state[u] = ST_A;
+                seed[u] = bv;
+                changed = 1;
             }
+        } else {
+            for (int64_t u = 0; u < n; u++) {
+                best[u] = -1;
+                if (state[u] != ST_U) continue;
+                double bs = -1.0;
+                for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++) {
+                    int32_t v = L->col[e];
+                    double s = L->score[e];
+                    if (s < 0.0 || state[v] == ST_A) continue;
+                    if (s > bs || (s == bs && best[u] >= 0 && v < best[u])) { bs = s; best[u] = v; }
+                }
+            }
+            memcpy(nstate, state, sizeof(int32_t) * (size_t)n);
+            memcpy(nseed, seed, sizeof(int32_t) * (size_t)n);
+            for (int64_t u = 0; u < n; u++) {
+                if (state[u] != ST_U || best[u] < 0) continue;
+                int32_t v = best[u];
+                if (state[v] == ST_S) { nstate[u] = ST_A; nseed[u] = v; changed = 1; }
+                else if (state[v] == ST_U && best[v] == (int32_t)u) {
+                    int32_t lo = (int32_t)u < v ? (int32_t)u : v, hi = (int32_t)u < v ? v : (int32_t)u;
+                    nstate[lo] = ST_S; nstate[hi] = ST_A; nseed[hi] = lo; changed = 1;
+                }
+            }
+            memcpy(state, nstate, sizeof(int32_t) * (size_t)n);
+            memcpy(seed, nseed, sizeof(int32_t) * (size_t)n);
         }
-        memcpy(state, nstate, sizeof(int32_t) * (size_t)n);
-        memcpy(seed, nseed, sizeof(int32_t) * (size_t)n);
         int64_t nc = (nd > 0 ? 1 : 0);
         for (int64_t u = 0; u < n; u++) if (state[u] == ST_S || state[u] == ST_U) nc++;
         double alpha = (double)nc / (double)n;
@@ -644,7 +672,7 @@ static void aggregate(orc_level *L, const orc_opts *o) {
         }
         if (alpha <= amax || !changed) break;
     }
-    L->rounds = r > o->max_rounds ? o->max_rounds : r;
+    L->rounds = r > max_stages ? max_stages : r;
     L->sel_round = best_round;
     L->alpha = best_alpha;
     memcpy(state, bstate, sizeof(int32_t) * (size_t)n);

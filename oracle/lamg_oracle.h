@@ -35,7 +35,7 @@ typedef struct {
     double   gamma;            /* cycle index, Sec. 4.1 ("gamma = 1.5")             */
     int32_t  k_finest;         /* TVs at the finest level, Sec. 4.1 (4)              */
     int32_t  k_max;            /* TVs at coarse levels grow up to this, Sec. 4.1 (10) */
-    int32_t  k_step;           /* TV increase per level (reading: 2)                 */
+    int32_t  k_step;           /* TV increase per level (reading: 1)                 */
     int32_t  nu_tv;            /* GS sweeps per TV, Sec. 4.1 (3)                     */
     int32_t  nu1, nu2;         /* pre/post sweeps, Eq. (4.1) (1, 2)                  */
     int32_t  n_coarsest;       /* stop coarsening below this size, Sec. 4.1 (150)    */
@@ -50,6 +50,9 @@ typedef struct {
     int32_t  coarse_sweeps;    /* GS sweeps when the coarsest level is too large     */
     double   mu_flat;          /* flat energy correction, Eq. (3.9) (4/3)            */
     uint64_t seed;             /* seed of the counter-based generator                */
+    int32_t  agg_rule;         /* 0: the parallel handshake (the library's rule);
+                                  1: the paper's sequential scan, Sec. 3.4.2, at most
+                                  two stages (a quality reference; no GPU counterpart) */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;

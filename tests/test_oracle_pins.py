@@ -341,10 +341,12 @@ GRAPHS = {
 }
 
 
+@pytest.mark.parametrize("rule", [0, 1])
 @pytest.mark.parametrize("gname", list(GRAPHS))
-def test_aggregation_rules(gname):
+def test_aggregation_rules(gname, rule):
+    # rule 0: the parallel handshake; rule 1: the paper's sequential scan (Sec. 3.4.2)
     g = GRAPHS[gname]()
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=rule)
     assert h.num_levels >= 2
     for l in range(h.num_levels - 1):
         info = h.info(l)
@@ -364,6 +366,49 @@ def test_aggregation_rules(gname):
             e = rp[u] + np.searchsorted(col[rp[u]:rp[u + 1]], s)
             assert col[e] == s                                     # a direct neighbour
             assert score[e] >= 0 and q[e] <= 2.5                   # admissible (Sec. 3.4.5)
+        if rule == 1:
+            assert info["rounds"] <= 2                             # at most two stages
+            # a complete scan leaves u undecided only if, at its turn, every admissible
+            # neighbour was an associate, and associates stay associates
+            for u in np.flatnonzero(state == 0):
+                nb = col[rp[u]:rp[u + 1]][score[rp[u]:rp[u + 1]] >= 0]
+                assert np.all(state[nb] == 2)
+
+
+QUALITY = {
+    "grid": lambda: W.grid2d(64, 64),
+    "grid3d": lambda: W.grid3d(24, 24, 24, 1, 1, 0.01),
+    "chung_lu": lambda: W.chung_lu(20000, seed=3),
+    "rgg": lambda: W.rgg2d(10000, seed=4),
+    "er": lambda: W.erdos_renyi(10000, seed=5),
+}
+
+
+def _acf_and_work_per_digit(h, b):
+    _, hist = h.solve(b, tol=1e-8, max_cycles=400)
+    p = len(hist) - 1
+    acf = (hist[-1] / hist[0]) ** (1.0 / p)
+    # cycle work in finest-level entries: level l is visited prod_{k<l} gamma_k times (Eq. (4.1))
+    nnz0, visits, work = h.info(0)["nnz"], 1.0, 0.0
+    for l in range(h.num_levels):
+        i = h.info(l)
+        work += visits * i["nnz"] / nnz0
+        if not i["coarsest"]:
+            visits *= i["gamma"]
+    return acf, work / -math.log10(acf)
+
+
+@pytest.mark.parametrize("gname", list(QUALITY))
+def test_handshake_quality_against_sequential_scan(gname):
+    # The parallel handshake is a reading, not the paper's rule.  Its quality is
+    # checked against the paper's own sequential scan on the same scores: the ACF
+    # within 1.5x, and the work per digit of residual reduction within 2x.
+    g = QUALITY[gname]()
+    b = W.zero_sum_rhs(g.n, 1)
+    acf0, wpd0 = _acf_and_work_per_digit(oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=0), b)
+    acf1, wpd1 = _acf_and_work_per_digit(oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=1), b)
+    assert acf0 <= 1.5 * acf1, (acf0, acf1)
+    assert wpd0 <= 2.0 * wpd1, (wpd0, wpd1)
 
 
 @pytest.mark.parametrize("gname", list(GRAPHS))
