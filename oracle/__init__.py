@@ -42,7 +42,8 @@ class Opts(C.Structure):
                 ("alpha_stall", C.c_double), ("relax_fast_ratio", C.c_double),
                 ("max_rounds", C.c_int32), ("max_levels", C.c_int32),
                 ("dense_max", C.c_int32), ("coarse_sweeps", C.c_int32),
-                ("mu_flat", C.c_double), ("seed", C.c_uint64), ("agg_rule", C.c_int32)]
+                ("mu_flat", C.c_double), ("seed", C.c_uint64), ("agg_rule", C.c_int32),
+                ("elim", C.c_int32), ("elim_min_frac", C.c_double)]
 
 
 _P = C.c_void_p
@@ -79,6 +80,7 @@ def lib():
                 "orc_level_tv": (None, [_P, _I32, _P]),
                 "orc_level_scores": (None, [_P, _I32, _P, _P, _P]),
                 "orc_level_agg": (None, [_P, _I32, _P, _P, _P]),
+                "orc_level_elim": (None, [_P, _I32, _P]),
                 "orc_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _P, _P]),
                 "orc_cycle": (_I32, [_P, _P, _P, _I32]),
                 "orc_adjoint": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32]),
@@ -239,7 +241,7 @@ class Hierarchy:
         return dict(n=int(a[0]), nnz=int(a[1]), ncolours=int(a[2]), K=int(a[3]), nc=int(a[4]),
                     rounds=int(a[5]), sel_round=int(a[6]), coarsest=bool(a[7]),
                     stop_reason=int(a[8]), alpha=float(f[9]), gamma=float(f[10]),
-                    tv_ratio=float(f[11]), jp_rounds=int(a[12]))
+                    tv_ratio=float(f[11]), jp_rounds=int(a[12]), elim=bool(a[13]), nF=int(a[14]))
 
     def csr(self, l):
         i = self.info(l)
@@ -265,6 +267,12 @@ class Hierarchy:
         aff, q, s = np.zeros(nnz), np.zeros(nnz), np.zeros(nnz)
         lib().orc_level_scores(self._h, l, _p(aff), _p(q), _p(s))
         return aff, q, s
+
+    def elim(self, l):
+        """Level l followed by its Schur complement: coarse index of each node, -1 in F."""
+        cidx = np.zeros(self.info(l)["n"], np.int32)
+        lib().orc_level_elim(self._h, l, _p(cidx))
+        return cidx
 
     def agg(self, l):
         n = self.info(l)["n"]

@@ -38,6 +38,8 @@ void orc_default_opts(orc_opts *o) {
     o->mu_flat = 4.0 / 3.0;    /* Eq. (3.10) with Q = 2 */
     o->seed = 1;
     o->agg_rule = 0;           /* parallel handshake */
+    o->elim = 0;               /* no elimination levels (as the library) */
+    o->elim_min_frac = 0.1;    /* reading of "until |F| becomes small", Sec. 3.2 */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -497,6 +499,9 @@ typedef struct {
     int32_t rounds, sel_round;
     double *chol;                     /* coarsest dense factor, if direct */
     int32_t *comp; int32_t ncomp;     /* coarsest: connected components */
+    int32_t elim;                     /* 1: the next level is this level's Schur complement */
+    int64_t nF;                       /* eliminated nodes */
+    int32_t *cidx;                    /* coarse index of each C node, -1 for F nodes */
 } orc_level;
 
 struct orc_hier {
@@ -738,6 +743,98 @@ static void galerkin(const orc_level *F, orc_level *C) {
     free(E); free(D); free(t);
 }
 
+/* Low-degree elimination, Sec. 3.2.  F is an independent set of nodes of
+ * degree 1..4 (unweighted, |E_u|), taken by one scan in increasing index: an
+ * eligible node joins F and its neighbours become ineligible.  (Degree 0 is
+ * left out: an isolated node has a_uu = 0.)  C = N \ F keeps the fine order:
+ * cidx[u] = rank of u among the C nodes, -1 for u in F.  Returns |F|. */
+static int64_t elim_select(const orc_level *L, int32_t *cidx) {
+    int64_t n = L->n, nF = 0, nc = 0;
+    uint8_t *inel = (uint8_t *)xcalloc((size_t)n, 1);
+    for (int64_t u = 0; u < n; u++) {
+        int64_t deg = L->rp[u + 1] - L->rp[u];
+        cidx[u] = 0;
+        if (inel[u] || deg < 1 || deg > 4) continue;
+        cidx[u] = -1;
+        nF++;
+        for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++) inel[L->col[e]] = 1;
+    }
+    for (int64_t u = 0; u < n; u++) if (cidx[u] != -1) cidx[u] = (int32_t)nc++;
+    free(inel);
+    return nF;
+}
+
+typedef struct { int32_t col; int64_t key; double v; } elim_term;
+
+static int elim_cmp(const void *a, const void *b) {
+    const elim_term *x = (const elim_term *)a, *y = (const elim_term *)b;
+    if (x->col != y->col) return x->col < y->col ? -1 : 1;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return 0;
+}
+
+/* Schur complement of F, Eq. (3.1): A^c = A_CC - A_CF A_FF^-1 A_FC, again a
+ * graph Laplacian.  A_FF is diagonal (F independent), so the coarse weight of
+ * c1 != c2 is W^c = w_{c1 c2} + sum over f in F adjacent to both of
+ * (w_{f c1} w_{f c2}) / a_ff.  Summation order (build reading): the direct
+ * edge first, then the fill terms by increasing f, summed canonically; the
+ * product is commutative, so W^c is bit-symmetric.  Coarse rows and columns
+ * follow cidx; the diagonal is the row sum (Eq. (1.2)). */
+static void eliminate(const orc_level *F, const int32_t *cidx, orc_level *C) {
+    int64_t n = F->n, nc = 0, maxt = 0;
+    for (int64_t u = 0; u < n; u++) if (cidx[u] >= 0) nc++;
+    C->n = nc;
+    C->rp = (int64_t *)xcalloc((size_t)(nc + 1), sizeof(int64_t));
+    /* terms of each coarse row: first count them */
+    int64_t *cnt = (int64_t *)xcalloc((size_t)(nc + 1), sizeof(int64_t));
+    for (int64_t u = 0; u < n; u++) {
+        if (cidx[u] < 0) continue;
+        int64_t t = 0;
+        for (int64_t e = F->rp[u]; e < F->rp[u + 1]; e++) {
+            int32_t v = F->col[e];
+            t += cidx[v] >= 0 ? 1 : (F->rp[v + 1] - F->rp[v] - 1);
+        }
+        cnt[cidx[u]] = t;
+        if (t > maxt) maxt = t;
+    }
+    elim_term *T = (elim_term *)xcalloc((size_t)maxt, sizeof(elim_term));
+    double *t = (double *)xcalloc((size_t)maxt, sizeof(double));
+    /* two passes over the rows: sizes, then entries */
+    int64_t cap = 0;
+    for (int64_t U = 0; U < nc; U++) cap += cnt[U];
+    C->col = (int32_t *)xcalloc((size_t)cap, sizeof(int32_t));
+    C->w = (double *)xcalloc((size_t)cap, sizeof(double));
+    int64_t nnz = 0;
+    for (int64_t u = 0; u < n; u++) {
+        if (cidx[u] < 0) continue;
+        int64_t k = 0;
+        for (int64_t e = F->rp[u]; e < F->rp[u + 1]; e++) {
+            int32_t v = F->col[e];
+            if (cidx[v] >= 0) {
+                T[k].col = cidx[v]; T[k].key = -1; T[k].v = F->w[e]; k++;
+                continue;
+            }
+            for (int64_t e2 = F->rp[v]; e2 < F->rp[v + 1]; e2++) {
+                int32_t c2 = F->col[e2];
+                if (c2 == (int32_t)u) continue;
+                T[k].col = cidx[c2]; T[k].key = v; T[k].v = (F->w[e] * F->w[e2]) / F->diag[v]; k++;
+            }
+        }
+        qsort(T, (size_t)k, sizeof(elim_term), elim_cmp);
+        for (int64_t i = 0; i < k;) {
+            int64_t j = i;
+            while (j < k && T[j].col == T[i].col) { t[j - i] = T[j].v; j++; }
+            C->col[nnz] = T[i].col;
+            C->w[nnz] = orc_canon_sum(t, j - i);
+            nnz++;
+            i = j;
+        }
+        C->rp[cidx[u] + 1] = nnz;
+    }
+    C->nnz = nnz;
+    free(cnt); free(T); free(t);
+}
+
 /* Cycle index per level, Eq. (4.1).  As printed, the second branch
  * min{2, .7|E^{l+1}|/|E^l|} is below 0.7 < 1 whenever the coarse level has
  * fewer edges; the text says gamma^l is raised at coarse levels at a bounded
@@ -750,6 +847,7 @@ static void galerkin(const orc_level *F, orc_level *C) {
 static void cycle_indices(orc_hier *h) {
     double m1 = (double)h->lv[0].nnz / 2.0;
     for (int32_t l = 0; l < h->L - 1; l++) {
+        if (h->lv[l].elim) { h->lv[l].gamma_l = 1.0; continue; }   /* Sec. 4.2: gamma = 1 before elimination */
         double ml = (double)h->lv[l].nnz / 2.0, mn = (double)h->lv[l + 1].nnz / 2.0;
         double g = mn > 0.0 ? 0.7 * ml / mn : 2.0;
         double gmax = ml > 0.1 * m1 ? h->o.gamma : 2.0;
@@ -812,6 +910,7 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
     memcpy(L0->col, col, sizeof(int32_t) * (size_t)L0->nnz);
     memcpy(L0->w, w, sizeof(double) * (size_t)L0->nnz);
     int32_t maxl = o->max_levels < 128 ? o->max_levels : 128;
+    int32_t nagg = 0;   /* aggregation levels so far (the TV count grows with them) */
     for (int32_t l = 0;; l++) {
         orc_level *L = &h->lv[l];
         level_prepare(L, o->seed, l);
@@ -821,7 +920,20 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
             st = make_coarsest(L, o);
             break;
         }
-        int32_t K = o->k_finest + o->k_step * l;
+        if (o->elim) {   /* low-degree elimination before aggregating, Sec. 3.2 */
+            int32_t *cidx = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
+            int64_t nF = elim_select(L, cidx);
+            if (nF >= 1 && (double)nF >= o->elim_min_frac * (double)L->n) {
+                L->elim = 1;
+                L->nF = nF;
+                L->cidx = cidx;
+                L->nc = L->n - nF;
+                eliminate(L, cidx, &h->lv[l + 1]);
+                continue;
+            }
+            free(cidx);
+        }
+        int32_t K = o->k_finest + o->k_step * nagg;
         if (K > o->k_max) K = o->k_max;
         if (K > 16) K = 16;
         if (K < 1) K = 1;
@@ -849,6 +961,7 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
             break;
         }
         galerkin(L, &h->lv[l + 1]);
+        nagg++;
     }
     cycle_indices(h);
     if (st != ORC_OK) { orc_free(h); return st; }
@@ -871,7 +984,7 @@ void orc_free(orc_hier *h) {
         orc_level *L = &h->lv[l];
         free(L->rp); free(L->col); free(L->w); free(L->diag); free(L->colour);
         free(L->X); free(L->aff); free(L->q); free(L->score); free(L->hub);
-        free(L->state); free(L->agg); free(L->chol); free(L->comp);
+        free(L->state); free(L->agg); free(L->chol); free(L->comp); free(L->cidx);
     }
     free(h);
 }
@@ -885,6 +998,7 @@ void orc_level_info(const orc_hier *h, int32_t l, int64_t *info) {
     info[5] = L->rounds; info[6] = L->sel_round; info[7] = L->coarsest; info[8] = L->stop_reason;
     memcpy(&info[9], &L->alpha, 8); memcpy(&info[10], &L->gamma_l, 8); memcpy(&info[11], &L->tv_ratio, 8);
     info[12] = L->jp_rounds;
+    info[13] = L->elim; info[14] = L->nF;
 }
 
 void orc_level_csr(const orc_hier *h, int32_t l, int64_t *rp, int32_t *col, double *w) {
@@ -909,6 +1023,11 @@ void orc_level_scores(const orc_hier *h, int32_t l, double *aff, double *q, doub
     memcpy(aff, L->aff, sizeof(double) * (size_t)L->nnz);
     memcpy(q, L->q, sizeof(double) * (size_t)L->nnz);
     memcpy(score, L->score, sizeof(double) * (size_t)L->nnz);
+}
+
+void orc_level_elim(const orc_hier *h, int32_t l, int32_t *cidx) {
+    const orc_level *L = &h->lv[l];
+    if (L->cidx) memcpy(cidx, L->cidx, sizeof(int32_t) * (size_t)L->n);
 }
 
 void orc_level_agg(const orc_hier *h, int32_t l, int32_t *agg, int32_t *state, uint8_t *hub) {
@@ -990,6 +1109,53 @@ static void recombine(const orc_level *L, const double *b, double *x, int theta,
     free(d0); free(d1);
 }
 
+static void visit(solve_ctx *c, int32_t l, int theta);
+
+/* One step of a level whose next level is its Schur complement (Sec. 3.2 and
+ * Sec. 4.2: gamma = 1, no relaxation, no energy correction).  With r = b - A x,
+ * the coarse right-hand side is r_C - A_CF A_FF^-1 r_F, i.e.
+ * b^c_c = r_c + sum over f in F of w_cf r_f / a_ff; after the coarse visit
+ * x_C += x^c, and x_F is recomputed exactly, x_f = (b_f + sum_c w_fc x_c) / a_ff
+ * (back-substitution; with an exact coarse solve the level is solved exactly). */
+static void elim_step(solve_ctx *c, int32_t l) {
+    const orc_hier *h = c->h;
+    const orc_level *F = &h->lv[l], *C = &h->lv[l + 1];
+    int64_t n = F->n;
+    double *x = c->x[l], *b = c->b[l], *r = c->r[l];
+    double *bc = c->b[l + 1], *xc = c->x[l + 1];
+    residual(F, b, x, r);
+    for (int64_t u = 0; u < n; u++) {
+        int32_t U = F->cidx[u];
+        if (U < 0) continue;
+        double s = r[u];
+        for (int64_t e = F->rp[u]; e < F->rp[u + 1]; e++) {
+            int32_t f = F->col[e];
+            if (F->cidx[f] < 0) s += F->w[e] * r[f] / F->diag[f];
+        }
+        bc[U] = s;
+        xc[U] = 0.0;
+    }
+    if (C->coarsest) coarsest_solve(C, &h->o, bc, xc);
+    else if (C->elim) elim_step(c, l + 1);
+    else visit(c, l + 1, 1);
+    for (int64_t u = 0; u < n; u++) if (F->cidx[u] >= 0) x[u] += xc[F->cidx[u]];
+    for (int64_t f = 0; f < n; f++) {
+        if (F->cidx[f] >= 0) continue;
+        double s = b[f];
+        for (int64_t e = F->rp[f]; e < F->rp[f + 1]; e++) s += F->w[e] * x[F->col[e]];
+        x[f] = s / F->diag[f];
+    }
+}
+
+/* theta visits of level l: elimination steps, or the two-level steps below */
+static void visit_level(solve_ctx *c, int32_t l, int theta) {
+    if (c->h->lv[l].elim) {
+        for (int i = 0; i < theta; i++) elim_step(c, l);
+        return;
+    }
+    visit(c, l, theta);
+}
+
 /* One visit to level l (< L-1) consisting of theta two-level steps, Sec. 3.4.6
  * and Fig. 4.2: pre-relax nu1, [save x_i, r_i], b^{l+1} = mu P^T r, coarse
  * visit, x += P x^{l+1}, post-relax nu2; then recombine when adaptive and l is
@@ -1025,7 +1191,7 @@ static void visit(solve_ctx *c, int32_t l, int theta) {
             int th = (int)(ceil((double)(k + 1) * g) - ceil((double)k * g));
             if (th < 1) th = 1;
             if (th > 2) th = 2;
-            visit(c, l + 1, th);
+            visit_level(c, l + 1, th);
         }
         for (int64_t u = 0; u < n; u++) x[u] += xc[F->agg[u]];
         for (int s = 0; s < o->nu2; s++) relax(F, b, x);
@@ -1065,7 +1231,7 @@ static void cycle_once(solve_ctx *c, const double *b, double *x) {
     memcpy(c->x[0], x, sizeof(double) * (size_t)n);
     memcpy(c->b[0], b, sizeof(double) * (size_t)n);
     for (int32_t l = 0; l < h->L; l++) c->visits[l] = 0;
-    visit(c, 0, 1);
+    visit_level(c, 0, 1);
     memcpy(x, c->x[0], sizeof(double) * (size_t)n);
     subtract_mean_ranges(x, h->ngraphs, h->gptr);
 }

@@ -53,6 +53,10 @@ typedef struct {
     int32_t  agg_rule;         /* 0: the parallel handshake (the library's rule);
                                   1: the paper's sequential scan, Sec. 3.4.2, at most
                                   two stages (a quality reference; no GPU counterpart) */
+    int32_t  elim;             /* 1: low-degree elimination levels before each
+                                  aggregation, Sec. 3.2 (default 0: none, as the library) */
+    double   elim_min_frac;    /* an elimination round is kept only if it removes at
+                                  least this fraction of the level's nodes (reading: 0.1) */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;
@@ -106,6 +110,8 @@ void     orc_level_colour(const orc_hier *h, int32_t l, int32_t *colour);
 void     orc_level_tv(const orc_hier *h, int32_t l, double *X);
 void     orc_level_scores(const orc_hier *h, int32_t l, double *aff, double *q, double *score);
 void     orc_level_agg(const orc_hier *h, int32_t l, int32_t *agg, int32_t *state, uint8_t *hub);
+/* level l followed by an elimination level: cidx[u] = coarse index of u, or -1 for u in F */
+void     orc_level_elim(const orc_hier *h, int32_t l, int32_t *cidx);
 
 /* ---- solve ---- */
 /* Cycles until ||b - A x||_2 <= tol ||b||_2 or max_cycles. x: in = initial guess, out = result.
