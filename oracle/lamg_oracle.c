@@ -61,6 +61,10 @@ static uint64_t colour_key(uint64_t seed, int32_t level) {
 static uint64_t tv_key(uint64_t seed, int32_t level) {
     return orc_splitmix64(orc_splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 2)));
 }
+/* elimination scan order: the colour key's form with the top bit set */
+static uint64_t elim_key(uint64_t seed, int32_t level) {
+    return orc_splitmix64(orc_splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 1)) ^ (1ULL << 63));
+}
 
 /* TV initial value "random[-1,1]" (Sec. 3.3.1): the top 53 bits of the draw as a
  * uniform t in [0,1), then 2t - 1 (both steps exact in FP64). */
@@ -744,23 +748,38 @@ static void galerkin(const orc_level *F, orc_level *C) {
 }
 
 /* Low-degree elimination, Sec. 3.2.  F is an independent set of nodes of
- * degree 1..4 (unweighted, |E_u|), taken by one scan in increasing index: an
- * eligible node joins F and its neighbours become ineligible.  (Degree 0 is
- * left out: an isolated node has a_uu = 0.)  C = N \ F keeps the fine order:
- * cidx[u] = rank of u among the C nodes, -1 for u in F.  Returns |F|. */
-static int64_t elim_select(const orc_level *L, int32_t *cidx) {
+ * degree 1..4 (unweighted, |E_u|), taken by one sweep through the nodes: an
+ * eligible node joins F and its neighbours become ineligible.  The paper does
+ * not fix the sweep order; this build sweeps by decreasing priority
+ * splitmix64(elim_key + u), ties to the lower index, so that the same set can
+ * be found in parallel rounds of small depth (each candidate waits only for
+ * its higher-priority candidate neighbours).  Degree 0 is left out: an
+ * isolated node has a_uu = 0.  C = N \ F keeps the fine order: cidx[u] = rank
+ * of u among the C nodes, -1 for u in F.  Returns |F|. */
+typedef struct { uint64_t p; int64_t u; } elim_prio;
+
+static int elim_prio_cmp(const void *a, const void *b) {
+    const elim_prio *x = (const elim_prio *)a, *y = (const elim_prio *)b;
+    if (x->p != y->p) return x->p > y->p ? -1 : 1;
+    return x->u < y->u ? -1 : (x->u > y->u);
+}
+
+static int64_t elim_select(const orc_level *L, uint64_t key, int32_t *cidx) {
     int64_t n = L->n, nF = 0, nc = 0;
     uint8_t *inel = (uint8_t *)xcalloc((size_t)n, 1);
-    for (int64_t u = 0; u < n; u++) {
+    elim_prio *ord = (elim_prio *)xcalloc((size_t)n, sizeof(elim_prio));
+    for (int64_t u = 0; u < n; u++) { ord[u].p = orc_splitmix64(key + (uint64_t)u); ord[u].u = u; cidx[u] = 0; }
+    qsort(ord, (size_t)n, sizeof(elim_prio), elim_prio_cmp);
+    for (int64_t i = 0; i < n; i++) {
+        int64_t u = ord[i].u;
         int64_t deg = L->rp[u + 1] - L->rp[u];
-        cidx[u] = 0;
         if (inel[u] || deg < 1 || deg > 4) continue;
         cidx[u] = -1;
         nF++;
         for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++) inel[L->col[e]] = 1;
     }
     for (int64_t u = 0; u < n; u++) if (cidx[u] != -1) cidx[u] = (int32_t)nc++;
-    free(inel);
+    free(inel); free(ord);
     return nF;
 }
 
@@ -922,7 +941,7 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
         }
         if (o->elim) {   /* low-degree elimination before aggregating, Sec. 3.2 */
             int32_t *cidx = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
-            int64_t nF = elim_select(L, cidx);
+            int64_t nF = elim_select(L, elim_key(o->seed, l), cidx);
             if (nF >= 1 && (double)nF >= o->elim_min_frac * (double)L->n) {
                 L->elim = 1;
                 L->nF = nF;
