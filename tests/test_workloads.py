@@ -23,6 +23,7 @@ GENERATORS = {
     "star": lambda: W.star(40),
     "complete": lambda: W.complete(30),
     "grid2d": lambda: W.grid2d(12, 9),
+    "torus": lambda: W.grid2d_periodic(10),
     "grid3d": lambda: W.grid3d(6, 5, 4, 1.0, 1.0, 0.01),
     "chung_lu": lambda: W.chung_lu(20000, seed=3),
     "rgg": lambda: W.rgg2d(20000, seed=4),
@@ -45,6 +46,8 @@ def test_recipe_sizes():
     assert (g.n, g.m) == (120, 5 * 5 * 4 + 6 * 4 * 4 + 6 * 5 * 3)
     assert set(np.unique(g.w)) == {0.01, 1.0}
     assert (W.path(50).m, W.star(40).m, W.complete(30).m) == (49, 39, 30 * 29 // 2)
+    t = W.grid2d_periodic(10)
+    assert (t.n, t.m) == (100, 200) and np.all(np.diff(t.rp) == 4)       # a torus: degree 4 everywhere
     cl = W.chung_lu(20000, seed=3)
     mean = 2 * cl.m / cl.n
     assert 8.0 <= mean <= 12.0
