@@ -731,6 +731,7 @@ void set_batch_cols(lamg_ctx *h, int32_t cols) {
 void autotune_batched(lamg_ctx *h, int32_t nrhs, lamg_precision p, cudaStream_t s, int32_t *chosen,
                       double *ms_out) {
     LAMG_REQUIRE(h->ngraphs == 1, LAMG_ERR_ARG, "lamg_autotune_batched: needs a single-graph handle");
+    LAMG_REQUIRE(!has_elim(h), LAMG_ERR_ARG, "lamg_autotune_batched: elimination levels are not supported");
     prepare_solve(h);
     const int32_t n = h->lv[0].n;
     const int kind = p == LAMG_FP64 ? 0 : 1;
@@ -775,6 +776,7 @@ void solve_batched_device(lamg_ctx *h, int32_t nrhs, const double *B, double *X,
     const auto t0 = std::chrono::steady_clock::now();
     LAMG_REQUIRE(h->ngraphs == 1, LAMG_ERR_ARG,
                  "lamg_solve_batched: several right-hand sides need a single-graph handle");
+    LAMG_REQUIRE(!has_elim(h), LAMG_ERR_ARG, "lamg_solve_batched: elimination levels are not supported");
     prepare_solve(h);
     const int32_t n = h->lv[0].n;
     const int32_t *perm = h->lv[0].perm.get();
