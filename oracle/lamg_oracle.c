@@ -783,6 +783,15 @@ static int64_t elim_select(const orc_level *L, uint64_t key, int32_t *cidx) {
     return nF;
 }
 
+int64_t orc_elim_set(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key, int32_t *cidx) {
+    orc_level L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    L.rp = (int64_t *)rp;
+    L.col = (int32_t *)col;
+    return elim_select(&L, key, cidx);
+}
+
 typedef struct { int32_t col; int64_t key; double v; } elim_term;
 
 static int elim_cmp(const void *a, const void *b) {
