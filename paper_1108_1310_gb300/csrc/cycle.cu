@@ -593,7 +593,6 @@ struct Builder {
         if (h->lv[l].elim) {
             // Sec. 3.2 / 4.2: a level above an elimination has gamma = 1 and no
             // relaxation; the step is exact, so no recombination and no mu
-            if (groups) throw Error{LAMG_ERR_ARG, "batched solves do not support elimination levels"};
             for (int i = 0; i < theta; i++) {
                 emit(OP_RESID, l, -1, 0, sb);
                 emit(OP_ELIM_RESTRICT, l, 0, 0, sb);

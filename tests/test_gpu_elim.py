@@ -163,11 +163,17 @@ def test_elim_adjoint_matches_oracle(L):
     s.close()
 
 
-def test_elim_batched_is_rejected(L):
-    g = _graph("grid2d")
+@pytest.mark.parametrize("gname,R", [("grid2d", 4), ("chung_lu", 9), ("hubs", 16)])
+def test_elim_batched_matches_single(L, gname, R):
+    # the batched engine runs the same elimination steps on 4 interleaved columns
+    g = _graph(gname)
     s = L.Solver.from_graph(g, elim=1)
-    B = torch.tensor(W.zero_sum_rhs(g.n, 9, count=4), device="cuda")
-    with pytest.raises(L.LamgError) as e:
-        s.solve_batched(B)
-    assert e.value.status == L.LAMG_ERR_ARG
+    B = W.zero_sum_rhs(g.n, 9, count=R)
+    X, stats = s.solve_batched(torch.tensor(B, device="cuda"), tol=1e-10)
+    Xg = X.cpu().numpy()
+    for c in sorted({0, R // 2, R - 1}):
+        xs, st1 = s.solve(torch.tensor(np.ascontiguousarray(B[:, c]), device="cuda"), tol=1e-10)
+        assert stats[c].status == 0 and stats[c].rel_res <= 1e-10
+        assert abs(stats[c].cycles - st1.cycles) <= 1
+        assert np.linalg.norm(Xg[:, c] - xs.cpu().numpy()) <= 1e-7 * np.linalg.norm(xs.cpu().numpy())
     s.close()
