@@ -886,11 +886,21 @@ static void cycle_indices(orc_hier *h) {
     h->lv[h->L - 1].gamma_l = 0.0;
 }
 
-static void level_prepare(orc_level *L, uint64_t seed, int32_t level) {
+static void level_diag(orc_level *L) {
     L->diag = (double *)xcalloc((size_t)L->n, sizeof(double));
     diag_canon(L->n, L->rp, L->w, L->diag);
+}
+
+/* The JP colouring of a level that relaxes.  A level followed by elimination
+ * never relaxes (Sec. 4.2: nu = 0 there), so it gets one colour, 0, instead. */
+static void level_colour(orc_level *L, uint64_t seed, int32_t level, int relaxes) {
     L->colour = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
-    L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), L->colour, &L->jp_rounds);
+    if (relaxes) {
+        L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), L->colour, &L->jp_rounds);
+    } else {
+        L->ncolours = 1;
+        L->jp_rounds = 0;
+    }
 }
 
 /* Coarsest level: the direct solve uses (A + sum_K 1_K 1_K^T / n_K)^-1 over the
@@ -941,9 +951,10 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
     int32_t nagg = 0;   /* aggregation levels so far (the TV count grows with them) */
     for (int32_t l = 0;; l++) {
         orc_level *L = &h->lv[l];
-        level_prepare(L, o->seed, l);
+        level_diag(L);
         h->L = l + 1;
         if (L->n < o->n_coarsest || l + 1 >= maxl) {
+            level_colour(L, o->seed, l, 1);
             L->stop_reason = L->n < o->n_coarsest ? 1 : 4;
             st = make_coarsest(L, o);
             break;
@@ -952,6 +963,7 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
             int32_t *cidx = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
             int64_t nF = elim_select(L, elim_key(o->seed, l), cidx);
             if (nF >= 1 && (double)nF >= o->elim_min_frac * (double)L->n) {
+                level_colour(L, o->seed, l, 0);
                 L->elim = 1;
                 L->nF = nF;
                 L->cidx = cidx;
@@ -961,6 +973,7 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
             }
             free(cidx);
         }
+        level_colour(L, o->seed, l, 1);
         int32_t K = o->k_finest + o->k_step * nagg;
         if (K > o->k_max) K = o->k_max;
         if (K > 16) K = 16;

@@ -1375,54 +1375,59 @@ static int coop_grid(const void *kernel, const char *what) {
     return sms;
 }
 
-static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s) {
+// The JP colouring of a level that relaxes, and the (colour, tier, id) order of
+// its nodes.  A level followed by elimination never relaxes (nu = 0, Sec. 4.2):
+// it gets one colour, 0, and only the order.
+static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s, bool relaxes = true) {
     const int32_t n = L.n;
     L.colour.alloc(n);
-    k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, -1);
+    k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, relaxes ? -1 : 0);
     LAMG_CHECK_LAUNCH();
-    const uint64_t key = colour_key(h->opt.seed, level);
-    PhaseTimer ct(s);
-    ct.level = level;
     int32_t batch_rounds = 0;
     const int32_t fin_rounds = 0;
-    {
-    // wait counts, the first frontier, then all rounds in one cooperative launch
-    Tmp<int32_t> deg(n, s), wait(n, s);
-    Tmp<uint64_t> hsh(n, s);
-    k_jp_prio<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), key, deg.get(), hsh.get());
-    LAMG_CHECK_LAUNCH();
-    LAUNCH3(k_jp_wait, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
-            deg.get(), hsh.get(), wait.get());
-    const int64_t cap = n;
-    Tmp<int32_t> lst(6 * (size_t)cap, s), fcnt(6, s), out(1, s), err(1, s);
-    Tmp<unsigned int> bar(2, s);
-    int32_t c6[6] = {0, 0, 0, 0, 0, 0};
-    {
-        Tmp<uint8_t> f(n, s);
-        for (int t = 0; t < 3; t++) {
-            k_jp_ready<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), n, t, wait.get(), f.get());
-            LAMG_CHECK_LAUNCH();
-            c6[t] = (int32_t)compact_indices(f.get(), lst.get() + t * cap, n, s);
+    if (relaxes) {
+        const uint64_t key = colour_key(h->opt.seed, level);
+        PhaseTimer ct(s);
+        ct.level = level;
+        {
+        // wait counts, the first frontier, then all rounds in one cooperative launch
+        Tmp<int32_t> deg(n, s), wait(n, s);
+        Tmp<uint64_t> hsh(n, s);
+        k_jp_prio<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), key, deg.get(), hsh.get());
+        LAMG_CHECK_LAUNCH();
+        LAUNCH3(k_jp_wait, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
+                deg.get(), hsh.get(), wait.get());
+        const int64_t cap = n;
+        Tmp<int32_t> lst(6 * (size_t)cap, s), fcnt(6, s), out(1, s), err(1, s);
+        Tmp<unsigned int> bar(2, s);
+        int32_t c6[6] = {0, 0, 0, 0, 0, 0};
+        {
+            Tmp<uint8_t> f(n, s);
+            for (int t = 0; t < 3; t++) {
+                k_jp_ready<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), n, t, wait.get(), f.get());
+                LAMG_CHECK_LAUNCH();
+                c6[t] = (int32_t)compact_indices(f.get(), lst.get() + t * cap, n, s);
+            }
         }
-    }
-    LAMG_CUDA(cudaMemcpyAsync(fcnt.get(), c6, sizeof(c6), cudaMemcpyHostToDevice, s));
-    LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
-    LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
-    const int grid = coop_grid((const void *)k_jp_dag, "colouring kernel");
-    {
-        const int32_t *rpp = L.rp.get(), *colp = L.col.get(), *dp = deg.get();
-        const uint64_t *hp = hsh.get();
-        int32_t *wp = wait.get(), *colour = L.colour.get(), *lp = lst.get(), *cp = fcnt.get(), *op = out.get(),
-                *ep = err.get();
-        int64_t capv = cap;
-        unsigned int *bp = bar.get();
-        void *args[] = {&rpp, &colp, &dp, &hp, &wp, &colour, &lp, &capv, &cp, &op, &bp, &ep};
-        LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_jp_dag, dim3(grid), dim3(kBlk), args, 0, s));
-        note_launch();
-    }
-    LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "colouring: grid barrier timed out");
-    batch_rounds = read_scalar(out.get(), s);
-    ct.mark("jp_rounds");
+        LAMG_CUDA(cudaMemcpyAsync(fcnt.get(), c6, sizeof(c6), cudaMemcpyHostToDevice, s));
+        LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
+        LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
+        const int grid = coop_grid((const void *)k_jp_dag, "colouring kernel");
+        {
+            const int32_t *rpp = L.rp.get(), *colp = L.col.get(), *dp = deg.get();
+            const uint64_t *hp = hsh.get();
+            int32_t *wp = wait.get(), *colour = L.colour.get(), *lp = lst.get(), *cp = fcnt.get(), *op = out.get(),
+                    *ep = err.get();
+            int64_t capv = cap;
+            unsigned int *bp = bar.get();
+            void *args[] = {&rpp, &colp, &dp, &hp, &wp, &colour, &lp, &capv, &cp, &op, &bp, &ep};
+            LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_jp_dag, dim3(grid), dim3(kBlk), args, 0, s));
+            note_launch();
+        }
+        LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "colouring: grid barrier timed out");
+        batch_rounds = read_scalar(out.get(), s);
+        ct.mark("jp_rounds");
+        }
     }
     L.jp_rounds = batch_rounds + fin_rounds;
     L.ncolours = reduce_max_i32(L.colour.get(), n, s) + 1;
@@ -1877,9 +1882,9 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         LAUNCH3(k_node_stats, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
                 L.col.get(), L.w.get(), o.hub_factor, diag.get(), maxw.get(), L.hub.get());
         pt.mark("stats");
-        colour_level(h, L, l, T, s);
-        pt.mark("colour");
         if (nl < o.n_coarsest || l + 1 >= maxl) {
+            colour_level(h, L, l, T, s);
+            pt.mark("colour");
             L.coarsest = 1;
             L.stop_reason = nl < o.n_coarsest ? 1 : 4;
             break;
@@ -1887,6 +1892,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         if (o.elim) {   // low-degree elimination before aggregating (Sec. 3.2)
             L.nF = select_elim(h, L, l, s);
             if (L.nF >= 1 && (double)L.nF >= o.elim_min_frac * (double)nl) {
+                colour_level(h, L, l, T, s, false);   // no relaxation on this level: one colour
                 L.elim = 1;
                 L.nc = (int32_t)(nl - L.nF);
                 Tmp<int32_t> erow(L.nnz, s);
@@ -1900,6 +1906,8 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
             L.nF = 0;
             L.cidx.release();
         }
+        colour_level(h, L, l, T, s);
+        pt.mark("colour");
         int K = o.k_finest + o.k_step * nagg;
         if (K > o.k_max) K = o.k_max;
         if (K > 16) K = 16;
