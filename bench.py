@@ -4,7 +4,7 @@ exponent 2.5, mean degree 10, FP32 weights, FP32 cycles inside FP64 iterative
 refinement), timed with CUDA events.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload chung_lu1m|grid256|grid64] [--precision fp32ir|fp64]
+                  [--workload chung_lu1m|grid256|grid64|grid1024] [--precision fp32ir|fp64] [--elim]
 
 Multi-GPU: the solve of one graph does not shard (each relaxation sweep would
 need a halo exchange); N GPUs run N independent replicas of the step.  The
@@ -36,8 +36,9 @@ WORKLOADS = {
     "grid256": ("grid256", "fp32ir",
                 "256^3 7-point grid, weights 1/1/0.01; FP32 cycles in FP64 IR to 1e-8"),
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
+    "grid1024": ("grid1024", "fp32ir", "1024x1024 5-point grid, unit weights (run with --elim); FP32 cycles in FP64 IR to 1e-8"),
 }
-TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10}
+TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10, "grid1024": 1e-8}
 # DRAM bytes (read + write) of one engine launch from one ncu capture of this
 # workload (profiles/k_engine_chung_lu1m_fp32ir.md); must be emptied
 # whenever the engine kernel changes.
@@ -54,7 +55,8 @@ BATCHED = {
     "er500": "500 Erdos-Renyi graphs (LCC), n uniform in [1k, 200k], mean degree 8, unit weights, one zero-sum "
              "RHS each, as one block-diagonal union (lamg_setup_graphs); FP32 cycles in FP64 IR to 1e-8 per graph",
 }
-CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64)}
+CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64),
+              "grid1024": ("grid2d", 256)}
 
 
 def load_peaks():
