@@ -91,13 +91,15 @@ typedef struct {
                                   uses b minus its mean instead (per graph, per column),
                                   the compatible part of b (Sec. 1), and leaves the
                                   caller's b unchanged                                    */
+    double   mu_adaptive;      /* restriction factor of the adaptive cycle (recombination,
+                                  Eq. (3.13)): 1 (default) or a mild flat correction
+                                  on top of recombination; see the oracle's figures    */
     int32_t  elim;             /* 1: low-degree elimination levels before each aggregation
                                   (Sec. 3.2): an independent set F of degree-1..4 nodes,
                                   taken by one sweep in decreasing hashed priority, is
                                   replaced by the Schur complement on the rest; the level
                                   above it then has gamma = 1 and no relaxation, and the
-                                  cycle back-substitutes F exactly.  Default 0.  Batched
-                                  solves (lamg_solve_batched) reject such hierarchies.    */
+                                  cycle back-substitutes F exactly.  Default 0.           */
     double   elim_min_frac;    /* an elimination round is kept only if it removes at least
                                   this fraction of the level's nodes: 0.1                 */
 } lamg_options;
