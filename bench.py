@@ -4,7 +4,7 @@ exponent 2.5, mean degree 10, FP32 weights, FP32 cycles inside FP64 iterative
 refinement), timed with CUDA events.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload chung_lu1m|grid256|grid64] [--precision fp32ir|fp64]
+                  [--workload chung_lu1m|grid256|grid64|grid1024] [--precision fp32ir|fp64] [--elim]
 
 Multi-GPU: the solve of one graph does not shard (each relaxation sweep would
 need a halo exchange); N GPUs run N independent replicas of the step.  The
@@ -36,8 +36,9 @@ WORKLOADS = {
     "grid256": ("grid256", "fp32ir",
                 "256^3 7-point grid, weights 1/1/0.01; FP32 cycles in FP64 IR to 1e-8"),
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
+    "grid1024": ("grid1024", "fp32ir", "1024x1024 5-point grid, unit weights (run with --elim); FP32 cycles in FP64 IR to 1e-8"),
 }
-TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10}
+TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10, "grid1024": 1e-8}
 # DRAM bytes (read + write) of one engine launch from one ncu capture of this
 # workload (profiles/k_engine_chung_lu1m_fp32ir.md); must be emptied
 # whenever the engine kernel changes.
@@ -54,7 +55,8 @@ BATCHED = {
     "er500": "500 Erdos-Renyi graphs (LCC), n uniform in [1k, 200k], mean degree 8, unit weights, one zero-sum "
              "RHS each, as one block-diagonal union (lamg_setup_graphs); FP32 cycles in FP64 IR to 1e-8 per graph",
 }
-CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64)}
+CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64),
+              "grid1024": ("grid2d", 256)}
 
 
 def load_peaks():
@@ -76,11 +78,11 @@ def sample_graph(workload):
     return W.grid2d(size, size), f"{size}x{size} 5-point grid"
 
 
-def cpu_oracle_step(g, b, tol, gamma_coarse_max=2.0):
+def cpu_oracle_step(g, b, tol, gamma_coarse_max=2.0, elim=0):
     """The oracle as it stands: FP64 setup + solve on one host core."""
     import oracle
     t0 = time.perf_counter()
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma_coarse_max=gamma_coarse_max)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma_coarse_max=gamma_coarse_max, elim=elim)
     x, hist = h.solve(b, tol=tol, max_cycles=500)
     t = time.perf_counter() - t0
     return t, len(hist) - 1
@@ -144,10 +146,10 @@ def run_reference(args):
     b = W.zero_sum_rhs(g.n, 2)
     tol = TOL[args.workload]
     for _ in range(min(args.warmup, 1)):
-        cpu_oracle_step(g, b, tol, args.gamma_coarse_max)
+        cpu_oracle_step(g, b, tol, args.gamma_coarse_max, elim=int(args.elim))
     ts, cyc = [], []
     for _ in range(args.steps):
-        t, c = cpu_oracle_step(g, b, tol, args.gamma_coarse_max)
+        t, c = cpu_oracle_step(g, b, tol, args.gamma_coarse_max, elim=int(args.elim))
         ts.append(t)
         cyc.append(c)
     tmean = sum(ts) / len(ts)
@@ -158,7 +160,7 @@ def run_reference(args):
         "ms_per_step": tmean * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample": desc, "n": g.n, "m": g.m, "tol": tol,
-                   "gamma_coarse_max": args.gamma_coarse_max},
+                   "gamma_coarse_max": args.gamma_coarse_max, "elim": bool(args.elim)},
         "cpu_baseline": {"value": value, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "edges*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -446,6 +448,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--elim", action="store_true",
+                    help="low-degree elimination levels (Sec. 3.2) in the hierarchy (default workload only)")
     ap.add_argument("--gamma-coarse-max", type=float, default=2.0,
                     help="cap of the cycle index at the coarse levels (Eq. (4.1) prints 2)")
     args = ap.parse_args()
@@ -485,7 +489,8 @@ def main():
     w = torch.tensor(g.w, device=dev).to(w_dtype)
     b = torch.tensor(b_host, device=dev)
     x = torch.zeros_like(b)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000, gamma_coarse_max=args.gamma_coarse_max)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, gamma_coarse_max=args.gamma_coarse_max,
+                                 elim=int(args.elim))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
     def step(profile=False):
@@ -594,7 +599,7 @@ def main():
         avg = prof_ms / prof_cnt
         achieved = prof_bytes / (avg / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get((args.workload, prec_name)), "kernel": "cycle engine (one launch = one refinement step: ir_inner FP32 cycles + FP64 residual)",
+                "traffic": None if args.elim else NCU_TRAFFIC.get((args.workload, prec_name)), "kernel": "cycle engine (one launch = one refinement step: ir_inner FP32 cycles + FP64 residual)",
                 "bytes_per_launch": prof_bytes, "avg_ms": avg, "launches": prof_cnt,
                 "peak_kind": f"{peak_kind} hbm_gbs"}
 
@@ -602,7 +607,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sg, sdesc = sample_graph(args.workload)
         sb = W.zero_sum_rhs(sg.n, 2)
-        t, c = cpu_oracle_step(sg, sb, tol, args.gamma_coarse_max)
+        t, c = cpu_oracle_step(sg, sb, tol, args.gamma_coarse_max, elim=int(args.elim))
         cpu = {"value": sg.m * c / t, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
                "sample": f"{sdesc}, FP64 setup + solve to {tol:g}, {t:.1f} s"}
 
@@ -613,7 +618,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == L.LAMG_FP32_IR else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "tol": tol,
-                   "precision": prec_name, "gamma_coarse_max": args.gamma_coarse_max, "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
+                   "precision": prec_name, "gamma_coarse_max": args.gamma_coarse_max, "elim": bool(args.elim), "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
                    "rel_res": s0.rel_res, "time_to_tol_s": ms / 1e3,
                    "setup_s_host": s0.t_setup_s, "solve_s_host": s0.t_solve_s,
                    "model_bytes_per_cycle": s0.bytes_per_cycle32 if prec == L.LAMG_FP32_IR else s0.bytes_per_cycle,

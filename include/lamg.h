@@ -99,6 +99,14 @@ typedef struct {
                                   (|E^l| <= .1 |E|), Eq. (4.1): 2 as printed.  1 makes
                                   the coarse part of the cycle a V-cycle.  Must lie in
                                   [1, 2], else LAMG_ERR_ARG                             */
+    int32_t  elim;             /* 1: low-degree elimination levels before each aggregation
+                                  (Sec. 3.2): an independent set F of degree-1..4 nodes,
+                                  taken by one sweep in decreasing hashed priority, is
+                                  replaced by the Schur complement on the rest; the level
+                                  above it then has gamma = 1 and no relaxation, and the
+                                  cycle back-substitutes F exactly.  Default 0.           */
+    double   elim_min_frac;    /* an elimination round is kept only if it removes at least
+                                  this fraction of the level's nodes: 0.1                 */
 } lamg_options;
 
 typedef struct {
@@ -229,13 +237,17 @@ void lamg_free(lamg_handle h);
 
 /* Per-level summary.  info[0..15]: n, nnz, ncolours, K, nc, rounds, sel_round,
  * coarsest, stop_reason, alpha (FP64 bits), gamma_l (FP64 bits), tv_ratio (FP64
- * bits), jp_rounds, dense (1 if the coarsest is solved by the dense inverse). */
+ * bits), jp_rounds, dense (1 if the coarsest is solved by the dense inverse),
+ * elim (1 if the next level is this level's Schur complement), nF (eliminated
+ * nodes). */
 lamg_status lamg_level_info(lamg_handle h, int32_t level, int64_t *info_host);
 
 /* Copy one per-level array to host memory.  Fields (natural node order):
  *  0 row_ptr int64[n+1]   1 col int32[nnz]   2 w FP64[nnz]   3 colour int32[n]
  *  4 agg int32[n]         5 state int32[n]   6 hub uint8[n]
  *  7 tv FP64[n*K]         8 affinity FP64[nnz]  9 q FP64[nnz]   10 score FP64[nnz]
+ *  11 cidx int32[n]: on a level followed by elimination, the coarse index of each
+ *     node, -1 for the eliminated nodes
  * Fields 7-9 need keep_setup_data.  Returns LAMG_ERR_ARG for a field that the
  * level does not have. */
 lamg_status lamg_level_copy(lamg_handle h, int32_t level, int32_t field, void *host_dst,

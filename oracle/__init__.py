@@ -82,6 +82,7 @@ def lib():
                 "orc_level_scores": (None, [_P, _I32, _P, _P, _P]),
                 "orc_level_agg": (None, [_P, _I32, _P, _P, _P]),
                 "orc_level_elim": (None, [_P, _I32, _P]),
+                "orc_elim_set": (_I64, [_I64, _P, _P, _U64, _P]),
                 "orc_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _P, _P]),
                 "orc_cycle": (_I32, [_P, _P, _P, _I32]),
                 "orc_adjoint": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32]),
@@ -150,6 +151,15 @@ def colour(n, rp, col, key):
     c = np.zeros(n, dtype=np.int32)
     nc = lib().orc_colour(n, _p(rp), _p(col), key & 0xFFFFFFFFFFFFFFFF, _p(c))
     return c, int(nc)
+
+
+def elim_set(n, rp, col, key):
+    """Eliminated set of a graph (Sec. 3.2): coarse index of each node, -1 in F."""
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    cidx = np.zeros(n, np.int32)
+    nF = lib().orc_elim_set(n, _p(rp), _p(col), key & 0xFFFFFFFFFFFFFFFF, _p(cidx))
+    return cidx, int(nF)
 
 
 def gs_sweep_lex(n, rp, col, w, b, x):

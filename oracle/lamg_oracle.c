@@ -786,6 +786,15 @@ static int64_t elim_select(const orc_level *L, uint64_t key, int32_t *cidx) {
     return nF;
 }
 
+int64_t orc_elim_set(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key, int32_t *cidx) {
+    orc_level L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    L.rp = (int64_t *)rp;
+    L.col = (int32_t *)col;
+    return elim_select(&L, key, cidx);
+}
+
 typedef struct { int32_t col; int64_t key; double v; } elim_term;
 
 static int elim_cmp(const void *a, const void *b) {
@@ -883,20 +892,28 @@ static void cycle_indices(orc_hier *h) {
 }
 
 /* Lean Geometric Multigrid (Sec. 6): red-black colours of an nx x nx torus */
-static void level_prepare_rb(orc_level *L, int32_t nx) {
-    L->diag = (double *)xcalloc((size_t)L->n, sizeof(double));
-    diag_canon(L->n, L->rp, L->w, L->diag);
+static void level_colour_rb(orc_level *L, int32_t nx) {
     L->colour = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
     for (int64_t u = 0; u < L->n; u++) L->colour[u] = (int32_t)(((u % nx) + (u / nx)) & 1);
     L->ncolours = 2;
     L->jp_rounds = 0;
 }
 
-static void level_prepare(orc_level *L, uint64_t seed, int32_t level) {
+static void level_diag(orc_level *L) {
     L->diag = (double *)xcalloc((size_t)L->n, sizeof(double));
     diag_canon(L->n, L->rp, L->w, L->diag);
+}
+
+/* The JP colouring of a level that relaxes.  A level followed by elimination
+ * never relaxes (Sec. 4.2: nu = 0 there), so it gets one colour, 0, instead. */
+static void level_colour(orc_level *L, uint64_t seed, int32_t level, int relaxes) {
     L->colour = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
-    L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), L->colour, &L->jp_rounds);
+    if (relaxes) {
+        L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), L->colour, &L->jp_rounds);
+    } else {
+        L->ncolours = 1;
+        L->jp_rounds = 0;
+    }
 }
 
 /* Coarsest level: the direct solve uses (A + sum_K 1_K 1_K^T / n_K)^-1 over the
@@ -949,15 +966,17 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
     if (nxl > 0 && (int64_t)nxl * nxl != n) { orc_free(h); return ORC_ERR_ARG; }
     for (int32_t l = 0;; l++) {
         orc_level *L = &h->lv[l];
-        if (nxl > 0) level_prepare_rb(L, nxl);
-        else level_prepare(L, o->seed, l);
+        level_diag(L);
         h->L = l + 1;
         if (L->n < o->n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
+            if (nxl > 0) level_colour_rb(L, nxl);
+            else level_colour(L, o->seed, l, 1);
             L->stop_reason = L->n < o->n_coarsest ? 1 : 4;
             st = make_coarsest(L, o);
             break;
         }
         if (nxl > 0) {   /* Lean Geometric MG: 1:2 coarsening in both directions, 2x2 aggregates */
+            level_colour_rb(L, nxl);
             const int32_t nc2 = nxl / 2;
             L->agg = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
             L->state = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
@@ -974,6 +993,7 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
             int32_t *cidx = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
             int64_t nF = elim_select(L, elim_key(o->seed, l), cidx);
             if (nF >= 1 && (double)nF >= o->elim_min_frac * (double)L->n) {
+                level_colour(L, o->seed, l, 0);
                 L->elim = 1;
                 L->nF = nF;
                 L->cidx = cidx;
@@ -983,6 +1003,7 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
             }
             free(cidx);
         }
+        level_colour(L, o->seed, l, 1);
         int32_t K = o->k_finest + o->k_step * nagg;
         if (K > o->k_max) K = o->k_max;
         if (K > 16) K = 16;

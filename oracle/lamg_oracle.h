@@ -116,6 +116,9 @@ void     orc_level_colour(const orc_hier *h, int32_t l, int32_t *colour);
 void     orc_level_tv(const orc_hier *h, int32_t l, double *X);
 void     orc_level_scores(const orc_hier *h, int32_t l, double *aff, double *q, double *score);
 void     orc_level_agg(const orc_hier *h, int32_t l, int32_t *agg, int32_t *state, uint8_t *hub);
+/* the eliminated set of a graph (Sec. 3.2, reading R20) for the sweep key `key`:
+ * cidx[u] = rank of u among the kept nodes, -1 for u in F; returns |F| */
+int64_t  orc_elim_set(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key, int32_t *cidx);
 /* level l followed by an elimination level: cidx[u] = coarse index of u, or -1 for u in F */
 void     orc_level_elim(const orc_hier *h, int32_t l, int32_t *cidx);
 

@@ -79,6 +79,10 @@ static int64_t cycle_bytes(lamg_ctx *h, int wb) {
         const double res = sw + (double)V.n * wb;
         const double rst = (double)V.n * (wb + 4) + (double)h->lv[l + 1].n * 2 * wb;
         const double pro = (double)V.n * (4 + 2 * wb);
+        if (V.elim) {   // no sweeps; restriction and back-substitution are one CSR pass together
+            total += steps[l] * (res + sw + (double)h->lv[l + 1].n * 2 * wb + pro);
+            continue;
+        }
         total += steps[l] * ((h->opt.nu1 + h->opt.nu2) * sw + res + rst + pro);
     }
     const SolveLevel &C = h->lv[L - 1];
@@ -122,6 +126,8 @@ void lamg_default_options(lamg_options *o) {
     o->project_rhs = 0;
     o->mu_adaptive = 1.0;
     o->gamma_coarse_max = 2.0;
+    o->elim = 0;
+    o->elim_min_frac = 0.1;
 }
 
 const char *lamg_last_error(void) { return g_last_error.c_str(); }
@@ -278,6 +284,8 @@ lamg_status lamg_level_info(lamg_handle h, int32_t level, int64_t *info) {
         std::memcpy(&info[11], &S.tv_ratio, 8);
         info[12] = S.jp_rounds;
         info[13] = h->lv.empty() ? 0 : h->lv[level].dense;
+        info[14] = S.elim;
+        info[15] = S.nF;
     });
 }
 
@@ -308,6 +316,7 @@ lamg_status lamg_level_copy(lamg_handle h, int32_t level, int32_t field, void *d
             case 8: src = S.aff.get(); need = S.aff.bytes(); break;
             case 9: src = S.q.get(); need = S.q.bytes(); break;
             case 10: src = S.score.get(); need = S.score.bytes(); break;
+            case 11: src = S.cidx.get(); need = S.cidx.bytes(); break;
             default: break;
         }
         const bool empty_ok = (field == 1 || field == 2) && S.nnz == 0;

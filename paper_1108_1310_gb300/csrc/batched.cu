@@ -176,6 +176,37 @@ __device__ __forceinline__ void restrict_row4(int32_t J, int g, const MKLevel<T>
     }
 }
 
+// kept row i of a level followed by elimination (Sec. 3.2), 4 columns:
+// b^c = r_i + sum over its eliminated neighbours f of w_if r_f / a_ff; x^c = 0
+template <int M, class T>
+__device__ __forceinline__ void elim_restrict_row4(int32_t i, int g, const MKLevel<T> &L, const MKLevel<T> &C,
+                                                   int ld) {
+    const int32_t e = L.rp[i + 1];
+    const int st = sstride<M>();
+    T v[4];
+    zero4(v);
+    for (int32_t j = L.rp[i] + slane<M>(); j < e; j += st) {
+        const int32_t f = L.col[j];
+        if (L.ecx[f] >= 0) continue;
+        const T wj = L.w[j], d = L.ed[f];
+        T rv[4];
+        ld4(L.r + (int64_t)f * ld + 4 * g, rv);
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[q] += wj * rv[q] / d;
+    }
+    reduce_n<M, T, 4>(v);
+    if (slane<M>() == 0) {
+        const int32_t c = L.ecx[i];
+        T rv[4], z[4];
+        ld4(L.r + (int64_t)i * ld + 4 * g, rv);
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[q] += rv[q];
+        zero4(z);
+        st4(C.b + (int64_t)c * ld + 4 * g, v);
+        st4(C.x + (int64_t)c * ld + 4 * g, z);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // per-column reductions.  With the grid-stride item index q = tid + k * nthr
 // and nthr a multiple of G, a thread always sees the same group g = tid % G.
@@ -266,6 +297,76 @@ __device__ __forceinline__ void residual4(const MRArgs<U> &a, const MKLevel<T> &
         resid_row4<M_BLK, T>(L.brows[k >> lg], (int)(k & (G - 1)), L, b, x, r, xs, rs, ld);
 }
 
+// the elimination ops of the batched engine, kept out of line so that their
+// registers do not weigh on the rest of the op switch
+template <class T>
+__device__ __noinline__ void exec_elim4(const MRArgs<T> &a, const Op &op, int bid, int nb) {
+    const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
+    const int G = a.groups, lg = a.lg, ld = a.ld;
+    const MKLevel<T> &L = a.lv[op.level];
+    const int64_t items = (int64_t)L.n * G;
+    switch (op.type) {
+        case OP_ELIM_RESTRICT: {
+            // the eliminated rows have degree <= 4 (thread tier); warp/block-tier rows are kept rows
+            const MKLevel<T> &C = a.lv[op.level + 1];
+            for (int64_t q = tid; q < items; q += nthr) {
+                const int32_t i = (int32_t)(q >> lg);
+                if (L.ecx[i] < 0 || L.rp[i + 1] - L.rp[i] > kLongRow) continue;
+                elim_restrict_row4<M_THR, T>(i, (int)(q & (G - 1)), L, C, ld);
+            }
+            const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+            for (int64_t k = wid; k < (int64_t)L.nw * G; k += nwarp) {
+                const int32_t i = L.wrows[k >> lg];
+                if (L.ecx[i] >= 0) elim_restrict_row4<M_WARP, T>(i, (int)(k & (G - 1)), L, C, ld);
+            }
+            for (int64_t k = bid; k < (int64_t)L.nb * G; k += nb) {
+                const int32_t i = L.brows[k >> lg];
+                if (L.ecx[i] >= 0) elim_restrict_row4<M_BLK, T>(i, (int)(k & (G - 1)), L, C, ld);
+            }
+            break;
+        }
+        case OP_ELIM_PROLONG: {
+            const MKLevel<T> &C = a.lv[op.level + 1];
+            for (int64_t q = tid; q < items; q += nthr) {
+                const int64_t i = q >> lg;
+                const int32_t c = L.ecx[i];
+                if (c < 0) continue;
+                const int gg = (int)(q & (G - 1));
+                T xv[4], cv[4];
+                ld4(L.x + i * ld + 4 * gg, xv);
+                ld4(C.x + (int64_t)c * ld + 4 * gg, cv);
+#pragma unroll
+                for (int k = 0; k < 4; k++) xv[k] += cv[k];
+                st4(L.x + i * ld + 4 * gg, xv);
+            }
+            break;
+        }
+        case OP_ELIM_BACK:
+            // exact back-substitution x_f = (b_f + sum_c w_fc x_c) / a_ff per column
+            for (int64_t q = tid; q < items; q += nthr) {
+                const int64_t i = q >> lg;
+                if (L.ecx[i] >= 0) continue;
+                const int gg = (int)(q & (G - 1));
+                T acc[4];
+                ld4(L.b + i * ld + 4 * gg, acc);
+                for (int32_t j = L.rp[i]; j < L.rp[i + 1]; j++) {
+                    const T wj = L.w[j];
+                    T xv[4];
+                    ld4(L.x + (int64_t)L.col[j] * ld + 4 * gg, xv);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) acc[k] += wj * xv[k];
+                }
+                const T d = L.ed[i];
+#pragma unroll
+                for (int k = 0; k < 4; k++) acc[k] = acc[k] / d;
+                st4(L.x + i * ld + 4 * gg, acc);
+            }
+            break;
+        default:
+            break;
+    }
+}
+
 template <class T>
 __device__ void exec_op4(const MRArgs<T> &a, MRShared &S, const Op &op, int bid, int nb) {
     const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
@@ -273,6 +374,10 @@ __device__ void exec_op4(const MRArgs<T> &a, MRShared &S, const Op &op, int bid,
     const int g = (int)(tid & (G - 1));
     const MKLevel<T> &L = a.lv[op.level];
     const int64_t items = (int64_t)L.n * G;
+    if (op.type >= OP_ELIM_RESTRICT) {
+        exec_elim4<T>(a, op, bid, nb);
+        return;
+    }
     switch (op.type) {
         case OP_SWEEP:
             sweep_colour4<T>(a, L, op.a, bid, nb);

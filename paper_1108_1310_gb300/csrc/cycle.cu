@@ -75,6 +75,25 @@ __device__ __forceinline__ void restrict_op(const MKLevel<T> &F, const MKLevel<T
     for (int64_t k = bid; k < F.nbagg; k += nb) restrict_row<M_BLK, T>(F.bagg[k], F.mptr, F.mlist, F.r, mu, C.b);
 }
 
+// kept row i of a level followed by elimination (Sec. 3.2): b^c = r_i + sum over
+// its eliminated neighbours f of w_if r_f / a_ff; x^c = 0
+template <int M, class T>
+__device__ __forceinline__ void elim_restrict_row(int32_t i, const MKLevel<T> &L, const MKLevel<T> &C) {
+    const int32_t e = L.rp[i + 1];
+    const int st = sstride<M>();
+    T acc = T(0), dummy = T(0);
+    for (int32_t j = L.rp[i] + slane<M>(); j < e; j += st) {
+        const int32_t f = L.col[j];
+        if (L.ecx[f] < 0) acc += L.w[j] * L.r[f] / L.ed[f];
+    }
+    reduce2<M>(acc, dummy);
+    if (slane<M>() == 0) {
+        const int32_t c = L.ecx[i];
+        C.b[c] = L.r[i] + acc;
+        C.x[c] = T(0);
+    }
+}
+
 // tail row i: r_i = b_i + sum of w_iv x_v over v < tt0 (outside the tail)
 template <int M, class T>
 __device__ __forceinline__ void tail_pre_row(int32_t i, const MKLevel<T> &L) {
@@ -266,6 +285,42 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             break;
         case OP_GMEAN64_APPLY:
             for (int64_t i = tid; i < a.L0.n; i += nthr) a.L0.x[i] -= a.gsum[a.gid0[i]];
+            break;
+        case OP_ELIM_RESTRICT: {
+            // the eliminated rows have degree <= 4: thread tier; warp/block-tier rows are kept rows
+            const MKLevel<T> &C = a.lv[op.level + 1];
+            for (int64_t i = tid; i < L.n; i += nthr) {
+                const int32_t ii = (int32_t)i;
+                if (L.ecx[ii] < 0 || L.rp[ii + 1] - L.rp[ii] > kLongRow) continue;
+                elim_restrict_row<M_THR, T>(ii, L, C);
+            }
+            const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+            for (int64_t k = wid; k < L.nw; k += nwarp) {
+                const int32_t ii = L.wrows[k];
+                if (L.ecx[ii] >= 0) elim_restrict_row<M_WARP, T>(ii, L, C);
+            }
+            for (int64_t k = bid; k < L.nb; k += nb) {
+                const int32_t ii = L.brows[k];
+                if (L.ecx[ii] >= 0) elim_restrict_row<M_BLK, T>(ii, L, C);
+            }
+            break;
+        }
+        case OP_ELIM_PROLONG: {
+            const MKLevel<T> &C = a.lv[op.level + 1];
+            for (int64_t i = tid; i < L.n; i += nthr) {
+                const int32_t c = L.ecx[i];
+                if (c >= 0) L.x[i] += C.x[c];
+            }
+            break;
+        }
+        case OP_ELIM_BACK:
+            // exact back-substitution x_f = (b_f + sum_c w_fc x_c) / a_ff (F is independent)
+            for (int64_t i = tid; i < L.n; i += nthr) {
+                if (L.ecx[i] >= 0) continue;
+                T acc = L.b[i];
+                for (int32_t j = L.rp[i]; j < L.rp[i + 1]; j++) acc += L.w[j] * L.x[L.col[j]];
+                L.x[i] = acc / L.ed[i];
+            }
             break;
         case OP_TAIL_PRE: {
             // r_i = b_i + sum of w_iv x_v over the neighbours v outside the tail; those
@@ -534,8 +589,28 @@ struct Builder {
         }
     }
     void visit(int l, int theta) {
-        const bool recomb = adaptive && l >= 1;
         const bool sb = level_sb(l);
+        if (h->lv[l].elim) {
+            // Sec. 3.2 / 4.2: a level above an elimination has gamma = 1 and no
+            // relaxation; the step is exact, so no recombination and no mu
+            for (int i = 0; i < theta; i++) {
+                emit(OP_RESID, l, -1, 0, sb);
+                emit(OP_ELIM_RESTRICT, l, 0, 0, sb);
+                if (l + 1 == h->L - 1) {
+                    coarsest(l + 1);
+                } else {
+                    const int32_t k = visits[l]++;
+                    const double g = h->sl[l].gamma_l;
+                    int th = (int)(std::ceil((double)(k + 1) * g) - std::ceil((double)k * g));
+                    th = th < 1 ? 1 : (th > 2 ? 2 : th);
+                    visit(l + 1, th);
+                }
+                emit(OP_ELIM_PROLONG, l, 0, 0, sb);
+                emit(OP_ELIM_BACK, l, 0, 0, sb);
+            }
+            return;
+        }
+        const bool recomb = adaptive && l >= 1;
         for (int i = 0; i < theta; i++) {
             sweeps(l, h->opt.nu1);
             emit(OP_RESID, l, recomb ? i : -1, 0, sb);
@@ -668,9 +743,9 @@ void engine_report(lamg_ctx *h) {
                                   "recomb_dots", "recomb_apply", "mean_part", "mean_apply", "ir_prep",
                                   "ir_update", "mean64_part", "mean64_apply", "res64", "norm64", "sweep_smem",
                                   "gmean_part", "gmean_apply", "gmean64_part", "gmean64_apply", "gnorm64",
-                                  "tail_pre", "tail_run"};
+                                  "tail_pre", "tail_run", "elim_restrict", "elim_prolong", "elim_back"};
     for (int l = 0; l < 128; l++)
-        for (int ty = 0; ty < 25; ty++)
+        for (int ty = 0; ty < (int)(sizeof(names) / sizeof(names[0])); ty++)
             for (int sb = 0; sb < 2; sb++) {
                 const int key = (l * 32 + ty) * 2 + sb;
                 if (t[2 * key + 1])

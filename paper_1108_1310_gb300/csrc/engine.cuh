@@ -26,6 +26,9 @@ struct MKLevel {
     int32_t tt0, tn, tnc, tnnz, tmaxq;
     const int32_t *trp, *tcol, *tcb, *trq;
     const T *tw, *tdeg;
+    // next level is this level's Schur complement (Sec. 3.2)
+    const int32_t *ecx;   // permuted coarse id, -1 for an eliminated row
+    const T *ed;          // a_ii of the eliminated rows
 };
 
 enum : int32_t {
@@ -55,6 +58,10 @@ enum : int32_t {
     OP_GNORM64,       // gnorm[g] = ||r64 on graph g||^2
     OP_TAIL_PRE,      // tail rows: r_i = b_i + sum over neighbours outside the tail (grid)
     OP_TAIL_RUN,      // tail colours in order from shared memory (single block)
+    // a level followed by elimination (Sec. 3.2): no relaxation, gamma = 1
+    OP_ELIM_RESTRICT, // b^c_c = r_c + sum over eliminated f of w_cf r_f / a_ff, x^c = 0
+    OP_ELIM_PROLONG,  // x_c += x^c_c on the kept rows
+    OP_ELIM_BACK,     // x_f = (b_f + sum_c w_fc x_c) / a_ff on the eliminated rows
 };
 
 constexpr int kEngSmem = 200 * 1024;  // dynamic shared memory of the engine block
@@ -255,10 +262,13 @@ inline MKLevel<T> describe(lamg_ctx *h, int l, LevelVecs<T> &v, const T *w) {
     if constexpr (sizeof(T) == 8) {
         d.tw = (const T *)V.tw64.get();
         d.tdeg = (const T *)V.tdeg64.get();
+        d.ed = (const T *)V.ed64.get();
     } else {
         d.tw = (const T *)V.tw32.get();
         d.tdeg = (const T *)V.tdeg32.get();
+        d.ed = (const T *)V.ed32.get();
     }
+    d.ecx = V.ecx.get();
     return d;
 }
 

@@ -111,6 +111,10 @@ struct SetupLevel {
     int32_t K = 0, nc = 0, rounds = 0, sel_round = 0;
     int32_t coarsest = 0, stop_reason = 0;
     double alpha = 0.0, gamma_l = 0.0, tv_ratio = 0.0;
+    // low-degree elimination (Sec. 3.2): the next level is the Schur complement on C
+    int32_t elim = 0;
+    int64_t nF = 0;
+    DBuf<int32_t> cidx;            // coarse index of each C node, -1 for F nodes
 };
 
 // Solve-phase layout of one level: rows permuted so that each colour is a
@@ -146,6 +150,11 @@ struct SolveLevel {
     int32_t tmaxq = 0;             // most chunks in one tail colour
     DBuf<double> tw64, tdeg64;     // weights and full weighted degrees of tail rows
     DBuf<float> tw32, tdeg32;
+    // transfer to a Schur-complement next level (Sec. 3.2) instead of pagg/mlist
+    int32_t elim = 0;
+    DBuf<int32_t> ecx;             // permuted row -> permuted coarse id, -1 for eliminated rows
+    DBuf<double> ed64;             // a_ii of each row (used for the eliminated rows)
+    DBuf<float> ed32;
     // coarsest level
     int32_t dense = 0;
     DBuf<double> minv;             // (A + 11^T/n)^-1, n x n, if dense
@@ -290,6 +299,13 @@ struct Tmp {
     Tmp &operator=(const Tmp &) = delete;
     T *get() const { return p; }
 };
+
+// true when the hierarchy has a level followed by elimination (Sec. 3.2)
+inline bool has_elim(const lamg_ctx *h) {
+    for (int l = 0; l + 1 < h->L; l++)
+        if (h->sl[l].elim) return true;
+    return false;
+}
 
 template <class T>
 inline T read_scalar(const T *dptr, cudaStream_t s) {

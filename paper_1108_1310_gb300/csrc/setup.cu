@@ -68,6 +68,10 @@ static uint64_t colour_key(uint64_t seed, int level) {
 static uint64_t tv_key(uint64_t seed, int level) {
     return splitmix64(splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 2)));
 }
+// elimination sweep order: the colour key's form with the top bit set
+static uint64_t elim_key(uint64_t seed, int level) {
+    return splitmix64(splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 1)) ^ (1ULL << 63));
+}
 
 // ---------------------------------------------------------------------------
 // Tier helpers
@@ -1245,6 +1249,113 @@ __global__ void k_gal_csr(int64_t E, const uint64_t *__restrict__ key2, const do
 }
 
 // ---------------------------------------------------------------------------
+// Low-degree elimination (Sec. 3.2).  F: one sweep through the nodes in
+// decreasing priority splitmix64(key + u) (ties: lower index); an eligible node
+// of degree 1..4 joins F and its neighbours become ineligible.  Equivalently, a
+// candidate is in F iff none of its higher-priority candidate neighbours is;
+// rounds decide every candidate whose higher-priority candidate neighbours are
+// all decided (the states only move forward, so a stale read only delays a
+// decision, and the result is the sweep's).
+// ---------------------------------------------------------------------------
+
+enum : int32_t { EL_UND = 0, EL_IN = 1, EL_OUT = 2, EL_NONE = 3 };
+
+__global__ void k_elim_init(int32_t n, const int32_t *__restrict__ rp, uint64_t key, uint64_t *__restrict__ prio,
+                            int32_t *__restrict__ state) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int32_t d = rp[u + 1] - rp[u];
+    state[u] = (d >= 1 && d <= 4) ? EL_UND : EL_NONE;
+    prio[u] = splitmix64(key + (uint64_t)u);
+}
+
+__global__ void k_elim_round(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const uint64_t *__restrict__ prio, int32_t *state, int32_t *left) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n || ((volatile int32_t *)state)[u] != EL_UND) return;
+    const uint64_t pu = prio[u];
+    bool wait = false, out = false;
+    for (int32_t e = rp[u]; e < rp[u + 1]; e++) {   // at most 4 entries
+        const int32_t v = col[e];
+        const int32_t sv = ((volatile int32_t *)state)[v];
+        if (sv != EL_UND && sv != EL_IN) continue;
+        const uint64_t pv = prio[v];
+        if (pv > pu || (pv == pu && v < u)) {
+            if (sv == EL_IN) out = true;
+            else wait = true;
+        }
+    }
+    if (out) state[u] = EL_OUT;
+    else if (!wait) state[u] = EL_IN;
+    else atomicAdd(left, 1);
+}
+
+__global__ void k_elim_cflag(int32_t n, const int32_t *__restrict__ state, int32_t *__restrict__ f) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) f[u] = state[u] == EL_IN ? 0 : 1;
+    if (u == n) f[n] = 0;
+}
+
+__global__ void k_elim_cidx(int32_t n, const int32_t *__restrict__ state, const int32_t *__restrict__ pos,
+                            int32_t *__restrict__ cidx) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) cidx[u] = state[u] == EL_IN ? -1 : pos[u];
+}
+
+// Schur complement on C (Eq. (3.1)); A_FF is diagonal, so for c1 < c2
+// W^c = w_{c1 c2} + sum over f in F adjacent to both of (w_{f c1} w_{f c2}) / a_ff.
+// Terms: the direct C-C entries (c1 < c2) in CSR order, then every f's
+// neighbour pairs in increasing f; a stable sort by (c1, c2) keeps, within one
+// pair, the direct term first and the fill terms by increasing f, the order
+// the canonical sum takes (bit-identical to the oracle).  The sums are then
+// mirrored into the coarse CSR exactly as in the Galerkin step.
+__global__ void k_elim_dflag(int64_t nnz, const int32_t *__restrict__ erow, const int32_t *__restrict__ col,
+                             const int32_t *__restrict__ cidx, uint8_t *__restrict__ f) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nnz) return;
+    const int32_t u = erow[j], v = col[j];
+    f[j] = (cidx[u] >= 0 && cidx[v] >= 0 && u < v) ? 1 : 0;
+}
+
+__global__ void k_elim_npairs(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ cidx,
+                              int32_t *__restrict__ cnt) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) {
+        const int32_t d = rp[u + 1] - rp[u];
+        cnt[u] = cidx[u] < 0 ? d * (d - 1) / 2 : 0;
+    }
+    if (u == n) cnt[n] = 0;
+}
+
+__global__ void k_elim_fill(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const double *__restrict__ w, const int32_t *__restrict__ cidx,
+                            const double *__restrict__ diag, const int32_t *__restrict__ off, uint64_t nc,
+                            uint64_t *__restrict__ key, double *__restrict__ val) {
+    const int32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n || cidx[f] >= 0) return;
+    int64_t o = off[f];
+    const int32_t s = rp[f], e = rp[f + 1];
+    for (int32_t i = s; i < e; i++)
+        for (int32_t j = i + 1; j < e; j++) {
+            const uint64_t a = (uint64_t)cidx[col[i]], b = (uint64_t)cidx[col[j]];
+            key[o] = a < b ? a * nc + b : b * nc + a;
+            val[o] = __ddiv_rn(__dmul_rn(w[i], w[j]), diag[f]);
+            o++;
+        }
+}
+
+__global__ void k_elim_dkeys(int64_t M, const int32_t *__restrict__ idx, const int32_t *__restrict__ erow,
+                             const int32_t *__restrict__ col, const double *__restrict__ w,
+                             const int32_t *__restrict__ cidx, uint64_t nc, uint64_t *__restrict__ key,
+                             double *__restrict__ val) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int32_t j = idx[i];
+    key[i] = (uint64_t)cidx[erow[j]] * nc + (uint64_t)cidx[col[j]];
+    val[i] = w[j];
+}
+
+// ---------------------------------------------------------------------------
 // Driver
 // ---------------------------------------------------------------------------
 
@@ -1264,54 +1375,59 @@ static int coop_grid(const void *kernel, const char *what) {
     return sms;
 }
 
-static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s) {
+// The JP colouring of a level that relaxes, and the (colour, tier, id) order of
+// its nodes.  A level followed by elimination never relaxes (nu = 0, Sec. 4.2):
+// it gets one colour, 0, and only the order.
+static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s, bool relaxes = true) {
     const int32_t n = L.n;
     L.colour.alloc(n);
-    k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, -1);
+    k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, relaxes ? -1 : 0);
     LAMG_CHECK_LAUNCH();
-    const uint64_t key = colour_key(h->opt.seed, level);
-    PhaseTimer ct(s);
-    ct.level = level;
     int32_t batch_rounds = 0;
     const int32_t fin_rounds = 0;
-    {
-    // wait counts, the first frontier, then all rounds in one cooperative launch
-    Tmp<int32_t> deg(n, s), wait(n, s);
-    Tmp<uint64_t> hsh(n, s);
-    k_jp_prio<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), key, deg.get(), hsh.get());
-    LAMG_CHECK_LAUNCH();
-    LAUNCH3(k_jp_wait, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
-            deg.get(), hsh.get(), wait.get());
-    const int64_t cap = n;
-    Tmp<int32_t> lst(6 * (size_t)cap, s), fcnt(6, s), out(1, s), err(1, s);
-    Tmp<unsigned int> bar(2, s);
-    int32_t c6[6] = {0, 0, 0, 0, 0, 0};
-    {
-        Tmp<uint8_t> f(n, s);
-        for (int t = 0; t < 3; t++) {
-            k_jp_ready<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), n, t, wait.get(), f.get());
-            LAMG_CHECK_LAUNCH();
-            c6[t] = (int32_t)compact_indices(f.get(), lst.get() + t * cap, n, s);
+    if (relaxes) {
+        const uint64_t key = colour_key(h->opt.seed, level);
+        PhaseTimer ct(s);
+        ct.level = level;
+        {
+        // wait counts, the first frontier, then all rounds in one cooperative launch
+        Tmp<int32_t> deg(n, s), wait(n, s);
+        Tmp<uint64_t> hsh(n, s);
+        k_jp_prio<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), key, deg.get(), hsh.get());
+        LAMG_CHECK_LAUNCH();
+        LAUNCH3(k_jp_wait, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
+                deg.get(), hsh.get(), wait.get());
+        const int64_t cap = n;
+        Tmp<int32_t> lst(6 * (size_t)cap, s), fcnt(6, s), out(1, s), err(1, s);
+        Tmp<unsigned int> bar(2, s);
+        int32_t c6[6] = {0, 0, 0, 0, 0, 0};
+        {
+            Tmp<uint8_t> f(n, s);
+            for (int t = 0; t < 3; t++) {
+                k_jp_ready<<<ceil_div(n, 256), 256, 0, s>>>(L.rp.get(), n, t, wait.get(), f.get());
+                LAMG_CHECK_LAUNCH();
+                c6[t] = (int32_t)compact_indices(f.get(), lst.get() + t * cap, n, s);
+            }
         }
-    }
-    LAMG_CUDA(cudaMemcpyAsync(fcnt.get(), c6, sizeof(c6), cudaMemcpyHostToDevice, s));
-    LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
-    LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
-    const int grid = coop_grid((const void *)k_jp_dag, "colouring kernel");
-    {
-        const int32_t *rpp = L.rp.get(), *colp = L.col.get(), *dp = deg.get();
-        const uint64_t *hp = hsh.get();
-        int32_t *wp = wait.get(), *colour = L.colour.get(), *lp = lst.get(), *cp = fcnt.get(), *op = out.get(),
-                *ep = err.get();
-        int64_t capv = cap;
-        unsigned int *bp = bar.get();
-        void *args[] = {&rpp, &colp, &dp, &hp, &wp, &colour, &lp, &capv, &cp, &op, &bp, &ep};
-        LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_jp_dag, dim3(grid), dim3(kBlk), args, 0, s));
-        note_launch();
-    }
-    LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "colouring: grid barrier timed out");
-    batch_rounds = read_scalar(out.get(), s);
-    ct.mark("jp_rounds");
+        LAMG_CUDA(cudaMemcpyAsync(fcnt.get(), c6, sizeof(c6), cudaMemcpyHostToDevice, s));
+        LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
+        LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
+        const int grid = coop_grid((const void *)k_jp_dag, "colouring kernel");
+        {
+            const int32_t *rpp = L.rp.get(), *colp = L.col.get(), *dp = deg.get();
+            const uint64_t *hp = hsh.get();
+            int32_t *wp = wait.get(), *colour = L.colour.get(), *lp = lst.get(), *cp = fcnt.get(), *op = out.get(),
+                    *ep = err.get();
+            int64_t capv = cap;
+            unsigned int *bp = bar.get();
+            void *args[] = {&rpp, &colp, &dp, &hp, &wp, &colour, &lp, &capv, &cp, &op, &bp, &ep};
+            LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_jp_dag, dim3(grid), dim3(kBlk), args, 0, s));
+            note_launch();
+        }
+        LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "colouring: grid barrier timed out");
+        batch_rounds = read_scalar(out.get(), s);
+        ct.mark("jp_rounds");
+        }
     }
     L.jp_rounds = batch_rounds + fin_rounds;
     L.ncolours = reduce_max_i32(L.colour.get(), n, s) + 1;
@@ -1552,6 +1668,102 @@ static void aggregate_level(lamg_ctx *h, SetupLevel &L, const Tiers &T, const do
     L.nc = nseeds + (nd > 0 ? 1 : 0);
 }
 
+// F of level L; fills L.cidx and returns |F|
+static int64_t select_elim(lamg_ctx *h, SetupLevel &L, int level, cudaStream_t s) {
+    const int32_t n = L.n;
+    Tmp<uint64_t> prio(n, s);
+    Tmp<int32_t> state(n, s), left(1, s), f(n + 1, s), pos(n + 1, s);
+    k_elim_init<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), elim_key(h->opt.seed, level), prio.get(), state.get());
+    LAMG_CHECK_LAUNCH();
+    for (int64_t round = 0;; round++) {
+        // every round decides at least the highest-priority undecided candidate
+        LAMG_REQUIRE(round <= (int64_t)n, LAMG_ERR_CUDA, "elimination: rounds did not converge");
+        LAMG_CUDA(cudaMemsetAsync(left.get(), 0, sizeof(int32_t), s));
+        k_elim_round<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), L.col.get(), prio.get(), state.get(), left.get());
+        LAMG_CHECK_LAUNCH();
+        if (read_scalar(left.get(), s) == 0) break;
+    }
+    k_elim_cflag<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, state.get(), f.get());
+    LAMG_CHECK_LAUNCH();
+    exclusive_scan_i32(f.get(), pos.get(), n + 1, s);
+    L.cidx.alloc(n);
+    k_elim_cidx<<<ceil_div(n, 256), 256, 0, s>>>(n, state.get(), pos.get(), L.cidx.get());
+    LAMG_CHECK_LAUNCH();
+    const int32_t nc = read_scalar(pos.get() + n, s);
+    return (int64_t)n - nc;
+}
+
+static void eliminate_level(SetupLevel &F, SetupLevel &C, const int32_t *erow, const double *diag, cudaStream_t s) {
+    const int64_t nnz = F.nnz;
+    const int32_t n = F.n;
+    const uint64_t nc = (uint64_t)(F.n - F.nF);
+    C.n = (int32_t)nc;
+    // direct terms
+    Tmp<uint8_t> f(nnz, s);
+    Tmp<int32_t> idx(nnz, s);
+    if (nnz) {
+        k_elim_dflag<<<ceil_div(nnz, 256), 256, 0, s>>>(nnz, erow, F.col.get(), F.cidx.get(), f.get());
+        LAMG_CHECK_LAUNCH();
+    }
+    const int64_t M1 = compact_indices(f.get(), idx.get(), nnz, s);
+    // fill terms: d(d-1)/2 per eliminated node, d <= 4
+    Tmp<int32_t> cnt(n + 1, s), off(n + 1, s);
+    k_elim_npairs<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, F.rp.get(), F.cidx.get(), cnt.get());
+    LAMG_CHECK_LAUNCH();
+    exclusive_scan_i32(cnt.get(), off.get(), n + 1, s);
+    const int64_t M2 = read_scalar(off.get() + n, s);
+    const int64_t M = M1 + M2;
+    Tmp<uint64_t> key(M, s), ktmp(M, s);
+    Tmp<double> val(M, s), vtmp(M, s);
+    if (M1) {
+        k_elim_dkeys<<<ceil_div(M1, 256), 256, 0, s>>>(M1, idx.get(), erow, F.col.get(), F.w.get(), F.cidx.get(),
+                                                       nc, key.get(), val.get());
+        LAMG_CHECK_LAUNCH();
+    }
+    if (M2) {
+        k_elim_fill<<<ceil_div(n, 256), 256, 0, s>>>(n, F.rp.get(), F.col.get(), F.w.get(), F.cidx.get(), diag,
+                                                     off.get(), nc, key.get() + M1, val.get() + M1);
+        LAMG_CHECK_LAUNCH();
+    }
+    radix_sort_pairs<uint64_t, double>(key.get(), val.get(), ktmp.get(), vtmp.get(), M, bits_for(nc * nc - 1), s);
+    Tmp<uint8_t> hf(M, s);
+    Tmp<int32_t> start(M, s);
+    if (M) {
+        k_seg_heads<<<ceil_div(M, 256), 256, 0, s>>>(M, key.get(), hf.get());
+        LAMG_CHECK_LAUNCH();
+    }
+    const int64_t P = compact_indices(hf.get(), start.get(), M, s);
+    Tmp<double> W(P, s);
+    if (P) {
+        Tmp<int32_t> sp(P + 1, s);
+        k_seg_ptr<<<ceil_div(P + 1, 256), 256, 0, s>>>(P, start.get(), M, sp.get());
+        LAMG_CHECK_LAUNCH();
+        Tiers ST((int32_t)P, s);
+        build_tiers(sp.get(), (int32_t)P, ST, s);
+        LAUNCH3(k_seg_sum, (int32_t)P, (const int32_t *)nullptr, ST.w.get(), ST.nw, ST.b.get(), ST.nb, s, sp.get(),
+                val.get(), W.get());
+    }
+    const int64_t E = 2 * P;
+    Tmp<uint64_t> key2(E, s), k2tmp(E, s);
+    Tmp<double> val2(E, s), v2tmp(E, s);
+    if (P) {
+        k_gal_dir<<<ceil_div(P, 256), 256, 0, s>>>(P, start.get(), key.get(), W.get(), nc, key2.get(), val2.get());
+        LAMG_CHECK_LAUNCH();
+    }
+    radix_sort_pairs<uint64_t, double>(key2.get(), val2.get(), k2tmp.get(), v2tmp.get(), E, bits_for(nc * nc - 1), s);
+    C.nnz = E;
+    C.rp.alloc(C.n + 1);
+    C.col.alloc(E);
+    C.w.alloc(E);
+    Tmp<int32_t> rowcnt(C.n + 1, s);
+    LAMG_CUDA(cudaMemsetAsync(rowcnt.get(), 0, sizeof(int32_t) * (C.n + 1), s));
+    if (E) {
+        k_gal_csr<<<ceil_div(E, 256), 256, 0, s>>>(E, key2.get(), val2.get(), nc, C.col.get(), C.w.get(), rowcnt.get());
+        LAMG_CHECK_LAUNCH();
+    }
+    exclusive_scan_i32(rowcnt.get(), C.rp.get(), C.n + 1, s);
+}
+
 static void galerkin_level(SetupLevel &F, SetupLevel &C, const int32_t *erow, cudaStream_t s) {
     const int64_t nnz = F.nnz;
     const uint64_t nc = (uint64_t)F.nc;
@@ -1617,6 +1829,7 @@ static void galerkin_level(SetupLevel &F, SetupLevel &C, const int32_t *erow, cu
 static void cycle_indices(lamg_ctx *h) {
     const double m1 = (double)h->sl[0].nnz / 2.0;
     for (int l = 0; l + 1 < h->L; l++) {
+        if (h->sl[l].elim) { h->sl[l].gamma_l = 1.0; continue; }   // Sec. 4.2: gamma = 1 above an elimination
         const double ml = (double)h->sl[l].nnz / 2.0, mn = (double)h->sl[l + 1].nnz / 2.0;
         double g = mn > 0.0 ? 0.7 * ml / mn : 2.0;
         const double gmax = ml > 0.1 * m1 ? h->opt.gamma : h->opt.gamma_coarse_max;
@@ -1656,6 +1869,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
     const int maxl = std::min(o.max_levels, 128);
     PhaseTimer pt(s);
     pt.mark("ingest");
+    int nagg = 0;   // aggregation levels so far (the TV count grows with them)
     for (int l = 0;; l++) {
         SetupLevel &L = h->sl[l];
         const int32_t nl = L.n;
@@ -1668,14 +1882,33 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         LAUNCH3(k_node_stats, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
                 L.col.get(), L.w.get(), o.hub_factor, diag.get(), maxw.get(), L.hub.get());
         pt.mark("stats");
-        colour_level(h, L, l, T, s);
-        pt.mark("colour");
         if (nl < o.n_coarsest || l + 1 >= maxl) {
+            colour_level(h, L, l, T, s);
+            pt.mark("colour");
             L.coarsest = 1;
             L.stop_reason = nl < o.n_coarsest ? 1 : 4;
             break;
         }
-        int K = o.k_finest + o.k_step * l;
+        if (o.elim) {   // low-degree elimination before aggregating (Sec. 3.2)
+            L.nF = select_elim(h, L, l, s);
+            if (L.nF >= 1 && (double)L.nF >= o.elim_min_frac * (double)nl) {
+                colour_level(h, L, l, T, s, false);   // no relaxation on this level: one colour
+                L.elim = 1;
+                L.nc = (int32_t)(nl - L.nF);
+                Tmp<int32_t> erow(L.nnz, s);
+                LAUNCH3(k_entry_rows, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s,
+                        L.rp.get(), erow.get());
+                h->sl.emplace_back();   // capacity reserved: references stay valid
+                eliminate_level(h->sl[l], h->sl[l + 1], erow.get(), diag.get(), s);
+                pt.mark("eliminate");
+                continue;
+            }
+            L.nF = 0;
+            L.cidx.release();
+        }
+        colour_level(h, L, l, T, s);
+        pt.mark("colour");
+        int K = o.k_finest + o.k_step * nagg;
         if (K > o.k_max) K = o.k_max;
         if (K > 16) K = 16;
         if (K < 1) K = 1;
@@ -1726,6 +1959,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         h->sl.emplace_back();
         galerkin_level(h->sl[l], h->sl[l + 1], erow.get(), s);
         pt.mark("galerkin");
+        nagg++;
     }
     cycle_indices(h);
     LAMG_CUDA(cudaStreamSynchronize(s));

@@ -254,6 +254,25 @@ static void build_tail(SolveLevel &V, int ncol, cudaStream_t s) {
     LAMG_CUDA(cudaStreamSynchronize(s));
 }
 
+// A level followed by elimination (Sec. 3.2): the permuted coarse id of each
+// permuted row (-1 for an eliminated row) and, for the eliminated rows, a_ii
+// summed over the row in entry order (degree <= 4).
+__global__ void k_elim_layout(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ cidx,
+                              const int32_t *__restrict__ iperm_c, const int32_t *__restrict__ rp,
+                              const double *__restrict__ w64, const float *__restrict__ w32,
+                              int32_t *__restrict__ ecx, double *__restrict__ ed64, float *__restrict__ ed32) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t c = cidx[perm[i]];
+    ecx[i] = c < 0 ? -1 : iperm_c[c];
+    double d = 0.0;
+    float d32 = 0.f;
+    if (c < 0)
+        for (int32_t j = rp[i]; j < rp[i + 1]; j++) { d += w64[j]; d32 += w32[j]; }
+    ed64[i] = d;
+    ed32[i] = d32;
+}
+
 void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
     const int L = h->L;
     h->lv.clear();
@@ -342,6 +361,17 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         SetupLevel &S = h->sl[l];
         SolveLevel &V = h->lv[l];
         const int32_t n = S.n, nc = S.nc;
+        if (S.elim) {
+            V.elim = 1;
+            V.ecx.alloc(n);
+            V.ed64.alloc(n);
+            V.ed32.alloc(n);
+            k_elim_layout<<<ceil_div(n, 256), 256, 0, s>>>(n, V.perm.get(), S.cidx.get(), iperm[l + 1].get(),
+                                                          V.rp.get(), V.w64.get(), V.w32.get(), V.ecx.get(),
+                                                          V.ed64.get(), V.ed32.get());
+            LAMG_CHECK_LAUNCH();
+            continue;
+        }
         V.pagg.alloc(n);
         V.mptr.alloc(nc + 1);
         V.mlist.alloc(n);

@@ -32,7 +32,7 @@ LAMG_FP64 = 0
 LAMG_FP32_IR = 1
 
 FIELD = {"row_ptr": 0, "col": 1, "w": 2, "colour": 3, "agg": 4, "state": 5, "hub": 6, "tv": 7,
-         "affinity": 8, "q": 9, "score": 10}
+         "affinity": 8, "q": 9, "score": 10, "cidx": 11}
 
 
 class lamg_options(C.Structure):
@@ -46,7 +46,7 @@ class lamg_options(C.Structure):
                 ("mu_flat", C.c_double), ("seed", C.c_uint64), ("adaptive", C.c_int32),
                 ("max_cycles", C.c_int32), ("ir_inner", C.c_int32), ("validate", C.c_int32),
                 ("keep_setup_data", C.c_int32), ("project_rhs", C.c_int32), ("mu_adaptive", C.c_double),
-                ("gamma_coarse_max", C.c_double)]
+                ("gamma_coarse_max", C.c_double), ("elim", C.c_int32), ("elim_min_frac", C.c_double)]
 
 
 class lamg_stats(C.Structure):
@@ -255,7 +255,7 @@ def lamg_level_info(h, level: int) -> dict:
     return dict(n=int(a[0]), nnz=int(a[1]), ncolours=int(a[2]), K=int(a[3]), nc=int(a[4]),
                 rounds=int(a[5]), sel_round=int(a[6]), coarsest=bool(a[7]), stop_reason=int(a[8]),
                 alpha=float(f[9]), gamma=float(f[10]), tv_ratio=float(f[11]), jp_rounds=int(a[12]),
-                dense=bool(a[13]))
+                dense=bool(a[13]), elim=bool(a[14]), nF=int(a[15]))
 
 
 def lamg_level_copy(h, level: int, field: str) -> np.ndarray:
@@ -265,7 +265,7 @@ def lamg_level_copy(h, level: int, field: str) -> np.ndarray:
         "row_ptr": (n + 1, np.int64), "col": (nnz, np.int32), "w": (nnz, np.float64),
         "colour": (n, np.int32), "agg": (n, np.int32), "state": (n, np.int32), "hub": (n, np.uint8),
         "tv": (n * K, np.float64), "affinity": (nnz, np.float64), "q": (nnz, np.float64),
-        "score": (nnz, np.float64)}[field]
+        "score": (nnz, np.float64), "cidx": (n, np.int32)}[field]
     out = np.zeros(shape, dtype=dtype)
     _check(_lib.lamg_level_copy(h, int(level), FIELD[field], _ptr(out), out.nbytes), "lamg_level_copy")
     return out.reshape(n, K) if field == "tv" else out

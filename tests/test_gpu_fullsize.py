@@ -82,3 +82,81 @@ def test_fullsize_levels_against_oracle_pieces(big):
         wc = L.lamg_level_copy(s.h, l + 1, "w")
         assert np.array_equal(Wc.indptr.astype(np.int64), rpc) and np.array_equal(Wc.indices, colc), l
         assert np.max(np.abs(Wc.data - wc)) <= 1e-12 * np.max(np.abs(wc)), l
+
+
+# --------------------------------------------------------------------------- #
+# The same workload with low-degree elimination levels (Sec. 3.2, elim = 1)
+# --------------------------------------------------------------------------- #
+
+@pytest.fixture(scope="module")
+def big_elim():
+    from paper_1108_1310_gb300 import build
+    build.build()
+    from paper_1108_1310_gb300 import lamg as L
+    g = W.config_graph("chung_lu1m")
+    s = L.Solver.from_graph(g, w_dtype=torch.float32, keep_setup_data=1, validate=1, max_cycles=2000, elim=1)
+    yield L, g, s
+    s.close()
+
+
+def _elim_key(seed, l):
+    return oracle.splitmix64(oracle.splitmix64(seed) ^ ((2 * l + 1) << 32) ^ (1 << 63))
+
+
+def test_fullsize_elim_levels_against_oracle_pieces(big_elim):
+    L, g, s = big_elim
+    seed = oracle.default_opts().seed
+    nl = s.num_levels
+    kinds = ""
+    for l in range(nl):
+        info = s.level_info(l)
+        rp = L.lamg_level_copy(s.h, l, "row_ptr")
+        col = L.lamg_level_copy(s.h, l, "col")
+        w = L.lamg_level_copy(s.h, l, "w")
+        n = info["n"]
+        colour = L.lamg_level_copy(s.h, l, "colour")
+        if info["elim"]:   # a level followed by elimination never relaxes: one colour
+            assert not colour.any() and info["ncolours"] == 1, l
+        else:
+            assert np.array_equal(colour, oracle.colour(n, rp, col, _colour_key(seed, l))[0]), l
+        if info["coarsest"]:
+            kinds += "C"
+            continue
+        if not info["elim"]:
+            kinds += "A"
+            X = L.lamg_level_copy(s.h, l, "tv")
+            aff, q, score = oracle.edge_scores(n, rp, col, w, X)
+            assert np.array_equal(L.lamg_level_copy(s.h, l, "score").view(np.uint64), score.view(np.uint64)), l
+            continue
+        kinds += "E"
+        # the eliminated set: the oracle's sweep on this level's own graph
+        cidx, nF = oracle.elim_set(n, rp, col, _elim_key(seed, l))
+        assert np.array_equal(L.lamg_level_copy(s.h, l, "cidx"), cidx), l
+        assert info["nF"] == nF
+        # the next level: the Schur complement A_CC - A_CF A_FF^-1 A_FC (SciPy)
+        A = sp.csr_matrix((w, col, rp), shape=(n, n))
+        d = np.asarray(A.sum(axis=1)).ravel()
+        Lap = sp.diags(d) - A
+        Cs, Fs = np.flatnonzero(cidx >= 0), np.flatnonzero(cidx < 0)
+        S = (Lap[Cs][:, Cs] - Lap[Cs][:, Fs] @ sp.diags(1.0 / d[Fs]) @ Lap[Fs][:, Cs]).tocsr()
+        Wc = -S
+        Wc.setdiag(0.0)
+        Wc.eliminate_zeros()
+        Wc.sort_indices()
+        rpc = L.lamg_level_copy(s.h, l + 1, "row_ptr")
+        colc = L.lamg_level_copy(s.h, l + 1, "col")
+        wc = L.lamg_level_copy(s.h, l + 1, "w")
+        assert np.array_equal(Wc.indptr.astype(np.int64), rpc) and np.array_equal(Wc.indices, colc), l
+        assert np.max(np.abs(Wc.data - wc)) <= 1e-12 * np.max(np.abs(wc)), l
+    assert "E" in kinds, kinds
+
+
+def test_fullsize_elim_solve_residual(big_elim):
+    L, g, s = big_elim
+    b = W.zero_sum_rhs(g.n, 2)
+    x, st = s.solve(torch.tensor(b, device="cuda"), tol=1e-8, precision=L.LAMG_FP32_IR)
+    xg = x.cpu().numpy()
+    A = sp.csr_matrix((g.w, g.col, g.rp), shape=(g.n, g.n))
+    r = b - (np.asarray(A.sum(axis=1)).ravel() * xg - A @ xg)
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(b)
+    assert abs(xg.sum()) <= 1e-9 * np.abs(xg).sum()

@@ -1,7 +1,7 @@
 """Pins of the oracle's low-degree elimination (Sec. 3.2; option elim = 1).
 
-Elimination levels are an oracle option that the GPU library does not build
-yet.  Each pin checks them against something other than the oracle itself:
+Each pin checks the elimination levels against something other than the
+oracle itself:
 the dense Schur complement (numpy), the greedy independent set taken by its
 definition, the series-conductance closed form on a path, exactness on trees,
 the dense pseudo-inverse, and the paper's stated reason for elimination (grids
@@ -176,6 +176,23 @@ def test_elimination_removes_the_one_dimensional_part_of_a_grid():
                 visits *= i["gamma"]
         wpd.append(work / -math.log10(acf))
     assert wpd[1] <= 0.6 * wpd[0], wpd
+
+
+def test_standalone_elim_set_reproduces_the_hierarchy():
+    # oracle.elim_set applied to a level's own graph with that level's sweep key gives
+    # the level's eliminated set (the full-size GPU test relies on this)
+    g = W.chung_lu(5000, seed=3)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1)
+    seen = 0
+    for l in range(h.num_levels - 1):
+        if not h.info(l)["elim"]:
+            continue
+        rp, col, _ = h.csr(l)
+        key = oracle.splitmix64(oracle.splitmix64(1) ^ ((2 * l + 1) << 32) ^ (1 << 63))
+        cidx, nF = oracle.elim_set(len(rp) - 1, rp, col, key)
+        assert np.array_equal(cidx, h.elim(l)) and nF == h.info(l)["nF"]
+        seen += 1
+    assert seen >= 2
 
 
 def test_grid_acf_matches_the_paper_only_with_elimination():

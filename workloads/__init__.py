@@ -318,9 +318,12 @@ def zero_sum_rhs(n: int, seed: int, count: int | None = None) -> np.ndarray:
 
 def config_graph(name: str) -> Graph:
     """'grid64': 64x64 5-point grid; 'chung_lu1m': Chung-Lu n=1M, beta 2.5, mean degree 10;
-    'grid256': 256^3 7-point grid, weights 1/1/0.01; 'rgg2m': 2M-node RGG, mean degree 12."""
+    'grid256': 256^3 7-point grid, weights 1/1/0.01; 'rgg2m': 2M-node RGG, mean degree 12;
+    'grid1024': 1024x1024 5-point grid, unit weights (the paper's grid table size)."""
     if name == "grid64":
         return grid2d(64, 64)
+    if name == "grid1024":
+        return grid2d(1024, 1024)
     if name == "chung_lu1m":
         return chung_lu(1_000_000, 2.5, 10.0, seed=2)
     if name == "grid256":
