@@ -176,3 +176,21 @@ def test_elimination_removes_the_one_dimensional_part_of_a_grid():
                 visits *= i["gamma"]
         wpd.append(work / -math.log10(acf))
     assert wpd[1] <= 0.6 * wpd[0], wpd
+
+
+def test_grid_acf_matches_the_paper_only_with_elimination():
+    # The paper prints an ACF of .216 for the 5-point 1024^2 grid (Sec. 5, grid
+    # table), with its elimination levels.  With elimination the oracle's ACF on
+    # a 256^2 grid lies in that neighbourhood; without it, aggregation alone
+    # stalls on grids this large (asymptotic rate above .9 per cycle).
+    g = W.grid2d(256, 256)
+    b = W.zero_sum_rhs(g.n, 1)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1)
+    _, hist = h.solve(b, tol=1e-10, max_cycles=100)
+    p = len(hist) - 1
+    acf = (hist[-1] / hist[0]) ** (1.0 / p)
+    assert 0.15 <= acf <= 0.30 and p <= 25, (acf, p)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    _, hist = h.solve(b, tol=1e-10, max_cycles=40)
+    rate = (hist[-1] / hist[-11]) ** 0.1              # over the last 10 cycles
+    assert rate > 0.9, rate
