@@ -40,6 +40,7 @@ void orc_default_opts(orc_opts *o) {
     o->agg_rule = 0;           /* parallel handshake */
     o->elim = 0;               /* no elimination levels (as the library) */
     o->elim_min_frac = 0.1;    /* reading of "until |F| becomes small", Sec. 3.2 */
+    o->lgmg_nx = 0;            /* algebraic coarsening */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -867,6 +868,7 @@ static void cycle_indices(orc_hier *h) {
     double m1 = (double)h->lv[0].nnz / 2.0;
     for (int32_t l = 0; l < h->L - 1; l++) {
         if (h->lv[l].elim) { h->lv[l].gamma_l = 1.0; continue; }   /* Sec. 4.2: gamma = 1 before elimination */
+        if (h->o.lgmg_nx > 0) { h->lv[l].gamma_l = h->o.gamma; continue; }   /* Sec. 6: a standard gamma-cycle */
         double ml = (double)h->lv[l].nnz / 2.0, mn = (double)h->lv[l + 1].nnz / 2.0;
         double g = mn > 0.0 ? 0.7 * ml / mn : 2.0;
         double gmax = ml > 0.1 * m1 ? h->o.gamma : 2.0;
@@ -875,6 +877,16 @@ static void cycle_indices(orc_hier *h) {
         h->lv[l].gamma_l = g;
     }
     h->lv[h->L - 1].gamma_l = 0.0;
+}
+
+/* Lean Geometric Multigrid (Sec. 6): red-black colours of an nx x nx torus */
+static void level_prepare_rb(orc_level *L, int32_t nx) {
+    L->diag = (double *)xcalloc((size_t)L->n, sizeof(double));
+    diag_canon(L->n, L->rp, L->w, L->diag);
+    L->colour = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
+    for (int64_t u = 0; u < L->n; u++) L->colour[u] = (int32_t)(((u % nx) + (u / nx)) & 1);
+    L->ncolours = 2;
+    L->jp_rounds = 0;
 }
 
 static void level_prepare(orc_level *L, uint64_t seed, int32_t level) {
@@ -930,14 +942,30 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
     memcpy(L0->w, w, sizeof(double) * (size_t)L0->nnz);
     int32_t maxl = o->max_levels < 128 ? o->max_levels : 128;
     int32_t nagg = 0;   /* aggregation levels so far (the TV count grows with them) */
+    int32_t nxl = o->lgmg_nx;   /* Lean Geometric MG: the current grid side */
+    if (nxl > 0 && (int64_t)nxl * nxl != n) { orc_free(h); return ORC_ERR_ARG; }
     for (int32_t l = 0;; l++) {
         orc_level *L = &h->lv[l];
-        level_prepare(L, o->seed, l);
+        if (nxl > 0) level_prepare_rb(L, nxl);
+        else level_prepare(L, o->seed, l);
         h->L = l + 1;
-        if (L->n < o->n_coarsest || l + 1 >= maxl) {
+        if (L->n < o->n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
             L->stop_reason = L->n < o->n_coarsest ? 1 : 4;
             st = make_coarsest(L, o);
             break;
+        }
+        if (nxl > 0) {   /* Lean Geometric MG: 1:2 coarsening in both directions, 2x2 aggregates */
+            const int32_t nc2 = nxl / 2;
+            L->agg = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
+            L->state = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
+            L->hub = (uint8_t *)xcalloc((size_t)L->n, 1);
+            for (int64_t u = 0; u < L->n; u++)
+                L->agg[u] = (int32_t)((u / nxl) / 2 * nc2 + (u % nxl) / 2);
+            L->nc = (int64_t)nc2 * nc2;
+            L->alpha = (double)L->nc / (double)L->n;
+            galerkin(L, &h->lv[l + 1]);
+            nxl = nc2;
+            continue;
         }
         if (o->elim) {   /* low-degree elimination before aggregating, Sec. 3.2 */
             int32_t *cidx = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));

@@ -57,6 +57,10 @@ typedef struct {
                                   aggregation, Sec. 3.2 (default 0: none, as the library) */
     double   elim_min_frac;    /* an elimination round is kept only if it removes at
                                   least this fraction of the level's nodes (reading: 0.1) */
+    int32_t  lgmg_nx;          /* > 0: Lean Geometric Multigrid (Sec. 6) on an
+                                  lgmg_nx x lgmg_nx periodic 5-point grid: 2x2 aggregates
+                                  and red-black colours at every level, gamma at every
+                                  level; solve in flat mode with mu_flat = 2.  Default 0 */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;

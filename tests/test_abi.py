@@ -69,8 +69,8 @@ def test_default_options_match_the_oracle(lib):
     import oracle
     from paper_1108_1310_gb300 import lamg as L
     a, b = L.lamg_default_options(), oracle.default_opts()
-    # the sequential-scan quality reference and the elimination levels have no GPU form yet
-    oracle_only = {"agg_rule", "elim", "elim_min_frac"}
+    # oracle-only options: the sequential-scan reference, elimination, lean geometric MG
+    oracle_only = {"agg_rule", "elim", "elim_min_frac", "lgmg_nx"}
     assert (b.agg_rule, b.elim) == (0, 0)
     for f, _ in oracle.Opts._fields_:
         if f not in oracle_only:

@@ -605,3 +605,34 @@ def test_per_level_pieces_reproduce_the_hierarchy():
         assert np.array_equal(q.view(np.uint64), q2.view(np.uint64))
         assert np.array_equal(score.view(np.uint64), s2.view(np.uint64))
         assert np.array_equal(oracle.hubs(n, rp, col, w), h.agg(l)[2])
+
+
+def _per_unit_work(h, b, nu):
+    # asymptotic convergence factor per unit of work: the rate over the last 5 cycles,
+    # to the power 1/W, W = relaxation sweeps per cycle weighted by level size (the
+    # fractional cycle index of Eq. (4.1) replayed: steps_{l+1} = ceil(gamma steps_l))
+    _, hist = h.solve(b, tol=1e-10, max_cycles=80, adaptive=False)
+    acf = (hist[-1] / hist[-6]) ** 0.2
+    steps, work, n0 = 1, 0.0, h.info(0)["n"]
+    for l in range(h.num_levels - 1):
+        work += steps * nu * h.info(l)["n"] / n0
+        steps = math.ceil(steps * h.info(l)["gamma"])
+    return acf ** (1.0 / work)
+
+
+def test_lean_geometric_multigrid_rate():
+    # Sec. 6 (Lean Geometric Multigrid): on the 2-D periodic Poisson problem, 2x2
+    # aggregates, red-black GS, gamma = 1.5 and the flat correction mu = 2 (energy
+    # ratio 2 for every mode) converge at .5 per unit of work.  Without the energy
+    # correction (mu = 1) the same cycle is far slower (Sec. 3.4.3).
+    nx = 128
+    g = W.grid2d_periodic(nx)
+    b = W.zero_sum_rhs(g.n, 1)
+    nu = oracle.default_opts().nu1 + oracle.default_opts().nu2
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, lgmg_nx=nx, mu_flat=2.0, gamma=1.5)
+    assert [h.info(l)["ncolours"] for l in range(h.num_levels - 1)] == [2] * (h.num_levels - 1)
+    assert all(h.info(l + 1)["n"] * 4 == h.info(l)["n"] for l in range(h.num_levels - 1))
+    rate = _per_unit_work(h, b, nu)
+    assert 0.45 <= rate <= 0.56, rate
+    h1 = oracle.Hierarchy(g.n, g.rp, g.col, g.w, lgmg_nx=nx, mu_flat=1.0, gamma=1.5)
+    assert _per_unit_work(h1, b, nu) > 0.8

@@ -121,6 +121,16 @@ def grid2d(nx: int, ny: int, wx: float = 1.0, wy: float = 1.0) -> Graph:
                       f"grid{nx}x{ny}")
 
 
+def grid2d_periodic(nx: int) -> Graph:
+    """5-point nx x nx grid Laplacian with periodic boundary (a torus), unit
+    weights; node id = i + nx*j; nx >= 3."""
+    idx = np.arange(nx * nx).reshape(nx, nx)
+    us = [idx.ravel(), idx.ravel()]
+    vs = [np.roll(idx, -1, axis=1).ravel(), np.roll(idx, -1, axis=0).ravel()]
+    u, v = np.concatenate(us), np.concatenate(vs)
+    return from_edges(nx * nx, np.minimum(u, v), np.maximum(u, v), np.ones(u.size), f"torus{nx}")
+
+
 def grid3d(nx: int, ny: int, nz: int, wx=1.0, wy=1.0, wz=1.0) -> Graph:
     """7-point grid Laplacian with free boundary; node id = i + nx*(j + ny*k).
 
