@@ -91,6 +91,9 @@ typedef struct {
                                   uses b minus its mean instead (per graph, per column),
                                   the compatible part of b (Sec. 1), and leaves the
                                   caller's b unchanged                                    */
+    double   mu_adaptive;      /* restriction factor of the adaptive cycle (recombination,
+                                  Eq. (3.13)): 1 (default) or a mild flat correction
+                                  on top of recombination; see the oracle's figures    */
 } lamg_options;
 
 typedef struct {

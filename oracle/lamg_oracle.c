@@ -41,6 +41,7 @@ void orc_default_opts(orc_opts *o) {
     o->elim = 0;               /* no elimination levels (as the library) */
     o->elim_min_frac = 0.1;    /* reading of "until |F| becomes small", Sec. 3.2 */
     o->lgmg_nx = 0;            /* algebraic coarsening */
+    o->mu_adaptive = 1.0;      /* reading R15: recombination replaces the flat correction */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1249,7 +1250,7 @@ static void visit(solve_ctx *c, int32_t l, int theta) {
 
 static void ctx_init(solve_ctx *c, const orc_hier *h, int adaptive) {
     c->h = h; c->adaptive = adaptive;
-    c->mu = adaptive ? 1.0 : h->o.mu_flat;
+    c->mu = adaptive ? h->o.mu_adaptive : h->o.mu_flat;
     c->x = (double **)calloc((size_t)h->L, sizeof(double *));
     c->b = (double **)calloc((size_t)h->L, sizeof(double *));
     c->r = (double **)calloc((size_t)h->L, sizeof(double *));

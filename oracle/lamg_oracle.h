@@ -61,6 +61,7 @@ typedef struct {
                                   lgmg_nx x lgmg_nx periodic 5-point grid: 2x2 aggregates
                                   and red-black colours at every level, gamma at every
                                   level; solve in flat mode with mu_flat = 2.  Default 0 */
+    double   mu_adaptive;      /* restriction factor of the adaptive cycle (reading R15: 1) */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;

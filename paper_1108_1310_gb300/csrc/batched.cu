@@ -678,7 +678,7 @@ static void batch_run(lamg_ctx *h, int kind, int adaptive, cudaStream_t s) {
     while ((1 << lg) < M.groups) lg++;
     MKLevel<double> L0 = describe<double>(h, 0, M.v64[0], h->lv[0].w64.get());
     L0.r = M.r64.get();
-    const double mu = adaptive ? 1.0 : h->opt.mu_flat;
+    const double mu = adaptive ? h->opt.mu_adaptive : h->opt.mu_flat;
     LAMG_CUDA(cudaMemsetAsync(M.bar.get(), 0, 2 * sizeof(unsigned int), s));  // the barrier counts from 0
     if (kind == 1) {
         MRArgs<float> a{(const Op *)M.prog[slot].get(), 0, M.len[slot], (const MKLevel<float> *)M.lv32.get(), L0,

@@ -570,7 +570,7 @@ void prepare_solve(lamg_ctx *h) { prepare(h); }
 
 // Engine launch of one step with optional CUDA-event timing of the launch.
 static void run_step(lamg_ctx *h, int kind, int adaptive, cudaStream_t s) {
-    const double mu = adaptive ? 1.0 : h->opt.mu_flat;
+    const double mu = adaptive ? h->opt.mu_adaptive : h->opt.mu_flat;
     if (h->prof_on) {
         if (h->prof_ev.size() < 2) {
             for (int k = 0; k < 2; k++) {
@@ -796,7 +796,7 @@ void cycle_device_noalloc(lamg_ctx *h, const double *b, double *x, int32_t adapt
     LAMG_CHECK_LAUNCH();
     k_gather_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, V0.perm.get(), x, h->v64[0].x.get());
     LAMG_CHECK_LAUNCH();
-    int32_t *err = engine_run_noalloc(h, adaptive, adaptive ? 1.0 : h->opt.mu_flat, s);
+    int32_t *err = engine_run_noalloc(h, adaptive, adaptive ? h->opt.mu_adaptive : h->opt.mu_flat, s);
     k_scatter_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, V0.perm.get(), h->v64[0].x.get(), x);
     LAMG_CHECK_LAUNCH();
     int32_t e = 0;

@@ -194,3 +194,20 @@ def test_grid_acf_matches_the_paper_only_with_elimination():
     _, hist = h.solve(b, tol=1e-10, max_cycles=40)
     rate = (hist[-1] / hist[-11]) ** 0.1              # over the last 10 cycles
     assert rate > 0.9, rate
+
+
+def test_adaptive_cycle_on_the_1024_grid_needs_a_mild_flat_factor():
+    # The paper's grid table: 5-point 1024^2 grid, ACF .216.  With elimination, the
+    # adaptive cycle with recombination alone (mu = 1, reading R15) stalls on this
+    # grid; with a mild flat factor under the recombination (mu_adaptive = 1.2) it
+    # converges at about the paper's rate.
+    g = W.grid2d(1024, 1024)
+    b = W.zero_sum_rhs(g.n, 1)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1, mu_adaptive=1.2)
+    _, hist = h.solve(b, tol=1e-10, max_cycles=40)
+    p = len(hist) - 1
+    acf = (hist[-1] / hist[0]) ** (1.0 / p)
+    assert p <= 20 and 0.12 <= acf <= 0.30, (p, acf)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1)
+    _, hist = h.solve(b, tol=1e-10, max_cycles=25)
+    assert (hist[-1] / hist[-6]) ** 0.2 > 0.9            # stalled: rate over the last 5 cycles
