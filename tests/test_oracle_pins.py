@@ -607,6 +607,44 @@ def test_per_level_pieces_reproduce_the_hierarchy():
         assert np.array_equal(oracle.hubs(n, rp, col, w), h.agg(l)[2])
 
 
+@pytest.mark.parametrize("gname", ["chung_lu", "grid"])
+def test_test_vectors_are_colour_order_gs_from_the_counter_draws(gname):
+    """Sec. 3.3.1 and Sec. 4.1: each level's K test vectors start from random[-1,1]
+    draws and take nu_tv GS sweeps on A x = 0 in colour order.  Recomputed here in
+    numpy from the draws' definition (splitmix64 of the level's TV key plus the
+    entry index u K + k, top 53 bits as t in [0,1), then 2t - 1) and colour-class
+    updates x_S = (W x)_S / diag_S; K grows from 4 by one per level up to 10.
+    The last sweep's energy ratio is x^T A x after over before, the largest over
+    the K vectors."""
+    g = W.chung_lu(3000, seed=5) if gname == "chung_lu" else W.grid2d(40, 36)
+    o = oracle.default_opts()
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, relax_fast_ratio=1e-12)
+    for l in range(h.num_levels - 1):
+        i = h.info(l)
+        n, K = i["n"], i["K"]
+        assert K == min(o.k_finest + l, o.k_max)
+        rp, col, w = h.csr(l)
+        Wm = np.zeros((n, n))
+        Wm[np.repeat(np.arange(n), np.diff(rp)), col] = w
+        d = Wm.sum(axis=1)
+        A = np.diag(d) - Wm
+        key = oracle.splitmix64(oracle.splitmix64(o.seed) ^ ((2 * l + 2) << 32))
+        z = np.array([oracle.splitmix64((key + j) & (2**64 - 1)) for j in range(n * K)], dtype=np.uint64)
+        X = 2.0 * ((z >> np.uint64(11)).astype(np.float64) * 2.0**-53) - 1.0
+        X = X.reshape(n, K)
+        colour = h.colour(l)
+        energies = []
+        for _ in range(o.nu_tv):
+            for c in range(i["ncolours"]):
+                S = colour == c
+                X[S] = (Wm[S] @ X) / d[S, None]
+            energies.append(np.einsum("uk,uv,vk->k", X, A, X))
+        got = h.tv(l)
+        assert np.max(np.abs(got - X)) <= 1e-13 * np.max(np.abs(X)), l
+        ratio = np.max(energies[-1] / energies[-2])
+        assert i["tv_ratio"] == pytest.approx(ratio, rel=1e-9), l
+
+
 def _per_unit_work(h, b, nu):
     # asymptotic convergence factor per unit of work: the rate over the last 5 cycles,
     # to the power 1/W, W = relaxation sweeps per cycle weighted by level size (the
