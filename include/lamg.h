@@ -94,6 +94,9 @@ typedef struct {
     double   mu_adaptive;      /* restriction factor of the adaptive cycle (recombination,
                                   Eq. (3.13)): 1 (default) or a mild flat correction
                                   on top of recombination; see the oracle's figures    */
+    double   gamma_coarse_max; /* cap of the cycle index gamma^l at the coarse levels
+                                  (|E^l| <= .1 |E|), Eq. (4.1): 2 as printed.  1 makes
+                                  the coarse part of the cycle a V-cycle              */
 } lamg_options;
 
 typedef struct {
