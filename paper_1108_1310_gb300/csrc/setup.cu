@@ -516,12 +516,12 @@ __device__ __forceinline__ bool beats(int32_t du, uint64_t pu, int32_t u, int32_
     return pu > pv || (pu == pv && u < v);
 }
 
-// smallest colour not used by any neighbour, searched in windows of 64
+// smallest colour >= base0 not used by any neighbour, searched in windows of 64
 template <int M>
 __device__ __forceinline__ int32_t jp_free_colour(int32_t u, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ col,
-                                                  const int32_t *__restrict__ colour) {
-    for (int32_t base = 0;; base += 64) {
+                                                  const int32_t *__restrict__ colour, int32_t base0 = 0) {
+    for (int32_t base = base0;; base += 64) {
         unsigned long long mask = 0ull;
         for (int32_t i = rp[u] + tlane<M>(); i < rp[u + 1]; i += tstride<M>()) {
             const int32_t c = colour[col[i]];
@@ -661,11 +661,55 @@ __device__ __forceinline__ void jp_release(int32_t u, const int32_t *__restrict_
     }
 }
 
+// A round's hub rows (block tier) are few and long (a median of about 1,000
+// entries at the middle levels of a power-law graph).  With at most
+// kSpreadHubs of them, their entries are dealt to every warp of the grid in
+// pieces of 32, instead of one block per hub:
+//   colour phase:  each piece ORs its neighbours' colours below kFreeBits into
+//                  the hub's bitmap in global memory (gbits, kept zeroed);
+//   release phase: the hub's global warp j takes the first clear bit as the
+//                  colour and clears the bitmap, while all warps release the
+//                  hub's neighbours piece by piece.
+// The colours are the same as with one block per hub: the colour is the
+// smallest one free among the neighbours, and the release order changes no
+// decision.  More hubs in one round take the per-block path.
+constexpr int kSpreadHubs = 32;
+constexpr int kFreeWords = kFreeBits / 32;
+
+// the piece p of the frontier's c2 <= 32 hub rows: hub index j, row u and this
+// lane's entry e (valid when e < rp[u + 1]); hub data are held one per lane
+struct HubPieces {
+    int32_t myu, myn, incl, total;
+};
+__device__ __forceinline__ HubPieces hub_pieces(int32_t c2, const int32_t *L2, const int32_t *__restrict__ rp) {
+    const int lane = threadIdx.x & 31;
+    HubPieces h;
+    h.myu = lane < c2 ? L2[lane] : 0;
+    h.myn = lane < c2 ? (rp[h.myu + 1] - rp[h.myu] + 31) >> 5 : 0;
+    int32_t v = h.myn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    h.incl = v;
+    h.total = __shfl_sync(0xffffffffu, v, 31);
+    return h;
+}
+__device__ __forceinline__ void hub_piece(const HubPieces &h, int64_t p, int32_t c2, const int32_t *__restrict__ rp,
+                                          int &j, int32_t &u, int32_t &e) {
+    const int lane = threadIdx.x & 31;
+    j = __popc(__ballot_sync(0xffffffffu, lane < c2 && h.incl <= p));
+    u = __shfl_sync(0xffffffffu, h.myu, j);
+    const int32_t start = __shfl_sync(0xffffffffu, h.incl - h.myn, j);
+    e = rp[u] + (int32_t)(p - start) * 32 + lane;
+}
+
 __global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                                 const int32_t *__restrict__ deg, const uint64_t *__restrict__ hsh,
                                                 int32_t *__restrict__ wait, int32_t *__restrict__ colour, int32_t *lst,
                                                 int64_t cap, int32_t *cnt, int32_t *out, unsigned int *bar,
-                                                int32_t *err) {
+                                                int32_t *err, unsigned int *gbits) {
     const int64_t nthr = (int64_t)gridDim.x * kBlk;
     // chunks of 32 items, consecutive chunks on consecutive blocks (spread over every SM)
     const int64_t tid = ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
@@ -682,6 +726,7 @@ __global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp,
         }
         const int32_t *L0 = lst + (int64_t)(r & 1) * 3 * cap, *L1 = L0 + cap, *L2 = L1 + cap;
         int32_t *N = lst + (int64_t)((r + 1) & 1) * 3 * cap;
+        const bool spread = c2 <= kSpreadHubs;
         // colour the frontier: its higher-priority neighbours are all coloured
         for (int64_t i = tid; i < c0; i += nthr) {
             const int32_t u = L0[i];
@@ -692,17 +737,64 @@ __global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp,
             const int32_t c = jp_free_colour<M_WARP>(u, rp, col, colour);
             if (lane == 0) colour[u] = c;
         }
-        for (int64_t i = blockIdx.x; i < c2; i += gridDim.x) {
-            const int32_t u = L2[i];
-            const int32_t c = jp_free_colour_blk(u, rp, col, colour);
-            if (threadIdx.x == 0) colour[u] = c;
+        if (spread) {
+            if (c2 > 0) {
+                const HubPieces hp = hub_pieces(c2, L2, rp);
+                for (int64_t p = wid; p < hp.total; p += nwarp) {
+                    int j;
+                    int32_t u, e;
+                    hub_piece(hp, p, c2, rp, j, u, e);
+                    if (e < rp[u + 1]) {
+                        const int32_t c = colour[col[e]];
+                        if (c >= 0 && c < kFreeBits) atomicOr(&gbits[j * kFreeWords + (c >> 5)], 1u << (c & 31));
+                    }
+                }
+            }
+        } else {
+            for (int64_t i = blockIdx.x; i < c2; i += gridDim.x) {
+                const int32_t u = L2[i];
+                const int32_t c = jp_free_colour_blk(u, rp, col, colour);
+                if (threadIdx.x == 0) colour[u] = c;
+            }
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) { nxt[0] = 0; nxt[1] = 0; nxt[2] = 0; }
         if (!coop_sync(bar, err, epoch)) return;
         // release the neighbours they beat
         for (int64_t i = tid; i < c0; i += nthr) jp_release<M_THR>(L0[i], rp, col, deg, hsh, wait, N, cap, nxt);
         for (int64_t i = wid; i < c1; i += nwarp) jp_release<M_WARP>(L1[i], rp, col, deg, hsh, wait, N, cap, nxt);
-        for (int64_t i = blockIdx.x; i < c2; i += gridDim.x) jp_release<M_BLK>(L2[i], rp, col, deg, hsh, wait, N, cap, nxt);
+        if (spread) {
+            if (c2 > 0) {
+                if (wid < c2) {   // the colour of hub j = wid: first clear bit of its bitmap, which is cleared
+                    const int32_t u = L2[wid];
+                    unsigned int *bw = gbits + wid * kFreeWords;
+                    int32_t first = kFreeBits;
+                    for (int k = lane; k < kFreeWords; k += 32) {
+                        const unsigned int m = bw[k];
+                        if (m != ~0u && first == kFreeBits) first = k * 32 + __ffs(~m) - 1;
+                        bw[k] = 0u;
+                    }
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+                    if (first == kFreeBits) first = jp_free_colour<M_WARP>(u, rp, col, colour, kFreeBits);
+                    if (lane == 0) colour[u] = first;
+                }
+                const HubPieces hp = hub_pieces(c2, L2, rp);
+                for (int64_t p = wid; p < hp.total; p += nwarp) {
+                    int j;
+                    int32_t u, e;
+                    hub_piece(hp, p, c2, rp, j, u, e);
+                    if (e < rp[u + 1]) {
+                        const int32_t v = col[e];
+                        if (beats(deg[u], hsh[u], u, deg[v], hsh[v], v) && atomicSub(&wait[v], 1) == 1) {
+                            const int t = row_tier(deg[v]);
+                            N[(int64_t)t * cap + atomicAdd(&nxt[t], 1)] = v;
+                        }
+                    }
+                }
+            }
+        } else {
+            for (int64_t i = blockIdx.x; i < c2; i += gridDim.x) jp_release<M_BLK>(L2[i], rp, col, deg, hsh, wait, N, cap, nxt);
+        }
         if (!coop_sync(bar, err, epoch)) return;
     }
 }
@@ -1412,6 +1504,8 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
         LAMG_CUDA(cudaMemcpyAsync(fcnt.get(), c6, sizeof(c6), cudaMemcpyHostToDevice, s));
         LAMG_CUDA(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
         LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
+        Tmp<unsigned int> gbits((size_t)kSpreadHubs * kFreeWords, s);   // hub colour bitmaps, kept zeroed by the kernel
+        LAMG_CUDA(cudaMemsetAsync(gbits.get(), 0, sizeof(unsigned int) * kSpreadHubs * kFreeWords, s));
         const int grid = coop_grid((const void *)k_jp_dag, "colouring kernel");
         {
             const int32_t *rpp = L.rp.get(), *colp = L.col.get(), *dp = deg.get();
@@ -1419,8 +1513,8 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
             int32_t *wp = wait.get(), *colour = L.colour.get(), *lp = lst.get(), *cp = fcnt.get(), *op = out.get(),
                     *ep = err.get();
             int64_t capv = cap;
-            unsigned int *bp = bar.get();
-            void *args[] = {&rpp, &colp, &dp, &hp, &wp, &colour, &lp, &capv, &cp, &op, &bp, &ep};
+            unsigned int *bp = bar.get(), *gb = gbits.get();
+            void *args[] = {&rpp, &colp, &dp, &hp, &wp, &colour, &lp, &capv, &cp, &op, &bp, &ep, &gb};
             LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_jp_dag, dim3(grid), dim3(kBlk), args, 0, s));
             note_launch();
         }
