@@ -94,6 +94,13 @@ typedef struct {
     double   mu_adaptive;      /* restriction factor of the adaptive cycle (recombination,
                                   Eq. (3.13)): 1 (default) or a mild flat correction
                                   on top of recombination; see the oracle's figures    */
+    int32_t  lgmg_nx;          /* > 0: Lean Geometric Multigrid (Sec. 6) on an
+                                  lgmg_nx x lgmg_nx periodic 5-point grid numbered row by
+                                  row (n = lgmg_nx^2, else LAMG_ERR_ARG): 2x2 aggregates
+                                  and red-black colours at every level, gamma at every
+                                  level; the paper's setting solves with adaptive = 0 and
+                                  mu_flat = 2.  Coarsening stops below n_coarsest nodes or
+                                  at an odd side or a side below 6.  Default 0           */
 } lamg_options;
 
 typedef struct {

@@ -1264,7 +1264,21 @@ static int coop_grid(const void *kernel, const char *what) {
     return sms;
 }
 
-static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s) {
+// Lean Geometric Multigrid (Sec. 6): node u = (row u / nx, column u % nx) of an
+// nx x nx periodic grid; red-black colours and 2x2 aggregates numbered row by row
+__global__ void k_rb_colour(int32_t n, int32_t nx, int32_t *__restrict__ colour) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) colour[u] = ((u % nx) + (u / nx)) & 1;
+}
+__global__ void k_geo_agg(int32_t n, int32_t nx, int32_t *__restrict__ agg, int32_t *__restrict__ state) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    agg[u] = (u / nx) / 2 * (nx / 2) + (u % nx) / 2;
+    state[u] = 0;
+}
+
+// rb_nx > 0: red-black colours of an rb_nx x rb_nx periodic grid instead of JP
+static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, int32_t rb_nx, cudaStream_t s) {
     const int32_t n = L.n;
     L.colour.alloc(n);
     k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, -1);
@@ -1274,7 +1288,10 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
     ct.level = level;
     int32_t batch_rounds = 0;
     const int32_t fin_rounds = 0;
-    {
+    if (rb_nx > 0) {
+        k_rb_colour<<<ceil_div(n, 256), 256, 0, s>>>(n, rb_nx, L.colour.get());
+        LAMG_CHECK_LAUNCH();
+    } else {
     // wait counts, the first frontier, then all rounds in one cooperative launch
     Tmp<int32_t> deg(n, s), wait(n, s);
     Tmp<uint64_t> hsh(n, s);
@@ -1617,6 +1634,10 @@ static void galerkin_level(SetupLevel &F, SetupLevel &C, const int32_t *erow, cu
 static void cycle_indices(lamg_ctx *h) {
     const double m1 = (double)h->sl[0].nnz / 2.0;
     for (int l = 0; l + 1 < h->L; l++) {
+        if (h->opt.lgmg_nx > 0) {   // Sec. 6: a standard gamma-cycle
+            h->sl[l].gamma_l = h->opt.gamma;
+            continue;
+        }
         const double ml = (double)h->sl[l].nnz / 2.0, mn = (double)h->sl[l + 1].nnz / 2.0;
         double g = mn > 0.0 ? 0.7 * ml / mn : 2.0;
         const double gmax = ml > 0.1 * m1 ? h->opt.gamma : 2.0;
@@ -1654,6 +1675,9 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         }
     }
     const int maxl = std::min(o.max_levels, 128);
+    int32_t nxl = o.lgmg_nx;   // Lean Geometric MG: the current grid side
+    LAMG_REQUIRE(nxl >= 0 && (nxl == 0 || (int64_t)nxl * nxl == n), LAMG_ERR_ARG,
+                 "lgmg_nx * lgmg_nx must equal n");
     PhaseTimer pt(s);
     pt.mark("ingest");
     for (int l = 0;; l++) {
@@ -1668,12 +1692,29 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         LAUNCH3(k_node_stats, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
                 L.col.get(), L.w.get(), o.hub_factor, diag.get(), maxw.get(), L.hub.get());
         pt.mark("stats");
-        colour_level(h, L, l, T, s);
+        colour_level(h, L, l, T, nxl, s);
         pt.mark("colour");
-        if (nl < o.n_coarsest || l + 1 >= maxl) {
+        if (nl < o.n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
             L.coarsest = 1;
             L.stop_reason = nl < o.n_coarsest ? 1 : 4;
             break;
+        }
+        if (nxl > 0) {   // Lean Geometric MG: 1:2 coarsening in both directions, 2x2 aggregates
+            L.agg.alloc(nl);
+            L.state.alloc(nl);
+            k_geo_agg<<<ceil_div(nl, 256), 256, 0, s>>>(nl, nxl, L.agg.get(), L.state.get());
+            LAMG_CHECK_LAUNCH();
+            LAMG_CUDA(cudaMemsetAsync(L.hub.get(), 0, (size_t)nl, s));
+            L.nc = (nxl / 2) * (nxl / 2);
+            L.alpha = (double)L.nc / (double)nl;
+            Tmp<int32_t> erow(L.nnz, s);
+            LAUNCH3(k_entry_rows, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                    erow.get());
+            h->sl.emplace_back();
+            galerkin_level(h->sl[l], h->sl[l + 1], erow.get(), s);
+            pt.mark("galerkin");
+            nxl /= 2;
+            continue;
         }
         int K = o.k_finest + o.k_step * l;
         if (K > o.k_max) K = o.k_max;

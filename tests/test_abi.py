@@ -69,8 +69,8 @@ def test_default_options_match_the_oracle(lib):
     import oracle
     from paper_1108_1310_gb300 import lamg as L
     a, b = L.lamg_default_options(), oracle.default_opts()
-    # oracle-only options: the sequential-scan reference, elimination, lean geometric MG
-    oracle_only = {"agg_rule", "elim", "elim_min_frac", "lgmg_nx"}
+    # oracle-only options: the sequential-scan reference, elimination
+    oracle_only = {"agg_rule", "elim", "elim_min_frac"}
     assert (b.agg_rule, b.elim) == (0, 0)
     for f, _ in oracle.Opts._fields_:
         if f not in oracle_only:
