@@ -91,12 +91,12 @@ def sample_graph(workload):
     return W.grid2d(size, size), f"{size}x{size} 5-point grid"
 
 
-def cpu_oracle_step(g, b, tol, workload=""):
+def cpu_oracle_step(g, b, tol, workload="", gamma_coarse_max=2.0):
     """The oracle as it stands: FP64 setup + solve on one host core."""
     import oracle
     opts, adaptive = method_opts(workload, g.n)
     t0 = time.perf_counter()
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, **opts)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma_coarse_max=gamma_coarse_max, **opts)
     x, hist = h.solve(b, tol=tol, max_cycles=500, adaptive=adaptive)
     t = time.perf_counter() - t0
     return t, len(hist) - 1
@@ -160,10 +160,10 @@ def run_reference(args):
     b = W.zero_sum_rhs(g.n, 2)
     tol = TOL[args.workload]
     for _ in range(min(args.warmup, 1)):
-        cpu_oracle_step(g, b, tol, args.workload)
+        cpu_oracle_step(g, b, tol, args.workload, args.gamma_coarse_max)
     ts, cyc = [], []
     for _ in range(args.steps):
-        t, c = cpu_oracle_step(g, b, tol, args.workload)
+        t, c = cpu_oracle_step(g, b, tol, args.workload, args.gamma_coarse_max)
         ts.append(t)
         cyc.append(c)
     tmean = sum(ts) / len(ts)
@@ -173,7 +173,8 @@ def run_reference(args):
         "unit": "edges*cycles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": min(args.warmup, 1),
         "ms_per_step": tmean * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": desc, "n": g.n, "m": g.m, "tol": tol},
+        "config": {"workload": args.workload, "sample": desc, "n": g.n, "m": g.m, "tol": tol,
+                   "gamma_coarse_max": args.gamma_coarse_max},
         "cpu_baseline": {"value": value, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "edges*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -259,8 +260,7 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
     x = torch.zeros_like(b)
     lam = torch.zeros_like(b)
     dw = torch.zeros(eu.size, dtype=torch.float64, device=dev)
-    mopts, adaptive = method_opts(args.workload, g.n)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000, adaptive=int(adaptive), **mopts)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, gamma_coarse_max=args.gamma_coarse_max)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(prec=L.LAMG_FP32_IR):
@@ -355,7 +355,7 @@ def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
     col = torch.tensor(g.col, device=dev)
     w = torch.tensor(g.w, device=dev).to(torch.float32)
     X = torch.zeros_like(B)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, gamma_coarse_max=args.gamma_coarse_max)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     tuned = {}
@@ -462,6 +462,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gamma-coarse-max", type=float, default=2.0,
+                    help="cap of the cycle index at the coarse levels (Eq. (4.1) prints 2)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -499,7 +501,9 @@ def main():
     w = torch.tensor(g.w, device=dev).to(w_dtype)
     b = torch.tensor(b_host, device=dev)
     x = torch.zeros_like(b)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000)
+    mopts, adaptive = method_opts(args.workload, g.n)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, adaptive=int(adaptive),
+                                 gamma_coarse_max=args.gamma_coarse_max, **mopts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
     def step(profile=False):
@@ -616,7 +620,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sg, sdesc = sample_graph(args.workload)
         sb = W.zero_sum_rhs(sg.n, 2)
-        t, c = cpu_oracle_step(sg, sb, tol, args.workload)
+        t, c = cpu_oracle_step(sg, sb, tol, args.workload, args.gamma_coarse_max)
         cpu = {"value": sg.m * c / t, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
                "sample": f"{sdesc}, FP64 setup + solve to {tol:g}, {t:.1f} s"}
 
@@ -627,7 +631,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == L.LAMG_FP32_IR else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "tol": tol,
-                   "precision": prec_name, "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
+                   "precision": prec_name, "gamma_coarse_max": args.gamma_coarse_max, "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
                    "rel_res": s0.rel_res, "time_to_tol_s": ms / 1e3,
                    "setup_s_host": s0.t_setup_s, "solve_s_host": s0.t_solve_s,
                    "model_bytes_per_cycle": s0.bytes_per_cycle32 if prec == L.LAMG_FP32_IR else s0.bytes_per_cycle,

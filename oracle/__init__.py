@@ -44,7 +44,7 @@ class Opts(C.Structure):
                 ("dense_max", C.c_int32), ("coarse_sweeps", C.c_int32),
                 ("mu_flat", C.c_double), ("seed", C.c_uint64), ("agg_rule", C.c_int32),
                 ("elim", C.c_int32), ("elim_min_frac", C.c_double), ("lgmg_nx", C.c_int32),
-                ("mu_adaptive", C.c_double)]
+                ("mu_adaptive", C.c_double), ("gamma_coarse_max", C.c_double)]
 
 
 _P = C.c_void_p

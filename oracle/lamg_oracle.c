@@ -42,6 +42,7 @@ void orc_default_opts(orc_opts *o) {
     o->elim_min_frac = 0.1;    /* reading of "until |F| becomes small", Sec. 3.2 */
     o->lgmg_nx = 0;            /* algebraic coarsening */
     o->mu_adaptive = 1.0;      /* reading R15: recombination replaces the flat correction */
+    o->gamma_coarse_max = 2.0; /* Eq. (4.1): min{2, ...} at coarse levels */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -862,7 +863,8 @@ static void eliminate(const orc_level *F, const int32_t *cidx, orc_level *C) {
  * work increase, so this build reads the ratio inverted,
  * g = .7 |E^l| / |E^{l+1}| (coarse work per fine visit stays at .7), and
  * applies the same bound at the fine levels, where the cap is gamma instead
- * of 2:  gamma^l = min{cap, max{1, g}}, cap = gamma if |E^l| > .1|E| else 2.
+ * of 2:  gamma^l = min{cap, max{1, g}}, cap = gamma if |E^l| > .1|E| else
+ * gamma_coarse_max (2, as printed).
  * (With the printed fine-level rule gamma^l = gamma, a level that coarsens
  * slowly, alpha ~ .85, makes the work per cycle grow without bound.) */
 static void cycle_indices(orc_hier *h) {
@@ -872,7 +874,7 @@ static void cycle_indices(orc_hier *h) {
         if (h->o.lgmg_nx > 0) { h->lv[l].gamma_l = h->o.gamma; continue; }   /* Sec. 6: a standard gamma-cycle */
         double ml = (double)h->lv[l].nnz / 2.0, mn = (double)h->lv[l + 1].nnz / 2.0;
         double g = mn > 0.0 ? 0.7 * ml / mn : 2.0;
-        double gmax = ml > 0.1 * m1 ? h->o.gamma : 2.0;
+        double gmax = ml > 0.1 * m1 ? h->o.gamma : h->o.gamma_coarse_max;
         if (g > gmax) g = gmax;
         if (g < 1.0) g = 1.0;
         h->lv[l].gamma_l = g;

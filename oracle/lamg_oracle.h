@@ -62,6 +62,7 @@ typedef struct {
                                   and red-black colours at every level, gamma at every
                                   level; solve in flat mode with mu_flat = 2.  Default 0 */
     double   mu_adaptive;      /* restriction factor of the adaptive cycle (reading R15: 1) */
+    double   gamma_coarse_max; /* cap of the cycle index at coarse levels, Eq. (4.1): 2    */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;

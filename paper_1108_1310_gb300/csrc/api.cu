@@ -121,6 +121,7 @@ void lamg_default_options(lamg_options *o) {
     o->keep_setup_data = 0;
     o->project_rhs = 0;
     o->mu_adaptive = 1.0;
+    o->gamma_coarse_max = 2.0;
     o->lgmg_nx = 0;
 }
 

@@ -1640,7 +1640,7 @@ static void cycle_indices(lamg_ctx *h) {
         }
         const double ml = (double)h->sl[l].nnz / 2.0, mn = (double)h->sl[l + 1].nnz / 2.0;
         double g = mn > 0.0 ? 0.7 * ml / mn : 2.0;
-        const double gmax = ml > 0.1 * m1 ? h->opt.gamma : 2.0;
+        const double gmax = ml > 0.1 * m1 ? h->opt.gamma : h->opt.gamma_coarse_max;
         if (g > gmax) g = gmax;
         if (g < 1.0) g = 1.0;
         h->sl[l].gamma_l = g;

@@ -645,6 +645,32 @@ def test_test_vectors_are_colour_order_gs_from_the_counter_draws(gname):
         assert i["tv_ratio"] == pytest.approx(ratio, rel=1e-9), l
 
 
+def test_coarse_cycle_index_cap():
+    # gamma_coarse_max caps gamma^l where |E^l| <= .1 |E| (Eq. (4.1) prints 2); the
+    # cap changes the cycle only, never the hierarchy, and with cap 1 the coarse part
+    # of the cycle is a V-cycle
+    g = W.chung_lu(20000, seed=3)
+    b = W.zero_sum_rhs(g.n, 2)
+    h2 = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    h1 = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma_coarse_max=1.0)
+    assert oracle.default_opts().gamma_coarse_max == 2.0
+    assert h1.num_levels == h2.num_levels
+    m1 = h2.info(0)["nnz"]
+    coarse = 0
+    for l in range(h2.num_levels - 1):
+        for k in range(3):
+            assert np.array_equal(h1.csr(l)[k], h2.csr(l)[k])
+        g1, g2 = h1.info(l)["gamma"], h2.info(l)["gamma"]
+        if h2.info(l)["nnz"] > 0.1 * m1:
+            assert g1 == g2 <= 1.5
+        else:
+            coarse += 1
+            assert g1 == 1.0 and 1.0 <= g2 <= 2.0
+    assert coarse >= 2
+    x, hist = h1.solve(b, tol=1e-10)
+    assert hist[-1] <= 1e-10 * hist[0]
+
+
 def _per_unit_work(h, b, nu):
     # asymptotic convergence factor per unit of work: the rate over the last 5 cycles,
     # to the power 1/W, W = relaxation sweeps per cycle weighted by level size (the
