@@ -93,10 +93,12 @@ typedef struct {
                                   caller's b unchanged                                    */
     double   mu_adaptive;      /* restriction factor of the adaptive cycle (recombination,
                                   Eq. (3.13)): 1 (default) or a mild flat correction
-                                  on top of recombination; see the oracle's figures    */
+                                  on top of recombination; see the oracle's figures.
+                                  Must lie in (0, 4), else LAMG_ERR_ARG                 */
     double   gamma_coarse_max; /* cap of the cycle index gamma^l at the coarse levels
                                   (|E^l| <= .1 |E|), Eq. (4.1): 2 as printed.  1 makes
-                                  the coarse part of the cycle a V-cycle              */
+                                  the coarse part of the cycle a V-cycle.  Must lie in
+                                  [1, 2], else LAMG_ERR_ARG                             */
     int32_t  lgmg_nx;          /* > 0: Lean Geometric Multigrid (Sec. 6) on an
                                   lgmg_nx x lgmg_nx periodic 5-point grid numbered row by
                                   row (n = lgmg_nx^2, else LAMG_ERR_ARG): 2x2 aggregates

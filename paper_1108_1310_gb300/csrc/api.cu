@@ -141,15 +141,19 @@ static lamg_status setup_impl(int32_t ngraphs, const int64_t *graph_ptr, int64_t
                      "graph_ptr must start at 0 and end at n");
         for (int32_t g = 0; g < ngraphs; g++)
             LAMG_REQUIRE(graph_ptr[g + 1] > graph_ptr[g], LAMG_ERR_ARG, "graph_ptr must be strictly increasing");
+        // the options are checked before anything is allocated
+        lamg_options o;
+        if (opt) o = *opt; else lamg_default_options(&o);
+        LAMG_REQUIRE(o.gamma >= 1.0 && o.nu_tv >= 0 && o.nu1 >= 0 && o.nu2 >= 0 && o.k_finest >= 1 &&
+                         o.max_rounds >= 1 && o.max_levels >= 1 && o.dense_max >= 1 &&
+                         o.gamma_coarse_max >= 1.0 && o.gamma_coarse_max <= 2.0 &&
+                         o.mu_adaptive > 0.0 && o.mu_adaptive < 4.0,
+                     LAMG_ERR_ARG, "invalid options");
         auto t0 = std::chrono::steady_clock::now();
         h = new lamg_ctx();
         h->ngraphs = ngraphs;
         h->gptr.assign(graph_ptr, graph_ptr + ngraphs + 1);
-        if (opt) h->opt = *opt; else lamg_default_options(&h->opt);
-        LAMG_REQUIRE(h->opt.gamma >= 1.0 && h->opt.nu_tv >= 0 && h->opt.nu1 >= 0 && h->opt.nu2 >= 0 &&
-                         h->opt.k_finest >= 1 && h->opt.max_rounds >= 1 && h->opt.max_levels >= 1 &&
-                         h->opt.dense_max >= 1,
-                     LAMG_ERR_ARG, "invalid options");
+        h->opt = o;
         cudaStream_t s = (cudaStream_t)stream;
         if (h->opt.validate) validate_graph(n, row_ptr, col, w, w_is_fp32, s, ngraphs, graph_ptr);
         build_hierarchy(h, n, row_ptr, col, w, w_is_fp32, s);

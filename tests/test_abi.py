@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -85,3 +86,14 @@ def test_errors_without_gpu_are_status_codes(lib):
     assert st == L.LAMG_ERR_ARG and not h.value
     assert b"n must be" in L._lib.lamg_last_error()
     L._lib.lamg_free(None)  # no-op
+    # options out of range are rejected before anything is allocated (the host
+    # row_ptr below is never read)
+    rp = np.zeros(5, dtype=np.int64)
+    for field, bad in (("gamma_coarse_max", 0.5), ("gamma_coarse_max", 3.0), ("gamma_coarse_max", float("nan")),
+                       ("mu_adaptive", 0.0), ("gamma", 0.9)):
+        o = L.lamg_default_options()
+        setattr(o, field, bad)
+        st = L._lib.lamg_setup(4, rp.ctypes.data_as(ctypes.c_void_p), None, None, 0, ctypes.byref(o), None,
+                               ctypes.byref(h))
+        assert st == L.LAMG_ERR_ARG and not h.value, field
+        assert b"invalid options" in L._lib.lamg_last_error()
