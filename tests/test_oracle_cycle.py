@@ -145,6 +145,9 @@ def _graphs():
         "grid_elim": (W.grid2d(36, 30), None, {"elim": 1}),
         "chung_lu_elim": (W.chung_lu(2500, seed=33), None, {"elim": 1}),
         "union": (*W.er_batch(12, 60, 400, seed=34), {}),
+        # the restriction factor under recombination, and the coarse cycle-index cap
+        "chung_lu_mu": (W.chung_lu(2500, seed=35), None, {"mu_adaptive": 1.2}),
+        "rgg_cap1": (W.rgg2d(1500, seed=36), None, {"gamma_coarse_max": 1.0}),
     }
 
 
