@@ -671,6 +671,28 @@ def test_coarse_cycle_index_cap():
     assert hist[-1] <= 1e-10 * hist[0]
 
 
+@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "grid3d", "er"])
+def test_cycle_work_is_about_ten_relaxations(gname):
+    # Sec. 4.2: the whole cycle costs about 10 relaxation sweeps of the finest level.
+    # With the paper's elimination levels, the bounded cycle index (reading R13)
+    # keeps the cycle's relaxation work, (nu1 + nu2) sum_l visits_l |A^l| / |A^0|,
+    # within a factor 2 of that on every family.
+    g = {"grid64": lambda: W.grid2d(64, 64), "chung_lu": lambda: W.chung_lu(20000, seed=3),
+         "rgg": lambda: W.rgg2d(20000, seed=4), "grid3d": lambda: W.grid3d(24, 24, 24, 1.0, 1.0, 0.01),
+         "er": lambda: W.erdos_renyi(5000, seed=5)}[gname]()
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1)
+    o = h.opts
+    visits, sweeps, nnz0 = 1.0, 0.0, h.info(0)["nnz"]
+    for l in range(h.num_levels):
+        i = h.info(l)
+        if i["coarsest"]:
+            break
+        if not i["elim"]:
+            sweeps += (o.nu1 + o.nu2) * visits * i["nnz"] / nnz0
+        visits *= i["gamma"]
+    assert 5.0 <= sweeps <= 20.0, sweeps
+
+
 def _per_unit_work(h, b, nu):
     # asymptotic convergence factor per unit of work: the rate over the last 5 cycles,
     # to the power 1/W, W = relaxation sweeps per cycle weighted by level size (the
