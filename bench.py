@@ -37,8 +37,11 @@ WORKLOADS = {
                 "256^3 7-point grid, weights 1/1/0.01; FP32 cycles in FP64 IR to 1e-8"),
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
     "grid1024": ("grid1024", "fp32ir", "1024x1024 5-point grid, unit weights (run with --elim); FP32 cycles in FP64 IR to 1e-8"),
+    "torus1024_lgmg": ("torus1024", "fp32ir",
+                       "1024x1024 periodic 5-point grid, unit weights; Lean Geometric MG (Sec. 6): 2x2 aggregates, "
+                       "red-black GS, gamma 1.5 at every level, flat mu 2; FP32 cycles in FP64 IR to 1e-8"),
 }
-TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10, "grid1024": 1e-8}
+TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10, "grid1024": 1e-8, "torus1024_lgmg": 1e-8}
 # DRAM bytes (read + write) of one engine launch from one ncu capture of this
 # workload (profiles/k_engine_chung_lu1m_fp32ir.md); must be emptied
 # whenever the engine kernel changes.
@@ -56,7 +59,17 @@ BATCHED = {
              "RHS each, as one block-diagonal union (lamg_setup_graphs); FP32 cycles in FP64 IR to 1e-8 per graph",
 }
 CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64),
-              "grid1024": ("grid2d", 256)}
+              "grid1024": ("grid2d", 256),
+              "torus1024_lgmg": ("torus", 1024)}
+
+
+def method_opts(workload, n):
+    """Options of the method for a workload of n nodes, the same for the library and
+    the oracle, and whether the solve is adaptive.  The geometric workloads run Lean
+    Geometric MG (Sec. 6) in flat mode with mu = 2 on the grid of side sqrt(n)."""
+    if workload.endswith("_lgmg"):
+        return {"lgmg_nx": int(round(n ** 0.5)), "mu_flat": 2.0}, False
+    return {}, True
 
 
 def load_peaks():
@@ -75,15 +88,18 @@ def sample_graph(workload):
         return W.chung_lu(size, 2.5, 10.0, seed=2), f"Chung-Lu n={size} (same family and seed rule)"
     if kind == "grid3d":
         return W.grid3d(size, size, size, 1.0, 1.0, 0.01), f"{size}^3 7-point grid, weights 1/1/0.01"
+    if kind == "torus":
+        return W.grid2d_periodic(size), f"{size}x{size} periodic 5-point grid, Lean Geometric MG"
     return W.grid2d(size, size), f"{size}x{size} 5-point grid"
 
 
-def cpu_oracle_step(g, b, tol, gamma_coarse_max=2.0, elim=0):
+def cpu_oracle_step(g, b, tol, workload="", gamma_coarse_max=2.0, elim=0):
     """The oracle as it stands: FP64 setup + solve on one host core."""
     import oracle
+    opts, adaptive = method_opts(workload, g.n)
     t0 = time.perf_counter()
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma_coarse_max=gamma_coarse_max, elim=elim)
-    x, hist = h.solve(b, tol=tol, max_cycles=500)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma_coarse_max=gamma_coarse_max, elim=elim, **opts)
+    x, hist = h.solve(b, tol=tol, max_cycles=500, adaptive=adaptive)
     t = time.perf_counter() - t0
     return t, len(hist) - 1
 
@@ -146,10 +162,10 @@ def run_reference(args):
     b = W.zero_sum_rhs(g.n, 2)
     tol = TOL[args.workload]
     for _ in range(min(args.warmup, 1)):
-        cpu_oracle_step(g, b, tol, args.gamma_coarse_max, elim=int(args.elim))
+        cpu_oracle_step(g, b, tol, args.workload, args.gamma_coarse_max, elim=int(args.elim))
     ts, cyc = [], []
     for _ in range(args.steps):
-        t, c = cpu_oracle_step(g, b, tol, args.gamma_coarse_max, elim=int(args.elim))
+        t, c = cpu_oracle_step(g, b, tol, args.workload, args.gamma_coarse_max, elim=int(args.elim))
         ts.append(t)
         cyc.append(c)
     tmean = sum(ts) / len(ts)
@@ -489,8 +505,9 @@ def main():
     w = torch.tensor(g.w, device=dev).to(w_dtype)
     b = torch.tensor(b_host, device=dev)
     x = torch.zeros_like(b)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000, gamma_coarse_max=args.gamma_coarse_max,
-                                 elim=int(args.elim))
+    mopts, adaptive = method_opts(args.workload, g.n)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, adaptive=int(adaptive),
+                                 gamma_coarse_max=args.gamma_coarse_max, elim=int(args.elim), **mopts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
     def step(profile=False):
@@ -607,7 +624,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sg, sdesc = sample_graph(args.workload)
         sb = W.zero_sum_rhs(sg.n, 2)
-        t, c = cpu_oracle_step(sg, sb, tol, args.gamma_coarse_max, elim=int(args.elim))
+        t, c = cpu_oracle_step(sg, sb, tol, args.workload, args.gamma_coarse_max, elim=int(args.elim))
         cpu = {"value": sg.m * c / t, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
                "sample": f"{sdesc}, FP64 setup + solve to {tol:g}, {t:.1f} s"}
 

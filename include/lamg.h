@@ -107,6 +107,13 @@ typedef struct {
                                   cycle back-substitutes F exactly.  Default 0.           */
     double   elim_min_frac;    /* an elimination round is kept only if it removes at least
                                   this fraction of the level's nodes: 0.1                 */
+    int32_t  lgmg_nx;          /* > 0: Lean Geometric Multigrid (Sec. 6) on an
+                                  lgmg_nx x lgmg_nx periodic 5-point grid numbered row by
+                                  row (n = lgmg_nx^2, else LAMG_ERR_ARG): 2x2 aggregates
+                                  and red-black colours at every level, gamma at every
+                                  level; the paper's setting solves with adaptive = 0 and
+                                  mu_flat = 2.  Coarsening stops below n_coarsest nodes or
+                                  at an odd side or a side below 6.  Default 0           */
 } lamg_options;
 
 typedef struct {

@@ -128,6 +128,7 @@ void lamg_default_options(lamg_options *o) {
     o->gamma_coarse_max = 2.0;
     o->elim = 0;
     o->elim_min_frac = 0.1;
+    o->lgmg_nx = 0;
 }
 
 const char *lamg_last_error(void) { return g_last_error.c_str(); }

@@ -1467,17 +1467,35 @@ static int coop_grid(const void *kernel, const char *what) {
     return sms;
 }
 
+// Lean Geometric Multigrid (Sec. 6): node u = (row u / nx, column u % nx) of an
+// nx x nx periodic grid; red-black colours and 2x2 aggregates numbered row by row
+__global__ void k_rb_colour(int32_t n, int32_t nx, int32_t *__restrict__ colour) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) colour[u] = ((u % nx) + (u / nx)) & 1;
+}
+__global__ void k_geo_agg(int32_t n, int32_t nx, int32_t *__restrict__ agg, int32_t *__restrict__ state) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    agg[u] = (u / nx) / 2 * (nx / 2) + (u % nx) / 2;
+    state[u] = 0;
+}
+
 // The JP colouring of a level that relaxes, and the (colour, tier, id) order of
 // its nodes.  A level followed by elimination never relaxes (nu = 0, Sec. 4.2):
-// it gets one colour, 0, and only the order.
-static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, cudaStream_t s, bool relaxes = true) {
+// it gets one colour, 0, and only the order.  rb_nx > 0: red-black colours of an
+// rb_nx x rb_nx periodic grid instead of JP.
+static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, int32_t rb_nx, cudaStream_t s,
+                         bool relaxes = true) {
     const int32_t n = L.n;
     L.colour.alloc(n);
     k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(L.colour.get(), n, relaxes ? -1 : 0);
     LAMG_CHECK_LAUNCH();
     int32_t batch_rounds = 0;
     const int32_t fin_rounds = 0;
-    if (relaxes) {
+    if (relaxes && rb_nx > 0) {
+        k_rb_colour<<<ceil_div(n, 256), 256, 0, s>>>(n, rb_nx, L.colour.get());
+        LAMG_CHECK_LAUNCH();
+    } else if (relaxes) {
         const uint64_t key = colour_key(h->opt.seed, level);
         PhaseTimer ct(s);
         ct.level = level;
@@ -1924,6 +1942,10 @@ static void cycle_indices(lamg_ctx *h) {
     const double m1 = (double)h->sl[0].nnz / 2.0;
     for (int l = 0; l + 1 < h->L; l++) {
         if (h->sl[l].elim) { h->sl[l].gamma_l = 1.0; continue; }   // Sec. 4.2: gamma = 1 above an elimination
+        if (h->opt.lgmg_nx > 0) {   // Sec. 6: a standard gamma-cycle
+            h->sl[l].gamma_l = h->opt.gamma;
+            continue;
+        }
         const double ml = (double)h->sl[l].nnz / 2.0, mn = (double)h->sl[l + 1].nnz / 2.0;
         double g = mn > 0.0 ? 0.7 * ml / mn : 2.0;
         const double gmax = ml > 0.1 * m1 ? h->opt.gamma : h->opt.gamma_coarse_max;
@@ -1961,6 +1983,9 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         }
     }
     const int maxl = std::min(o.max_levels, 128);
+    int32_t nxl = o.lgmg_nx;   // Lean Geometric MG: the current grid side
+    LAMG_REQUIRE(nxl >= 0 && (nxl == 0 || (int64_t)nxl * nxl == n), LAMG_ERR_ARG,
+                 "lgmg_nx * lgmg_nx must equal n");
     PhaseTimer pt(s);
     pt.mark("ingest");
     int nagg = 0;   // aggregation levels so far (the TV count grows with them)
@@ -1976,17 +2001,17 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         LAUNCH3(k_node_stats, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
                 L.col.get(), L.w.get(), o.hub_factor, diag.get(), maxw.get(), L.hub.get());
         pt.mark("stats");
-        if (nl < o.n_coarsest || l + 1 >= maxl) {
-            colour_level(h, L, l, T, s);
+        if (nl < o.n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
+            colour_level(h, L, l, T, nxl, s);
             pt.mark("colour");
             L.coarsest = 1;
             L.stop_reason = nl < o.n_coarsest ? 1 : 4;
             break;
         }
-        if (o.elim) {   // low-degree elimination before aggregating (Sec. 3.2)
+        if (o.elim && nxl == 0) {   // low-degree elimination before aggregating (Sec. 3.2)
             L.nF = select_elim(h, L, l, s);
             if (L.nF >= 1 && (double)L.nF >= o.elim_min_frac * (double)nl) {
-                colour_level(h, L, l, T, s, false);   // no relaxation on this level: one colour
+                colour_level(h, L, l, T, 0, s, false);   // no relaxation on this level: one colour
                 L.elim = 1;
                 L.nc = (int32_t)(nl - L.nF);
                 Tmp<int32_t> erow(L.nnz, s);
@@ -2000,8 +2025,25 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
             L.nF = 0;
             L.cidx.release();
         }
-        colour_level(h, L, l, T, s);
+        colour_level(h, L, l, T, nxl, s);
         pt.mark("colour");
+        if (nxl > 0) {   // Lean Geometric MG: 1:2 coarsening in both directions, 2x2 aggregates
+            L.agg.alloc(nl);
+            L.state.alloc(nl);
+            k_geo_agg<<<ceil_div(nl, 256), 256, 0, s>>>(nl, nxl, L.agg.get(), L.state.get());
+            LAMG_CHECK_LAUNCH();
+            LAMG_CUDA(cudaMemsetAsync(L.hub.get(), 0, (size_t)nl, s));
+            L.nc = (nxl / 2) * (nxl / 2);
+            L.alpha = (double)L.nc / (double)nl;
+            Tmp<int32_t> erow(L.nnz, s);
+            LAUNCH3(k_entry_rows, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                    erow.get());
+            h->sl.emplace_back();
+            galerkin_level(h->sl[l], h->sl[l + 1], erow.get(), s);
+            pt.mark("galerkin");
+            nxl /= 2;
+            continue;
+        }
         int K = o.k_finest + o.k_step * nagg;
         if (K > o.k_max) K = o.k_max;
         if (K > 16) K = 16;

@@ -46,7 +46,8 @@ class lamg_options(C.Structure):
                 ("mu_flat", C.c_double), ("seed", C.c_uint64), ("adaptive", C.c_int32),
                 ("max_cycles", C.c_int32), ("ir_inner", C.c_int32), ("validate", C.c_int32),
                 ("keep_setup_data", C.c_int32), ("project_rhs", C.c_int32), ("mu_adaptive", C.c_double),
-                ("gamma_coarse_max", C.c_double), ("elim", C.c_int32), ("elim_min_frac", C.c_double)]
+                ("gamma_coarse_max", C.c_double), ("elim", C.c_int32), ("elim_min_frac", C.c_double),
+                ("lgmg_nx", C.c_int32)]
 
 
 class lamg_stats(C.Structure):

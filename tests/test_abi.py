@@ -70,8 +70,8 @@ def test_default_options_match_the_oracle(lib):
     import oracle
     from paper_1108_1310_gb300 import lamg as L
     a, b = L.lamg_default_options(), oracle.default_opts()
-    # oracle-only options: the sequential-scan reference, lean geometric MG
-    oracle_only = {"agg_rule", "lgmg_nx"}
+    # oracle-only option: the sequential-scan reference
+    oracle_only = {"agg_rule"}
     assert (b.agg_rule, b.elim) == (0, 0)
     for f, _ in oracle.Opts._fields_:
         if f not in oracle_only:
