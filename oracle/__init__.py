@@ -44,7 +44,7 @@ class Opts(C.Structure):
                 ("dense_max", C.c_int32), ("coarse_sweeps", C.c_int32),
                 ("mu_flat", C.c_double), ("seed", C.c_uint64), ("agg_rule", C.c_int32),
                 ("elim", C.c_int32), ("elim_min_frac", C.c_double), ("lgmg_nx", C.c_int32),
-                ("mu_adaptive", C.c_double), ("gamma_coarse_max", C.c_double)]
+                ("mu_adaptive", C.c_double), ("gamma_coarse_max", C.c_double), ("plain_sums", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -83,6 +83,8 @@ def lib():
                 "orc_level_agg": (None, [_P, _I32, _P, _P, _P]),
                 "orc_level_elim": (None, [_P, _I32, _P]),
                 "orc_elim_set": (_I64, [_I64, _P, _P, _U64, _P]),
+                "orc_aggregate": (None, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+                "orc_galerkin": (_I64, [_I64, _P, _P, _P, _P, _I64, _P, _P, _P]),
                 "orc_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _P, _P]),
                 "orc_cycle": (_I32, [_P, _P, _P, _I32]),
                 "orc_adjoint": (_I32, [_P, _P, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32]),
@@ -160,6 +162,32 @@ def elim_set(n, rp, col, key):
     cidx = np.zeros(n, np.int32)
     nF = lib().orc_elim_set(n, _p(rp), _p(col), key & 0xFFFFFFFFFFFFFFFF, _p(cidx))
     return cidx, int(nF)
+
+
+def aggregate(n, rp, col, w, score, hub, opts: Opts | None = None, **kw):
+    """One level's aggregation (Sec. 3.4.1-3.4.2, the setup's rule) from its CSR,
+    edge scores and hub flags: (agg, state, info) with info = nc, rounds,
+    selected round, alpha."""
+    o = opts if opts is not None else default_opts(**kw)
+    rp, col, w = _csr(rp, col, w)
+    score = np.ascontiguousarray(score, dtype=np.float64)
+    hub = np.ascontiguousarray(hub, dtype=np.uint8)
+    agg, state = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    info = np.zeros(4, np.int64)
+    lib().orc_aggregate(n, _p(rp), _p(col), _p(w), _p(score), _p(hub), C.byref(o), _p(agg), _p(state), _p(info))
+    return agg, state, dict(nc=int(info[0]), rounds=int(info[1]), sel_round=int(info[2]),
+                            alpha=float(info[3:4].view(np.float64)[0]))
+
+
+def galerkin(n, rp, col, w, agg, nc):
+    """One level's Galerkin operator P^T A P (Eq. (2.5)) as a CSR (rp, col, w)."""
+    rp, col, w = _csr(rp, col, w)
+    agg = np.ascontiguousarray(agg, dtype=np.int32)
+    rpc = np.zeros(nc + 1, np.int64)
+    colc = np.zeros(max(col.size, 1), np.int32)
+    wc = np.zeros(max(col.size, 1))
+    nnz = lib().orc_galerkin(n, _p(rp), _p(col), _p(w), _p(agg), nc, _p(rpc), _p(colc), _p(wc))
+    return rpc, colc[:nnz].copy(), wc[:nnz].copy()
 
 
 def gs_sweep_lex(n, rp, col, w, b, x):

@@ -43,6 +43,7 @@ void orc_default_opts(orc_opts *o) {
     o->lgmg_nx = 0;            /* algebraic coarsening */
     o->mu_adaptive = 1.0;      /* reading R15: recombination replaces the flat correction */
     o->gamma_coarse_max = 2.0; /* Eq. (4.1): min{2, ...} at coarse levels */
+    o->plain_sums = 0;         /* the tiered canonical order of the setup sums */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -88,6 +89,17 @@ static double tv_uniform(uint64_t z) {
 /*                 the 32 group results by the halving tree again.             */
 /* ------------------------------------------------------------------------- */
 
+/* Plain order (option plain_sums): every canonical sum becomes one left-to-right
+ * sum from +0.0, the textbook definition.  The setup sets this switch for the
+ * duration of one hierarchy build; the oracle is serial. */
+static int g_plain_sums = 0;
+
+static double sum_left_to_right(const double *t, int64_t len) {
+    double s = 0.0;
+    for (int64_t i = 0; i < len; i++) s = s + t[i];
+    return s;
+}
+
 static double tree32(double *p) {
     for (int h = 16; h >= 1; h /= 2)
         for (int j = 0; j < h; j++) p[j] = p[j] + p[j + h];
@@ -95,11 +107,7 @@ static double tree32(double *p) {
 }
 
 double orc_canon_sum(const double *t, int64_t len) {
-    if (len <= 32) {
-        double s = 0.0;
-        for (int64_t i = 0; i < len; i++) s = s + t[i];
-        return s;
-    }
+    if (g_plain_sums || len <= 32) return sum_left_to_right(t, len);
     if (len <= 512) {
         double p[32];
         for (int j = 0; j < 32; j++) {
@@ -121,6 +129,7 @@ double orc_canon_sum(const double *t, int64_t len) {
  * are summed the same way, recursively. */
 double orc_canon_sum_global(const double *t, int64_t len) {
     const int64_t C = 512;
+    if (g_plain_sums) return sum_left_to_right(t, len);
     if (len <= C) return orc_canon_sum(t, len);
     int64_t nch = (len + C - 1) / C;
     double *part = (double *)malloc(sizeof(double) * (size_t)nch);
@@ -750,6 +759,42 @@ static void galerkin(const orc_level *F, orc_level *C) {
     free(E); free(D); free(t);
 }
 
+/* The aggregation of one level from its CSR, its edge scores and hub flags
+ * (Sec. 3.4.1-3.4.2 with readings R9-R11), as the setup runs it.
+ * info[0..3] = nc, rounds, selected round, alpha (double bits). */
+void orc_aggregate(int64_t n, const int64_t *rp, const int32_t *col, const double *w, const double *score,
+                   const uint8_t *hub, const orc_opts *o, int32_t *agg, int32_t *state, int64_t *info) {
+    orc_level L;
+    memset(&L, 0, sizeof(L));
+    L.n = n; L.nnz = rp[n];
+    L.rp = (int64_t *)rp; L.col = (int32_t *)col; L.w = (double *)w;
+    L.score = (double *)score; L.hub = (uint8_t *)hub;
+    L.agg = agg; L.state = state;
+    aggregate(&L, o);
+    info[0] = L.nc; info[1] = L.rounds; info[2] = L.sel_round;
+    memcpy(&info[3], &L.alpha, sizeof(double));
+}
+
+/* The Galerkin operator of one level (Eq. (2.5), reading R12) from its CSR and
+ * aggregates 0..nc-1.  The caller sizes rp_c as nc + 1 and col_c, w_c as the
+ * fine nnz (a bound on the coarse nnz).  Returns the coarse nnz. */
+int64_t orc_galerkin(int64_t n, const int64_t *rp, const int32_t *col, const double *w, const int32_t *agg,
+                     int64_t nc, int64_t *rp_c, int32_t *col_c, double *w_c) {
+    orc_level F, C;
+    memset(&F, 0, sizeof(F));
+    memset(&C, 0, sizeof(C));
+    F.n = n; F.nnz = rp[n];
+    F.rp = (int64_t *)rp; F.col = (int32_t *)col; F.w = (double *)w;
+    F.agg = (int32_t *)agg; F.nc = nc;
+    galerkin(&F, &C);
+    memcpy(rp_c, C.rp, sizeof(int64_t) * (size_t)(nc + 1));
+    memcpy(col_c, C.col, sizeof(int32_t) * (size_t)C.nnz);
+    memcpy(w_c, C.w, sizeof(double) * (size_t)C.nnz);
+    int64_t nnz = C.nnz;
+    free(C.rp); free(C.col); free(C.w);
+    return nnz;
+}
+
 /* Low-degree elimination, Sec. 3.2.  F is an independent set of nodes of
  * degree 1..4 (unweighted, |E_u|), taken by one sweep through the nodes: an
  * eligible node joins F and its neighbours become ineligible.  The paper does
@@ -942,8 +987,8 @@ static int make_coarsest(orc_level *L, const orc_opts *o) {
 /* Setup phase, Sec. 4.1: coarsen by caliber-1 aggregation until n < 150, or
  * until relaxation converges rapidly (TV energy ratio per sweep <= 0.1), or the
  * aggregation stalls (alpha > 0.9), or the depth limit. */
-int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
-                         int32_t ngraphs, const int64_t *gptr, const orc_opts *o, orc_hier **out) {
+static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                            int32_t ngraphs, const int64_t *gptr, const orc_opts *o, orc_hier **out) {
     *out = NULL;
     int32_t st = orc_validate_graphs(n, rp, col, w, ngraphs, gptr);
     if (st != ORC_OK) return st;
@@ -1038,6 +1083,15 @@ int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const
     if (st != ORC_OK) { orc_free(h); return st; }
     *out = h;
     return ORC_OK;
+}
+
+int32_t orc_setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                         int32_t ngraphs, const int64_t *gptr, const orc_opts *o, orc_hier **out) {
+    const int saved = g_plain_sums;
+    g_plain_sums = o->plain_sums != 0;
+    int32_t st = setup_graphs(n, rp, col, w, ngraphs, gptr, o, out);
+    g_plain_sums = saved;
+    return st;
 }
 
 int32_t orc_setup(int64_t n, const int64_t *rp, const int32_t *col, const double *w,

@@ -63,6 +63,9 @@ typedef struct {
                                   level; solve in flat mode with mu_flat = 2.  Default 0 */
     double   mu_adaptive;      /* restriction factor of the adaptive cycle (reading R15: 1) */
     double   gamma_coarse_max; /* cap of the cycle index at coarse levels, Eq. (4.1): 2    */
+    int32_t  plain_sums;       /* 1: every setup sum left to right from +0.0 (the plain
+                                  definition) instead of the tiered canonical order;
+                                  0 (default): the tiered order                         */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;
@@ -116,6 +119,15 @@ void     orc_level_colour(const orc_hier *h, int32_t l, int32_t *colour);
 void     orc_level_tv(const orc_hier *h, int32_t l, double *X);
 void     orc_level_scores(const orc_hier *h, int32_t l, double *aff, double *q, double *score);
 void     orc_level_agg(const orc_hier *h, int32_t l, int32_t *agg, int32_t *state, uint8_t *hub);
+/* One level's aggregation from its CSR, edge scores and hub flags (the setup's
+ * rule).  info[0..3]: nc, rounds, selected round, alpha (double bits). */
+void     orc_aggregate(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                       const double *score, const uint8_t *hub, const orc_opts *o,
+                       int32_t *agg, int32_t *state, int64_t *info);
+/* One level's Galerkin operator from its CSR and aggregates; col_c and w_c hold
+ * up to rp[n] entries.  Returns the coarse nnz. */
+int64_t  orc_galerkin(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                      const int32_t *agg, int64_t nc, int64_t *rp_c, int32_t *col_c, double *w_c);
 /* the eliminated set of a graph (Sec. 3.2, reading R20) for the sweep key `key`:
  * cidx[u] = rank of u among the kept nodes, -1 for u in F; returns |F| */
 int64_t  orc_elim_set(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key, int32_t *cidx);

@@ -605,6 +605,16 @@ def test_per_level_pieces_reproduce_the_hierarchy():
         assert np.array_equal(q.view(np.uint64), q2.view(np.uint64))
         assert np.array_equal(score.view(np.uint64), s2.view(np.uint64))
         assert np.array_equal(oracle.hubs(n, rp, col, w), h.agg(l)[2])
+        # the standalone aggregation and Galerkin step give this level's aggregates
+        # and the next level's CSR bit for bit
+        agg, state, hub = h.agg(l)
+        agg2, state2, ai = oracle.aggregate(n, rp, col, w, score, hub)
+        assert np.array_equal(agg2, agg) and np.array_equal(state2, state)
+        assert ai["nc"] == h.info(l)["nc"] and ai["alpha"] == h.info(l)["alpha"]
+        rpc, colc, wc = oracle.galerkin(n, rp, col, w, agg, ai["nc"])
+        rp1, col1, w1 = h.csr(l + 1)
+        assert np.array_equal(rpc, rp1) and np.array_equal(colc, col1)
+        assert np.array_equal(wc.view(np.uint64), w1.view(np.uint64))
 
 
 @pytest.mark.parametrize("gname", ["chung_lu", "grid"])

@@ -1,0 +1,155 @@
+"""The tiered summation order of the setup (reading R1) is an implementation
+order, not part of the method: the plain left-to-right definition gives the same
+hierarchy up to rounding.
+
+The oracle sums each setup row in tiers shaped like the GPU's thread, warp and
+block reductions.  With ``plain_sums = 1`` it sums every row left to right from
++0.0 instead.  On six graph families these checks hold level by level:
+
+- every setup float (test vectors, affinities, energy ratios, Galerkin weights)
+  of the tiered build lies within the summation error bound of the plain one;
+- colours are equal, and aggregates are equal except where a decision sits on a
+  tie that the rounding difference can flip (counted and reported);
+- the number of levels and the asymptotic convergence factor agree.
+
+Eqs. (3.5) and (3.12) define the affinity and the energy ratio, Eq. (2.5) the
+Galerkin operator; none of them fixes a summation order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+EPS = np.finfo(np.float64).eps
+
+FAMILIES = {
+    "grid2d_64": lambda: W.grid2d(64, 64),
+    "grid3d_20_aniso": lambda: W.grid3d(20, 20, 20, 1.0, 1.0, 0.01),
+    "chung_lu_20k": lambda: W.chung_lu(20_000, seed=5),
+    "rgg_10k": lambda: W.rgg2d(10_000, seed=4),
+    "er_5k": lambda: W.erdos_renyi(5_000, seed=5),
+    "knn_5k": lambda: W.knn_gmm(5_000, dim=16, k=10, seed=6)[0],
+}
+
+
+def _rel(a, b):
+    scale = max(np.max(np.abs(a)), np.max(np.abs(b)), 1e-300)
+    return float(np.max(np.abs(a - b)) / scale) if a.size else 0.0
+
+
+def _row_bound(rp):
+    """Relative error bound of the longest row sum of positive terms: (len - 1) eps."""
+    lens = np.diff(rp)
+    return float(max(lens.max(initial=1) - 1, 1) * EPS)
+
+
+def _degenerate_rows(rp, col, w, X):
+    """Rows whose energy ratio is 0/0 at rounding level (Eq. (3.12)): for some TV
+    the local minimum energy min_y E_u is below 1e-24 of the row's energy scale.
+    A degree-1 node is the usual case: exactly, E_u(x; x_s) = min_y E_u = 0 and
+    the ratio reads 1, but the computed energies are rounding noise, so their
+    ratio depends on the order of the sums."""
+    n = rp.size - 1
+    deg = np.diff(rp)
+    row = np.repeat(np.arange(n), deg)
+    a = np.zeros(n)
+    np.add.at(a, row, w)
+    Xv = X[col]
+    B = np.zeros_like(X)
+    np.add.at(B, row, w[:, None] * Xv)
+    ys = np.divide(B, a[:, None], out=np.zeros_like(B), where=a[:, None] > 0)
+    em = np.zeros_like(X)
+    np.add.at(em, row, w[:, None] * (ys[row] - Xv) ** 2)
+    sc = np.zeros_like(X)
+    np.add.at(sc, row, w[:, None] * Xv ** 2)
+    sc += a[:, None] * ys ** 2
+    return np.any(em <= 1e-24 * sc, axis=1)
+
+
+def _near_tie_nodes(rp, col, score, q, q_max, tol, degenerate):
+    """Nodes whose aggregation choice can flip under a relative perturbation of
+    `tol` in their scores or energy ratios: two admissible candidates with
+    scores within tol, an energy ratio within tol of q_max, or an energy ratio
+    that is 0/0 at rounding level (at the node or at a neighbour)."""
+    n = rp.size - 1
+    tie = degenerate.copy()
+    for u in range(n):
+        if tie[u]:
+            continue
+        s = score[rp[u]:rp[u + 1]]
+        qq = q[rp[u]:rp[u + 1]]
+        if np.any(np.abs(qq - q_max) <= tol * q_max):
+            tie[u] = True
+            continue
+        ok = np.sort(s[s >= 0.0])[::-1]
+        if ok.size >= 2 and ok[0] - ok[1] <= tol * max(ok[0], 1e-300):
+            tie[u] = True
+    return tie
+
+
+@pytest.mark.parametrize("name", list(FAMILIES))
+def test_tiered_sums_equal_the_plain_definition_up_to_rounding(name):
+    g = FAMILIES[name]()
+    ht = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    hp = oracle.Hierarchy(g.n, g.rp, g.col, g.w, plain_sums=1)
+    o = oracle.default_opts()
+    flips = 0
+    ties = 0
+    degen_total = 0
+    compared = 0
+    for l in range(min(ht.num_levels, hp.num_levels)):
+        it, ip = ht.info(l), hp.info(l)
+        rpt, colt, wt = ht.csr(l)
+        rpp, colp, wp = hp.csr(l)
+        assert np.array_equal(rpt, rpp) and np.array_equal(colt, colp), f"level {l}: coarse pattern"
+        # Galerkin weights: canonical sums of <= row-length positive terms
+        bound = 4 * _row_bound(rpt) * max(1, l)
+        assert _rel(wt, wp) <= max(bound, 64 * EPS), f"level {l}: weights {_rel(wt, wp)}"
+        assert np.array_equal(ht.colour(l), hp.colour(l)), f"level {l}: colours"
+        if it["coarsest"] or ip["coarsest"] or it["elim"]:
+            break
+        # test vectors: nu_tv GS sweeps, each row sum within its bound
+        Xt, Xp = ht.tv(l), hp.tv(l)
+        assert _rel(Xt, Xp) <= 1e-10, f"level {l}: TVs {_rel(Xt, Xp)}"
+        at, qt, st = ht.scores(l)
+        ap, qp, sp = hp.scores(l)
+        assert _rel(at, ap) <= 1e-8, f"level {l}: affinity"
+        n = rpt.size - 1
+        row = np.repeat(np.arange(n), np.diff(rpt))
+        degen = _degenerate_rows(rpt, colt, wt, Xt)
+        degen_total += int(degen.sum())
+        ok = ~degen[row]
+        assert np.array_equal(np.isfinite(qt[ok]), np.isfinite(qp[ok]))
+        fin = ok & np.isfinite(qt) & np.isfinite(qp)
+        assert np.all(np.abs(qt[fin] - qp[fin]) <= 1e-8 * np.maximum(qt[fin], 1.0)), f"level {l}: q"
+        aggt, statet, hubt = ht.agg(l)
+        aggp, statep, hubp = hp.agg(l)
+        assert np.array_equal(hubt, hubp), f"level {l}: hubs"
+        compared += 1
+        tie = _near_tie_nodes(rpt, colt, st, qt, o.q_max, 1e-8, degen)
+        ties += int(tie.sum())
+        if not np.array_equal(aggt, aggp):
+            # A flipped decision must come from a near-tie: the plain scores with
+            # the tied rows' scores taken from the tiered build give back the
+            # tiered aggregates.  Later levels then differ, so the walk stops.
+            assert tie.any(), f"level {l}: aggregates differ without a near-tie"
+            mix = sp.copy()
+            mix[tie[row]] = st[tie[row]]
+            aggm, _, _ = oracle.aggregate(n, rpt, colt, wt, mix, hubt)
+            assert np.array_equal(aggm, aggt), f"level {l}: a flip not explained by the near-ties"
+            flips += int(np.sum(statet != statep))
+            break
+    assert compared >= 1
+    # levels and convergence agree
+    b = W.zero_sum_rhs(g.n, 1)
+    _, hist_t = ht.solve(b, tol=1e-8, max_cycles=300)
+    _, hist_p = hp.solve(b, tol=1e-8, max_cycles=300)
+    acf_t = (hist_t[-1] / hist_t[0]) ** (1.0 / (len(hist_t) - 1))
+    acf_p = (hist_p[-1] / hist_p[0]) ** (1.0 / (len(hist_p) - 1))
+    print(f"{name}: levels {ht.num_levels}/{hp.num_levels}, cycles {len(hist_t) - 1}/{len(hist_p) - 1}, "
+          f"ACF {acf_t:.4f}/{acf_p:.4f}, near-tie nodes {ties} (0/0 energy ratios {degen_total}), "
+          f"flipped states {flips}")
+    assert abs(ht.num_levels - hp.num_levels) <= (0 if flips == 0 else 2)
+    assert abs(len(hist_t) - len(hist_p)) <= (0 if flips == 0 else 2)
+    assert abs(acf_t - acf_p) <= (1e-6 if flips == 0 else 0.05)
