@@ -62,6 +62,10 @@ typedef enum { LAMG_FP64 = 0, LAMG_FP32_IR = 1 } lamg_precision;
 /* Parameters of Sec. 4; lamg_default_options fills the paper's values and the
  * build's readings of the points the paper leaves open. */
 typedef struct {
+    int32_t  struct_size;      /* sizeof(lamg_options), set by lamg_default_options;
+                                  lamg_setup rejects any other value with LAMG_ERR_ARG,
+                                  so a caller built against another layout of this
+                                  struct fails instead of passing misread fields       */
     double   gamma;            /* cycle index (Sec. 4.1): 1.5                          */
     int32_t  k_finest;         /* TVs at the finest level (Sec. 4.1): 4                 */
     int32_t  k_max;            /* TVs grow up to this at coarse levels: 10 (max 16)     */
@@ -114,6 +118,25 @@ typedef struct {
                                   level; the paper's setting solves with adaptive = 0 and
                                   mu_flat = 2.  Coarsening stops below n_coarsest nodes or
                                   at an odd side or a side below 6.  Default 0           */
+    int32_t  agg_rule;         /* aggregation stages (Sec. 3.4.2):
+                                  2 (default): the paper's scan, visiting the undecided
+                                  nodes in decreasing priority splitmix64(key_l + u)
+                                  (ties to the lower index), at most two stages; the
+                                  GPU runs it in parallel rounds that reproduce the
+                                  sequential scan exactly;
+                                  1: the same scan in node-index order, the paper's
+                                  sequential form (deeper rounds on grids);
+                                  0: the parallel handshake of mutual best neighbours  */
+    int32_t  recomb_finest;    /* 1 (default): the adaptive cycle also recombines the
+                                  iterates of the finest level (Eq. (3.13)), so that
+                                  its coarse correction is energy-corrected too;
+                                  0: recombination below the finest level only       */
+    int32_t  relax_rule;       /* 0 (default): multicolour Gauss-Seidel on the JP
+                                  colouring; 1: lexicographic Gauss-Seidel (Eq. (2.3))
+                                  exactly, swept as the level sets of the lower-
+                                  triangular dependency graph (colour[u] = 1 + the
+                                  largest colour of a lower-index neighbour), for the
+                                  TV sweeps and the cycle alike                      */
 } lamg_options;
 
 typedef struct {

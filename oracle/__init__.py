@@ -44,7 +44,9 @@ class Opts(C.Structure):
                 ("dense_max", C.c_int32), ("coarse_sweeps", C.c_int32),
                 ("mu_flat", C.c_double), ("seed", C.c_uint64), ("agg_rule", C.c_int32),
                 ("elim", C.c_int32), ("elim_min_frac", C.c_double), ("lgmg_nx", C.c_int32),
-                ("mu_adaptive", C.c_double), ("gamma_coarse_max", C.c_double), ("plain_sums", C.c_int32)]
+                ("mu_adaptive", C.c_double), ("gamma_coarse_max", C.c_double), ("plain_sums", C.c_int32),
+                ("gamma_fine_printed", C.c_int32), ("recomb_finest", C.c_int32),
+                ("relax_rule", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -66,6 +68,7 @@ def lib():
                 "orc_validate_graphs": (_I32, [_I64, _P, _P, _P, _I32, _P]),
                 "orc_laplacian_dense": (None, [_I64, _P, _P, _P, _P]),
                 "orc_colour": (_I32, [_I64, _P, _P, _U64, _P]),
+                "orc_colour_lex": (_I32, [_I64, _P, _P, _P]),
                 "orc_gs_sweep_lex": (None, [_I64, _P, _P, _P, _P, _P]),
                 "orc_gs_sweep_colour": (None, [_I64, _P, _P, _P, _P, _I32, _P, _P]),
                 "orc_edge_scores": (None, [_I64, _P, _P, _P, _I32, _P, _D, _D, _P, _P, _P]),
@@ -83,7 +86,7 @@ def lib():
                 "orc_level_agg": (None, [_P, _I32, _P, _P, _P]),
                 "orc_level_elim": (None, [_P, _I32, _P]),
                 "orc_elim_set": (_I64, [_I64, _P, _P, _U64, _P]),
-                "orc_aggregate": (None, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+                "orc_aggregate": (None, [_I64, _P, _P, _P, _P, _P, _P, _I32, _P, _P, _P]),
                 "orc_galerkin": (_I64, [_I64, _P, _P, _P, _P, _I64, _P, _P, _P]),
                 "orc_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _P, _P]),
                 "orc_cycle": (_I32, [_P, _P, _P, _I32]),
@@ -155,6 +158,15 @@ def colour(n, rp, col, key):
     return c, int(nc)
 
 
+def colour_lex(n, rp, col):
+    """Level sets of the lower-triangular dependency graph (relax_rule 1)."""
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    c = np.zeros(n, dtype=np.int32)
+    nc = lib().orc_colour_lex(n, _p(rp), _p(col), _p(c))
+    return c, int(nc)
+
+
 def elim_set(n, rp, col, key):
     """Eliminated set of a graph (Sec. 3.2): coarse index of each node, -1 in F."""
     rp = np.ascontiguousarray(rp, dtype=np.int64)
@@ -164,7 +176,7 @@ def elim_set(n, rp, col, key):
     return cidx, int(nF)
 
 
-def aggregate(n, rp, col, w, score, hub, opts: Opts | None = None, **kw):
+def aggregate(n, rp, col, w, score, hub, level=0, opts: Opts | None = None, **kw):
     """One level's aggregation (Sec. 3.4.1-3.4.2, the setup's rule) from its CSR,
     edge scores and hub flags: (agg, state, info) with info = nc, rounds,
     selected round, alpha."""
@@ -174,7 +186,7 @@ def aggregate(n, rp, col, w, score, hub, opts: Opts | None = None, **kw):
     hub = np.ascontiguousarray(hub, dtype=np.uint8)
     agg, state = np.zeros(n, np.int32), np.zeros(n, np.int32)
     info = np.zeros(4, np.int64)
-    lib().orc_aggregate(n, _p(rp), _p(col), _p(w), _p(score), _p(hub), C.byref(o), _p(agg), _p(state), _p(info))
+    lib().orc_aggregate(n, _p(rp), _p(col), _p(w), _p(score), _p(hub), C.byref(o), level, _p(agg), _p(state), _p(info))
     return agg, state, dict(nc=int(info[0]), rounds=int(info[1]), sel_round=int(info[2]),
                             alpha=float(info[3:4].view(np.float64)[0]))
 

@@ -37,13 +37,16 @@ void orc_default_opts(orc_opts *o) {
     o->coarse_sweeps = 5;
     o->mu_flat = 4.0 / 3.0;    /* Eq. (3.10) with Q = 2 */
     o->seed = 1;
-    o->agg_rule = 0;           /* parallel handshake */
+    o->agg_rule = 2;           /* the paper's scan (Sec. 3.4.2) in hashed priority order */
     o->elim = 0;               /* no elimination levels (as the library) */
     o->elim_min_frac = 0.1;    /* reading of "until |F| becomes small", Sec. 3.2 */
     o->lgmg_nx = 0;            /* algebraic coarsening */
     o->mu_adaptive = 1.0;      /* reading R15: recombination replaces the flat correction */
     o->gamma_coarse_max = 2.0; /* Eq. (4.1): min{2, ...} at coarse levels */
     o->plain_sums = 0;         /* the tiered canonical order of the setup sums */
+    o->gamma_fine_printed = 0; /* reading R13: the fine-level index is bounded too */
+    o->recomb_finest = 1;      /* reading R15: recombination at the finest level too */
+    o->relax_rule = 0;         /* multicolour GS on the JP colouring (reading R2) */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -68,6 +71,11 @@ static uint64_t tv_key(uint64_t seed, int32_t level) {
 /* elimination scan order: the colour key's form with the top bit set */
 static uint64_t elim_key(uint64_t seed, int32_t level) {
     return orc_splitmix64(orc_splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 1)) ^ (1ULL << 63));
+}
+
+/* aggregation scan order (agg_rule 2): the TV key's form with the top bit set */
+static uint64_t agg_key(uint64_t seed, int32_t level) {
+    return orc_splitmix64(orc_splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 2)) ^ (1ULL << 63));
 }
 
 /* TV initial value "random[-1,1]" (Sec. 3.3.1): the top 53 bits of the draw as a
@@ -608,7 +616,15 @@ static double relax_tvs(orc_level *L, const orc_opts *o, int32_t level) {
  * the largest score (the smallest c_uv among those with q_uv <= 2.5, Sec.
  * 3.4.5); an undecided v thereby becomes a seed.  At most two stages are run,
  * as in the paper; the selection and the numbering are the same. */
-static void aggregate(orc_level *L, const orc_opts *o) {
+typedef struct { uint64_t p; int64_t u; } scan_prio;
+
+static int scan_prio_cmp(const void *a, const void *b) {
+    const scan_prio *x = (const scan_prio *)a, *y = (const scan_prio *)b;
+    if (x->p != y->p) return x->p > y->p ? -1 : 1;
+    return x->u < y->u ? -1 : (x->u > y->u);
+}
+
+static void aggregate(orc_level *L, const orc_opts *o, uint64_t key) {
     int64_t n = L->n;
     int32_t *state = L->state;
     int32_t *seed = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
@@ -637,11 +653,25 @@ static void aggregate(orc_level *L, const orc_opts *o) {
     }
     double amax = 0.7 / o->gamma;
     double best_alpha = INFINITY; int32_t best_round = 0, r;
-    const int32_t max_stages = o->agg_rule == 1 ? (o->max_rounds < 2 ? o->max_rounds : 2) : o->max_rounds;
+    const int32_t max_stages = o->agg_rule >= 1 ? (o->max_rounds < 2 ? o->max_rounds : 2) : o->max_rounds;
+    int64_t *order = NULL;
+    if (o->agg_rule >= 1) {
+        order = (int64_t *)xcalloc((size_t)n, sizeof(int64_t));
+        if (o->agg_rule == 2) {
+            scan_prio *sp = (scan_prio *)xcalloc((size_t)n, sizeof(scan_prio));
+            for (int64_t u = 0; u < n; u++) { sp[u].p = orc_splitmix64(key + (uint64_t)u); sp[u].u = u; }
+            qsort(sp, (size_t)n, sizeof(scan_prio), scan_prio_cmp);
+            for (int64_t i = 0; i < n; i++) order[i] = sp[i].u;
+            free(sp);
+        } else {
+            for (int64_t i = 0; i < n; i++) order[i] = i;
+        }
+    }
     for (r = 1; r <= max_stages; r++) {
         int changed = 0;
-        if (o->agg_rule == 1) {
-            for (int64_t u = 0; u < n; u++) {
+        if (o->agg_rule >= 1) {
+            for (int64_t i = 0; i < n; i++) {
+                const int64_t u = order[i];
                 if (state[u] != ST_U) continue;
                 int32_t bv = -1;
                 double bs = -1.0;
@@ -693,6 +723,7 @@ static void aggregate(orc_level *L, const orc_opts *o) {
         }
         if (alpha <= amax || !changed) break;
     }
+    free(order);
     L->rounds = r > max_stages ? max_stages : r;
     L->sel_round = best_round;
     L->alpha = best_alpha;
@@ -763,14 +794,15 @@ static void galerkin(const orc_level *F, orc_level *C) {
  * (Sec. 3.4.1-3.4.2 with readings R9-R11), as the setup runs it.
  * info[0..3] = nc, rounds, selected round, alpha (double bits). */
 void orc_aggregate(int64_t n, const int64_t *rp, const int32_t *col, const double *w, const double *score,
-                   const uint8_t *hub, const orc_opts *o, int32_t *agg, int32_t *state, int64_t *info) {
+                   const uint8_t *hub, const orc_opts *o, int32_t level, int32_t *agg, int32_t *state,
+                   int64_t *info) {
     orc_level L;
     memset(&L, 0, sizeof(L));
     L.n = n; L.nnz = rp[n];
     L.rp = (int64_t *)rp; L.col = (int32_t *)col; L.w = (double *)w;
     L.score = (double *)score; L.hub = (uint8_t *)hub;
     L.agg = agg; L.state = state;
-    aggregate(&L, o);
+    aggregate(&L, o, agg_key(o->seed, level));
     info[0] = L.nc; info[1] = L.rounds; info[2] = L.sel_round;
     memcpy(&info[3], &L.alpha, sizeof(double));
 }
@@ -931,6 +963,7 @@ static void cycle_indices(orc_hier *h) {
         double gmax = ml > 0.1 * m1 ? h->o.gamma : h->o.gamma_coarse_max;
         if (g > gmax) g = gmax;
         if (g < 1.0) g = 1.0;
+        if (h->o.gamma_fine_printed && ml > 0.1 * m1) g = h->o.gamma;   /* Eq. (4.1) as printed */
         h->lv[l].gamma_l = g;
     }
     h->lv[h->L - 1].gamma_l = 0.0;
@@ -951,9 +984,31 @@ static void level_diag(orc_level *L) {
 
 /* The JP colouring of a level that relaxes.  A level followed by elimination
  * never relaxes (Sec. 4.2: nu = 0 there), so it gets one colour, 0, instead. */
-static void level_colour(orc_level *L, uint64_t seed, int32_t level, int relaxes) {
+/* Lexicographic Gauss-Seidel (Eq. (2.3)) as a colour-ordered sweep: colour[u] =
+ * 1 + the largest colour of a lower-index neighbour (0 if none), the level sets of
+ * the lower-triangular dependency graph.  Neighbours never share a colour, every
+ * lower-index neighbour of u has a smaller colour and every higher-index one a
+ * larger colour, so sweeping the colours in order updates each node from the new
+ * values of its lower-index neighbours and the old values of the others: the
+ * lexicographic sweep exactly.  Returns the number of colours. */
+int32_t orc_colour_lex(int64_t n, const int64_t *rp, const int32_t *col, int32_t *colour) {
+    int32_t nc = 0;
+    for (int64_t u = 0; u < n; u++) {
+        int32_t c = 0;
+        for (int64_t e = rp[u]; e < rp[u + 1]; e++)
+            if (col[e] < u && colour[col[e]] + 1 > c) c = colour[col[e]] + 1;
+        colour[u] = c;
+        if (c + 1 > nc) nc = c + 1;
+    }
+    return nc;
+}
+
+static void level_colour(orc_level *L, uint64_t seed, int32_t level, int relaxes, int32_t relax_rule) {
     L->colour = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
-    if (relaxes) {
+    if (relaxes && relax_rule == 1) {
+        L->ncolours = orc_colour_lex(L->n, L->rp, L->col, L->colour);
+        L->jp_rounds = 0;
+    } else if (relaxes) {
         L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), L->colour, &L->jp_rounds);
     } else {
         L->ncolours = 1;
@@ -1015,7 +1070,7 @@ static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
         h->L = l + 1;
         if (L->n < o->n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
             if (nxl > 0) level_colour_rb(L, nxl);
-            else level_colour(L, o->seed, l, 1);
+            else level_colour(L, o->seed, l, 1, o->relax_rule);
             L->stop_reason = L->n < o->n_coarsest ? 1 : 4;
             st = make_coarsest(L, o);
             break;
@@ -1038,7 +1093,7 @@ static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
             int32_t *cidx = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
             int64_t nF = elim_select(L, elim_key(o->seed, l), cidx);
             if (nF >= 1 && (double)nF >= o->elim_min_frac * (double)L->n) {
-                level_colour(L, o->seed, l, 0);
+                level_colour(L, o->seed, l, 0, o->relax_rule);
                 L->elim = 1;
                 L->nF = nF;
                 L->cidx = cidx;
@@ -1048,7 +1103,7 @@ static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
             }
             free(cidx);
         }
-        level_colour(L, o->seed, l, 1);
+        level_colour(L, o->seed, l, 1, o->relax_rule);
         int32_t K = o->k_finest + o->k_step * nagg;
         if (K > o->k_max) K = o->k_max;
         if (K > 16) K = 16;
@@ -1070,7 +1125,7 @@ static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
         orc_hubs(L->n, L->rp, L->col, L->w, o->hub_factor, L->hub);
         L->state = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
         L->agg = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
-        aggregate(L, o);
+        aggregate(L, o, agg_key(o->seed, l));
         if (L->alpha > o->alpha_stall) {
             L->stop_reason = 3;
             st = make_coarsest(L, o);
@@ -1293,7 +1348,7 @@ static void visit(solve_ctx *c, int32_t l, int theta) {
     const orc_opts *o = &h->o;
     int64_t n = F->n;
     double *x = c->x[l], *b = c->b[l], *r = c->r[l];
-    int recomb = c->adaptive && l >= 1;
+    int recomb = c->adaptive && (l >= 1 || h->o.recomb_finest);
     double *xs[2] = {NULL, NULL}, *rs[2] = {NULL, NULL};
     for (int i = 0; i < theta; i++) {
         for (int s = 0; s < o->nu1; s++) relax(F, b, x);

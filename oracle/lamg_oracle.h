@@ -50,9 +50,12 @@ typedef struct {
     int32_t  coarse_sweeps;    /* GS sweeps when the coarsest level is too large     */
     double   mu_flat;          /* flat energy correction, Eq. (3.9) (4/3)            */
     uint64_t seed;             /* seed of the counter-based generator                */
-    int32_t  agg_rule;         /* 0: the parallel handshake (the library's rule);
-                                  1: the paper's sequential scan, Sec. 3.4.2, at most
-                                  two stages (a quality reference; no GPU counterpart) */
+    int32_t  agg_rule;         /* the aggregation stages (Sec. 3.4.2):
+                                  0: the parallel handshake (reading R9);
+                                  1: the paper's sequential scan in node-index order;
+                                  2 (default): the same scan in decreasing hashed
+                                  priority order (reading R9); at most two stages
+                                  for 1 and 2                                         */
     int32_t  elim;             /* 1: low-degree elimination levels before each
                                   aggregation, Sec. 3.2 (default 0: none, as the library) */
     double   elim_min_frac;    /* an elimination round is kept only if it removes at
@@ -66,6 +69,13 @@ typedef struct {
     int32_t  plain_sums;       /* 1: every setup sum left to right from +0.0 (the plain
                                   definition) instead of the tiered canonical order;
                                   0 (default): the tiered order                         */
+    int32_t  gamma_fine_printed; /* 1: gamma^l = gamma wherever |E^l| > .1|E| (Eq. (4.1) as
+                                  printed); 0 (default): bounded there as at coarse levels */
+    int32_t  recomb_finest;    /* 1 (default): the adaptive cycle recombines at the finest
+                                  level too (reading R15); 0: below the finest level only */
+    int32_t  relax_rule;       /* 0 (default): multicolour GS on the JP colouring (R2);
+                                  1: lexicographic GS (Eq. (2.3)), swept as the level
+                                  sets of the lower-triangular dependency graph       */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;
@@ -90,6 +100,8 @@ void     orc_laplacian_dense(int64_t n, const int64_t *rp, const int32_t *col, c
                              double *A /* n*n row-major */);
 int32_t  orc_colour(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key,
                     int32_t *colour /* out n */);
+/* the lexicographic order's level sets (relax_rule 1): returns the colour count */
+int32_t  orc_colour_lex(int64_t n, const int64_t *rp, const int32_t *col, int32_t *colour /* out n */);
 void     orc_gs_sweep_lex(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
                           const double *b, double *x);
 void     orc_gs_sweep_colour(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
@@ -122,7 +134,7 @@ void     orc_level_agg(const orc_hier *h, int32_t l, int32_t *agg, int32_t *stat
 /* One level's aggregation from its CSR, edge scores and hub flags (the setup's
  * rule).  info[0..3]: nc, rounds, selected round, alpha (double bits). */
 void     orc_aggregate(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
-                       const double *score, const uint8_t *hub, const orc_opts *o,
+                       const double *score, const uint8_t *hub, const orc_opts *o, int32_t level,
                        int32_t *agg, int32_t *state, int64_t *info);
 /* One level's Galerkin operator from its CSR and aggregates; col_c and w_c hold
  * up to rp[n] entries.  Returns the coarse nnz. */

@@ -99,6 +99,7 @@ extern "C" {
 void lamg_default_options(lamg_options *o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
+    o->struct_size = (int32_t)sizeof(lamg_options);
     o->gamma = 1.5;
     o->k_finest = 4;
     o->k_max = 10;
@@ -129,6 +130,9 @@ void lamg_default_options(lamg_options *o) {
     o->elim = 0;
     o->elim_min_frac = 0.1;
     o->lgmg_nx = 0;
+    o->agg_rule = 2;
+    o->recomb_finest = 1;
+    o->relax_rule = 0;
 }
 
 const char *lamg_last_error(void) { return g_last_error.c_str(); }
@@ -150,10 +154,15 @@ static lamg_status setup_impl(int32_t ngraphs, const int64_t *graph_ptr, int64_t
         // the options are checked before anything is allocated
         lamg_options o;
         if (opt) o = *opt; else lamg_default_options(&o);
+        LAMG_REQUIRE(o.struct_size == (int32_t)sizeof(lamg_options), LAMG_ERR_ARG,
+                     "lamg_options.struct_size does not match this library (fill it with lamg_default_options)");
         LAMG_REQUIRE(o.gamma >= 1.0 && o.nu_tv >= 0 && o.nu1 >= 0 && o.nu2 >= 0 && o.k_finest >= 1 &&
                          o.max_rounds >= 1 && o.max_levels >= 1 && o.dense_max >= 1 &&
                          o.gamma_coarse_max >= 1.0 && o.gamma_coarse_max <= 2.0 &&
-                         o.mu_adaptive > 0.0 && o.mu_adaptive < 4.0,
+                         o.mu_adaptive > 0.0 && o.mu_adaptive < 4.0 && o.mu_flat > 0.0 && o.mu_flat < 4.0 &&
+                         o.q_max > 0.0 && o.n_coarsest >= 1 && o.coarse_sweeps >= 0 &&
+                         o.agg_rule >= 0 && o.agg_rule <= 2 && (o.recomb_finest == 0 || o.recomb_finest == 1) &&
+                         (o.relax_rule == 0 || o.relax_rule == 1),
                      LAMG_ERR_ARG, "invalid options");
         auto t0 = std::chrono::steady_clock::now();
         h = new lamg_ctx();

@@ -725,7 +725,7 @@ static void alloc_vecs4(lamg_ctx *h, std::vector<LevelVecs<T>> &vv, int ld) {
         vv[l].x.alloc(n);
         vv[l].b.alloc(n);
         vv[l].r.alloc(n);
-        if (l >= 1 && l + 1 < h->L) {
+        if ((l >= 1 || h->opt.recomb_finest) && l + 1 < h->L) {
             vv[l].xs0.alloc(n); vv[l].xs1.alloc(n);
             vv[l].rs0.alloc(n); vv[l].rs1.alloc(n);
         }

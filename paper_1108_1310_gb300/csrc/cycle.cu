@@ -610,7 +610,7 @@ struct Builder {
             }
             return;
         }
-        const bool recomb = adaptive && l >= 1;
+        const bool recomb = adaptive && (l >= 1 || h->opt.recomb_finest);
         for (int i = 0; i < theta; i++) {
             sweeps(l, h->opt.nu1);
             emit(OP_RESID, l, recomb ? i : -1, 0, sb);

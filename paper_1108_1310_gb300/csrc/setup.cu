@@ -72,6 +72,10 @@ static uint64_t tv_key(uint64_t seed, int level) {
 static uint64_t elim_key(uint64_t seed, int level) {
     return splitmix64(splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 1)) ^ (1ULL << 63));
 }
+// aggregation scan order (agg_rule 2): the TV key's form with the top bit set
+static uint64_t agg_key(uint64_t seed, int level) {
+    return splitmix64(splitmix64(seed) ^ (0x100000000ULL * (uint64_t)(2 * level + 2)) ^ (1ULL << 63));
+}
 
 // ---------------------------------------------------------------------------
 // Tier helpers
@@ -1241,6 +1245,151 @@ __global__ void k_resolve(int32_t n, const int32_t *__restrict__ state, const in
     }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's aggregation scan (Sec. 3.4.2; agg_rule 1 and 2).  One stage visits
+// the undecided nodes in the order of rank (0 first); a node u that is still
+// undecided at its turn joins its best admissible neighbour that is a seed or
+// undecided (the largest score; an undecided one becomes a seed).  Parallel
+// rounds reproduce the sequential stage exactly.  A node is active while it is
+// undecided and has not had its turn.  u decides in a round when no active node
+// of smaller rank is a neighbour of u or a neighbour of an undecided neighbour of
+// u: only such nodes can change the states that u reads (its own, its
+// neighbours'), and states S, A and D never change again.  Nodes deciding in the
+// same round are then at least three edges apart, or share only seeds, so their
+// decisions commute.
+// ---------------------------------------------------------------------------
+
+constexpr int32_t kRankNone = 0x7fffffff;
+
+// (a, b): the two smallest ranks seen, a < b
+__device__ __forceinline__ void min2_merge(int32_t &a, int32_t &b, int32_t oa, int32_t ob) {
+    const int32_t lo = min(a, oa), hi = max(a, oa);
+    b = min(hi, min(b, ob));
+    a = lo;
+}
+
+template <int M>
+__device__ __forceinline__ void reduce_min2(int32_t &a, int32_t &b) {
+    if (M == M_THR) return;
+    for (int o = 16; o; o >>= 1) {
+        const int32_t oa = __shfl_xor_sync(kFull, a, o), ob = __shfl_xor_sync(kFull, b, o);
+        min2_merge(a, b, oa, ob);
+    }
+    if (M == M_WARP) return;
+    __shared__ int32_t ra[32], rb[32];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { ra[threadIdx.x >> 5] = a; rb[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        a = ra[threadIdx.x];
+        b = rb[threadIdx.x];
+        for (int o = 16; o; o >>= 1) {
+            const int32_t oa = __shfl_xor_sync(kFull, a, o), ob = __shfl_xor_sync(kFull, b, o);
+            min2_merge(a, b, oa, ob);
+        }
+        if (threadIdx.x == 0) { ra[0] = a; rb[0] = b; }
+    }
+    __syncthreads();
+    a = ra[0];
+    b = rb[0];
+}
+
+// rank of each node in the scan order: by decreasing splitmix64(key + u), ties to
+// the lower index (keys ~hash sorted ascending by a stable sort of u = 0..n-1)
+__global__ void k_scan_keys(int32_t n, uint64_t key, uint64_t *__restrict__ keys, int32_t *__restrict__ idx) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    keys[u] = ~splitmix64(key + (uint64_t)u);
+    idx[u] = u;
+}
+__global__ void k_scan_rank(int32_t n, const int32_t *__restrict__ order, int32_t *__restrict__ rank) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rank[order[i]] = i;
+}
+__global__ void k_iota(int32_t n, int32_t *__restrict__ a) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+__global__ void k_scan_stage_init(int32_t n, const int32_t *__restrict__ state, uint8_t *__restrict__ done) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) done[u] = state[u] != ST_U ? 1 : 0;
+}
+
+// per undecided node v: the two smallest ranks among its active neighbours
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_scan_top2(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const int32_t *__restrict__ rank, const int32_t *__restrict__ state,
+                            const uint8_t *__restrict__ done, int32_t *__restrict__ r1,
+                            int32_t *__restrict__ r2) {
+    int32_t v;
+    if (!get_row<M>(n, list, nlist, v)) return;
+    const int32_t s = rp[v], e = rp[v + 1];
+    if (M == M_THR && e - s > kLongRow) return;
+    if (state[v] != ST_U) return;   // read only for undecided v
+    int32_t a = kRankNone, b = kRankNone;
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
+        const int32_t w = col[j];
+        if (state[w] == ST_U && !done[w]) min2_merge(a, b, rank[w], kRankNone);
+    }
+    reduce_min2<M>(a, b);
+    if (tlane<M>() == 0) { r1[v] = a; r2[v] = b; }
+}
+
+// per active node u: whether it decides this round, and its decision:
+// dec[u] = -2 (waits, or not active), -1 (no admissible neighbour), else the seed
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_scan_decide(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+                              const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const double *__restrict__ score, const int32_t *__restrict__ rank,
+                              const int32_t *__restrict__ state, const uint8_t *__restrict__ done,
+                              const int32_t *__restrict__ r1, const int32_t *__restrict__ r2,
+                              int32_t *__restrict__ dec, int32_t *__restrict__ waiting) {
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
+    const int32_t s = rp[u], e = rp[u + 1];
+    if (M == M_THR && e - s > kLongRow) return;
+    if (state[u] != ST_U || done[u]) {
+        if (tlane<M>() == 0) dec[u] = -2;
+        return;
+    }
+    const int32_t ru = rank[u];
+    bool blocked = false;
+    double bs = -1.0;
+    int32_t bv = -1;
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
+        const int32_t v = col[j];
+        const int32_t sv = state[v];
+        if (sv == ST_U) {
+            if (!done[v] && rank[v] < ru) blocked = true;
+            const int32_t m = r1[v] == ru ? r2[v] : r1[v];
+            if (m < ru) blocked = true;
+        }
+        const double sc = score[j];
+        if (sc >= 0.0 && (sv == ST_U || sv == ST_S)) best_merge(bs, bv, sc, v);
+    }
+    blocked = reduce_any<M>(blocked);
+    bv = reduce_best<M>(bs, bv);
+    if (tlane<M>() == 0) {
+        dec[u] = blocked ? -2 : bv;
+        if (blocked) atomicAdd(waiting, 1);
+    }
+}
+
+__global__ void k_scan_apply(int32_t n, const int32_t *__restrict__ dec, int32_t *__restrict__ state,
+                             uint8_t *__restrict__ done, int32_t *__restrict__ seed, int32_t *changed) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int32_t d = dec[u];
+    if (d == -2) return;
+    done[u] = 1;
+    if (d < 0) return;
+    state[d] = ST_S;
+    state[u] = ST_A;
+    seed[u] = d;
+    *changed = 1;
+}
+
 __global__ void k_count_su(const int32_t *__restrict__ state, int32_t n, unsigned long long *out) {
     const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long c = 0;
@@ -1480,6 +1629,57 @@ __global__ void k_geo_agg(int32_t n, int32_t nx, int32_t *__restrict__ agg, int3
     state[u] = 0;
 }
 
+// Lexicographic Gauss-Seidel as a colour-ordered sweep (relax_rule 1): colour[u] =
+// 1 + the largest colour of a lower-index neighbour, the level sets of the lower-
+// triangular dependency graph, found by peeling: wait[u] counts the lower-index
+// neighbours not yet coloured; round r colours the frontier (wait 0) with r and
+// releases their higher-index neighbours.  Colours do not depend on the order in
+// which a round's frontier is listed.
+__global__ void k_lex_wait(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           int32_t *__restrict__ wait, uint8_t *__restrict__ ready) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int32_t c = 0;
+    for (int32_t j = rp[u]; j < rp[u + 1]; j++) c += col[j] < u ? 1 : 0;
+    wait[u] = c;
+    ready[u] = c == 0 ? 1 : 0;
+}
+__global__ void k_lex_round(const int32_t *__restrict__ front, int32_t nf, int32_t r,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            int32_t *__restrict__ wait, int32_t *__restrict__ colour,
+                            int32_t *__restrict__ next, int32_t *__restrict__ nnext) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const int32_t u = front[i];
+    colour[u] = r;
+    for (int32_t j = rp[u]; j < rp[u + 1]; j++) {
+        const int32_t v = col[j];
+        if (v > u && atomicSub(&wait[v], 1) == 1) next[atomicAdd(nnext, 1)] = v;
+    }
+}
+
+static void colour_lex(SetupLevel &L, cudaStream_t s) {
+    const int32_t n = L.n;
+    Tmp<int32_t> wait(n, s), fa(n, s), fb(n, s), cnt(1, s);
+    Tmp<uint8_t> ready(n, s);
+    k_lex_wait<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), L.col.get(), wait.get(), ready.get());
+    LAMG_CHECK_LAUNCH();
+    int32_t nf = (int32_t)compact_indices(ready.get(), fa.get(), n, s);
+    int32_t *cur = fa.get(), *nxt = fb.get();
+    int64_t done = 0;
+    for (int32_t r = 0; nf > 0; r++) {
+        done += nf;
+        LAMG_REQUIRE(done <= n, LAMG_ERR_CUDA, "lexicographic colouring: frontier overran the level");
+        LAMG_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
+        k_lex_round<<<ceil_div(nf, 256), 256, 0, s>>>(cur, nf, r, L.rp.get(), L.col.get(), wait.get(),
+                                                       L.colour.get(), nxt, cnt.get());
+        LAMG_CHECK_LAUNCH();
+        nf = read_scalar(cnt.get(), s);
+        std::swap(cur, nxt);
+    }
+    LAMG_REQUIRE(done == n, LAMG_ERR_CUDA, "lexicographic colouring: some nodes were never released");
+}
+
 // The JP colouring of a level that relaxes, and the (colour, tier, id) order of
 // its nodes.  A level followed by elimination never relaxes (nu = 0, Sec. 4.2):
 // it gets one colour, 0, and only the order.  rb_nx > 0: red-black colours of an
@@ -1495,6 +1695,8 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
     if (relaxes && rb_nx > 0) {
         k_rb_colour<<<ceil_div(n, 256), 256, 0, s>>>(n, rb_nx, L.colour.get());
         LAMG_CHECK_LAUNCH();
+    } else if (relaxes && h->opt.relax_rule == 1) {
+        colour_lex(L, s);
     } else if (relaxes) {
         const uint64_t key = colour_key(h->opt.seed, level);
         PhaseTimer ct(s);
@@ -1718,8 +1920,8 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, c
 }
 
 // Aggregation of one level; fills L.agg, L.state, L.nc, L.alpha, L.rounds, L.sel_round.
-static void aggregate_level(lamg_ctx *h, SetupLevel &L, const Tiers &T, const double *score, const double *maxw,
-                            cudaStream_t s) {
+static void aggregate_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, const double *score,
+                            const double *maxw, cudaStream_t s) {
     const int32_t n = L.n;
     const lamg_options &o = h->opt;
     Tmp<int32_t> state(n, s), seed(n, s), best(n, s), nstate(n, s), nseed(n, s), bseed(n, s);
@@ -1734,17 +1936,56 @@ static void aggregate_level(lamg_ctx *h, SetupLevel &L, const Tiers &T, const do
     int best_round = 0, r;
     Tmp<int32_t> changed(1, s);
     Tmp<unsigned long long> cnt(1, s);
-    for (r = 1; r <= o.max_rounds; r++) {
-        LAUNCH3(k_best, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
-                score, state.get(), best.get());
-        LAMG_CUDA(cudaMemcpyAsync(nstate.get(), state.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        LAMG_CUDA(cudaMemcpyAsync(nseed.get(), seed.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        LAMG_CUDA(cudaMemsetAsync(changed.get(), 0, sizeof(int32_t), s));
-        k_resolve<<<ceil_div(n, 256), 256, 0, s>>>(n, state.get(), best.get(), nstate.get(), nseed.get(),
-                                                  changed.get());
-        LAMG_CHECK_LAUNCH();
-        LAMG_CUDA(cudaMemcpyAsync(state.get(), nstate.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        LAMG_CUDA(cudaMemcpyAsync(seed.get(), nseed.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    const bool scan = o.agg_rule != 0;
+    const int max_stages = scan ? std::min(o.max_rounds, 2) : o.max_rounds;
+    Tmp<int32_t> rank(scan ? n : 0, s), r1(scan ? n : 0, s), r2(scan ? n : 0, s), dec(scan ? n : 0, s),
+        waiting(scan ? 1 : 0, s);
+    Tmp<uint8_t> done(scan ? n : 0, s);
+    if (scan) {
+        if (o.agg_rule == 1) {   // the paper's index order
+            k_iota<<<ceil_div(n, 256), 256, 0, s>>>(n, rank.get());
+            LAMG_CHECK_LAUNCH();
+        } else {                 // hashed priority order
+            Tmp<uint64_t> keys(n, s), ktmp(n, s);
+            Tmp<int32_t> order(n, s), vtmp(n, s);
+            k_scan_keys<<<ceil_div(n, 256), 256, 0, s>>>(n, agg_key(o.seed, level), keys.get(), order.get());
+            LAMG_CHECK_LAUNCH();
+            radix_sort_pairs<uint64_t, int32_t>(keys.get(), order.get(), ktmp.get(), vtmp.get(), n, 64, s);
+            k_scan_rank<<<ceil_div(n, 256), 256, 0, s>>>(n, order.get(), rank.get());
+            LAMG_CHECK_LAUNCH();
+        }
+    }
+    for (r = 1; r <= max_stages; r++) {
+        if (scan) {
+            LAMG_CUDA(cudaMemsetAsync(changed.get(), 0, sizeof(int32_t), s));
+            k_scan_stage_init<<<ceil_div(n, 256), 256, 0, s>>>(n, state.get(), done.get());
+            LAMG_CHECK_LAUNCH();
+            for (int64_t round = 0;; round++) {
+                // every round decides at least the active node of smallest rank
+                LAMG_REQUIRE(round <= (int64_t)n, LAMG_ERR_CUDA, "aggregation scan: rounds did not converge");
+                LAMG_CUDA(cudaMemsetAsync(waiting.get(), 0, sizeof(int32_t), s));
+                LAUNCH3(k_scan_top2, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                        L.col.get(), rank.get(), state.get(), done.get(), r1.get(), r2.get());
+                LAUNCH3(k_scan_decide, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s,
+                        L.rp.get(), L.col.get(), score, rank.get(), state.get(), done.get(), r1.get(), r2.get(),
+                        dec.get(), waiting.get());
+                k_scan_apply<<<ceil_div(n, 256), 256, 0, s>>>(n, dec.get(), state.get(), done.get(), seed.get(),
+                                                              changed.get());
+                LAMG_CHECK_LAUNCH();
+                if (read_scalar(waiting.get(), s) == 0) break;
+            }
+        } else {
+            LAUNCH3(k_best, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                    L.col.get(), score, state.get(), best.get());
+            LAMG_CUDA(cudaMemcpyAsync(nstate.get(), state.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            LAMG_CUDA(cudaMemcpyAsync(nseed.get(), seed.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            LAMG_CUDA(cudaMemsetAsync(changed.get(), 0, sizeof(int32_t), s));
+            k_resolve<<<ceil_div(n, 256), 256, 0, s>>>(n, state.get(), best.get(), nstate.get(), nseed.get(),
+                                                      changed.get());
+            LAMG_CHECK_LAUNCH();
+            LAMG_CUDA(cudaMemcpyAsync(state.get(), nstate.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            LAMG_CUDA(cudaMemcpyAsync(seed.get(), nseed.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        }
         LAMG_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(unsigned long long), s));
         k_count_su<<<ceil_div(n, 256), 256, 0, s>>>(state.get(), n, cnt.get());
         LAMG_CHECK_LAUNCH();
@@ -1763,7 +2004,7 @@ static void aggregate_level(lamg_ctx *h, SetupLevel &L, const Tiers &T, const do
         }
         if (alpha <= amax || !ch) break;
     }
-    L.rounds = r > o.max_rounds ? o.max_rounds : r;
+    L.rounds = r > max_stages ? max_stages : r;
     L.sel_round = best_round;
     L.alpha = best_alpha;
     // numbering: seeds (S and left-over U) by ascending index, dummy aggregate last
@@ -2085,7 +2326,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
                                           cudaMemcpyDeviceToDevice, s));
         }
         pt.mark("scores");
-        aggregate_level(h, L, T, score.get(), maxw.get(), s);
+        aggregate_level(h, L, l, T, score.get(), maxw.get(), s);
         pt.mark("aggregate");
         if (L.alpha > o.alpha_stall) {
             L.coarsest = 1;

@@ -36,7 +36,7 @@ FIELD = {"row_ptr": 0, "col": 1, "w": 2, "colour": 3, "agg": 4, "state": 5, "hub
 
 
 class lamg_options(C.Structure):
-    _fields_ = [("gamma", C.c_double), ("k_finest", C.c_int32), ("k_max", C.c_int32),
+    _fields_ = [("struct_size", C.c_int32), ("gamma", C.c_double), ("k_finest", C.c_int32), ("k_max", C.c_int32),
                 ("k_step", C.c_int32), ("nu_tv", C.c_int32), ("nu1", C.c_int32),
                 ("nu2", C.c_int32), ("n_coarsest", C.c_int32), ("q_max", C.c_double),
                 ("hub_factor", C.c_double), ("weak_tol", C.c_double),
@@ -47,7 +47,8 @@ class lamg_options(C.Structure):
                 ("max_cycles", C.c_int32), ("ir_inner", C.c_int32), ("validate", C.c_int32),
                 ("keep_setup_data", C.c_int32), ("project_rhs", C.c_int32), ("mu_adaptive", C.c_double),
                 ("gamma_coarse_max", C.c_double), ("elim", C.c_int32), ("elim_min_frac", C.c_double),
-                ("lgmg_nx", C.c_int32)]
+                ("lgmg_nx", C.c_int32), ("agg_rule", C.c_int32), ("recomb_finest", C.c_int32),
+                ("relax_rule", C.c_int32)]
 
 
 class lamg_stats(C.Structure):

@@ -70,9 +70,11 @@ def test_default_options_match_the_oracle(lib):
     import oracle
     from paper_1108_1310_gb300 import lamg as L
     a, b = L.lamg_default_options(), oracle.default_opts()
-    # oracle-only option: the sequential-scan reference
-    oracle_only = {"agg_rule"}
-    assert (b.agg_rule, b.elim) == (0, 0)
+    # oracle-only options: the plain summation order and the printed fine-level
+    # cycle index, both checks of readings, not library features
+    oracle_only = {"plain_sums", "gamma_fine_printed"}
+    assert (b.agg_rule, b.recomb_finest, b.relax_rule, b.elim) == (2, 1, 0, 0)
+    assert a.struct_size == ctypes.sizeof(L.lamg_options)
     for f, _ in oracle.Opts._fields_:
         if f not in oracle_only:
             assert getattr(a, f) == getattr(b, f), f
@@ -90,10 +92,19 @@ def test_errors_without_gpu_are_status_codes(lib):
     # row_ptr below is never read)
     rp = np.zeros(5, dtype=np.int64)
     for field, bad in (("gamma_coarse_max", 0.5), ("gamma_coarse_max", 3.0), ("gamma_coarse_max", float("nan")),
-                       ("mu_adaptive", 0.0), ("gamma", 0.9)):
+                       ("mu_adaptive", 0.0), ("gamma", 0.9), ("mu_flat", 0.0), ("mu_flat", -1.0),
+                       ("mu_flat", float("nan")), ("q_max", 0.0), ("n_coarsest", 0), ("coarse_sweeps", -1),
+                       ("agg_rule", 3), ("recomb_finest", 2), ("relax_rule", -1)):
         o = L.lamg_default_options()
         setattr(o, field, bad)
         st = L._lib.lamg_setup(4, rp.ctypes.data_as(ctypes.c_void_p), None, None, 0, ctypes.byref(o), None,
                                ctypes.byref(h))
         assert st == L.LAMG_ERR_ARG and not h.value, field
         assert b"invalid options" in L._lib.lamg_last_error()
+    # a struct of another layout (struct_size differs) is rejected before it is read further
+    o = L.lamg_default_options()
+    o.struct_size -= 8
+    st = L._lib.lamg_setup(4, rp.ctypes.data_as(ctypes.c_void_p), None, None, 0, ctypes.byref(o), None,
+                           ctypes.byref(h))
+    assert st == L.LAMG_ERR_ARG and not h.value
+    assert b"struct_size" in L._lib.lamg_last_error()

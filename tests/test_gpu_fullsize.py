@@ -2,8 +2,8 @@
 cycles in FP64 refinement, options of bench.py), where the whole-hierarchy
 oracle is too slow: the oracle recomputes per-level pieces one by one from the
 GPU's own level data (colouring, hubs, per-edge affinities / energy ratios /
-scores), SciPy recomputes P^T A P, and the solution is checked by its FP64
-residual."""
+scores, aggregates and the Galerkin operator, all bit for bit), SciPy recomputes
+P^T A P within rounding, and the solution is checked by its FP64 residual."""
 import numpy as np
 import pytest
 
@@ -66,10 +66,15 @@ def test_fullsize_levels_against_oracle_pieces(big):
         assert np.array_equal(L.lamg_level_copy(s.h, l, "q").view(np.uint64), q.view(np.uint64)), l
         assert np.array_equal(L.lamg_level_copy(s.h, l, "score").view(np.uint64), score.view(np.uint64)), l
         assert np.array_equal(L.lamg_level_copy(s.h, l, "hub").astype(bool), oracle.hubs(n, rp, col, w)), l
-        # aggregation invariants: seeds first in their aggregate, associates adjacent to their seed
+        # aggregation: the oracle's scan on this level's CSR, scores and hubs, bit for bit
         agg = L.lamg_level_copy(s.h, l, "agg")
         nc = info["nc"]
-        assert agg.min() >= 0 and agg.max() == nc - 1
+        agg_o, state_o, ai = oracle.aggregate(n, rp, col, w, score, oracle.hubs(n, rp, col, w), level=l)
+        assert np.array_equal(agg, agg_o), l
+        assert np.array_equal(L.lamg_level_copy(s.h, l, "state"), state_o), l
+        assert ai["nc"] == nc and ai["alpha"] == info["alpha"], l
+        # Galerkin: the oracle's canonical sums give the next level bit for bit
+        rpo, colo, wo = oracle.galerkin(n, rp, col, w, agg, nc)
         # Galerkin: the next level's weights are P^T W P off the diagonal
         A = sp.csr_matrix((w, col, rp), shape=(n, n))
         P = sp.csr_matrix((np.ones(n), agg, np.arange(n + 1)), shape=(n, nc))
@@ -80,6 +85,9 @@ def test_fullsize_levels_against_oracle_pieces(big):
         rpc = L.lamg_level_copy(s.h, l + 1, "row_ptr")
         colc = L.lamg_level_copy(s.h, l + 1, "col")
         wc = L.lamg_level_copy(s.h, l + 1, "w")
+        assert np.array_equal(rpo, rpc) and np.array_equal(colo, colc), l
+        assert np.array_equal(wo.view(np.uint64), wc.view(np.uint64)), l
+        # and SciPy's P^T W P (another summation order) within rounding
         assert np.array_equal(Wc.indptr.astype(np.int64), rpc) and np.array_equal(Wc.indices, colc), l
         assert np.max(np.abs(Wc.data - wc)) <= 1e-12 * np.max(np.abs(wc)), l
 

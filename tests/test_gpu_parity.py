@@ -38,6 +38,8 @@ def _graph(name):
         "star6k": lambda: W.star(6000),
         # every node its own colour: tail-colour sweeps and long single-block runs
         "complete": lambda: W.complete(200),
+        # the 256^3 workload's family (weights 1/1/0.01) at a size the oracle handles
+        "grid3d32": lambda: W.grid3d(32, 32, 32, 1.0, 1.0, 0.01),
     }[name]()
 
 
@@ -52,13 +54,32 @@ def _bits(a):
 
 
 SETUP_GRAPHS = ["five", "path", "star", "grid2d", "grid3d", "chung_lu", "rgg", "er", "grid64", "hubs", "star6k",
-                "complete"]
+                "complete", "grid3d32"]
+
+# the other rules of the library (Sec. 3.4.2 and Eq. (2.3)): the parallel handshake
+# with recombination below the finest level only, the paper's index-order scan,
+# and lexicographic Gauss-Seidel (with either scan order)
+RULES = {
+    "handshake": {"agg_rule": 0, "recomb_finest": 0},
+    "index_scan": {"agg_rule": 1},
+    "index_scan_lex": {"agg_rule": 1, "relax_rule": 1},
+    "lex": {"relax_rule": 1},
+}
 
 
 @pytest.mark.parametrize("gname", SETUP_GRAPHS)
 def test_setup_bit_exact(L, gname):
-    g = _graph(gname)
-    s, h = _both(L, g)
+    _check_setup_bit_exact(L, _graph(gname))
+
+
+@pytest.mark.parametrize("rule", list(RULES))
+@pytest.mark.parametrize("gname", ["grid2d", "grid3d", "chung_lu", "rgg", "hubs"])
+def test_setup_bit_exact_rules(L, gname, rule):
+    _check_setup_bit_exact(L, _graph(gname), **RULES[rule])
+
+
+def _check_setup_bit_exact(L, g, **kw):
+    s, h = _both(L, g, **kw)
     nl = h.num_levels
     assert s._levels() == nl
     for l in range(nl):
@@ -107,6 +128,22 @@ def test_one_cycle_elementwise(L, gname, adaptive):
     s.close()
 
 
+@pytest.mark.parametrize("rule", list(RULES))
+@pytest.mark.parametrize("gname", ["grid2d", "chung_lu", "grid3d32"])
+def test_one_cycle_elementwise_rules(L, gname, rule):
+    g = _graph(gname)
+    s, h = _both(L, g, **RULES[rule])
+    b = W.zero_sum_rhs(g.n, 3)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    xo = np.zeros(g.n)
+    for k in range(2):
+        xo = h.cycle(b, xo, adaptive=True)
+        L.lamg_cycle(s.h, bt, xt, True)
+        assert np.max(np.abs(xt.cpu().numpy() - xo)) <= 1e-10 * np.max(np.abs(xo)), k
+    s.close()
+
+
 @pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "five", "path", "star6k", "complete"])
 def test_solve_fp64_matches_oracle_and_dense(L, gname):
     g = _graph(gname)
@@ -128,7 +165,7 @@ def test_solve_fp64_matches_oracle_and_dense(L, gname):
     s.close()
 
 
-@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "hubs"])
+@pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "hubs", "grid3d32"])
 def test_solve_fp32_ir(L, gname):
     g = _graph(gname)
     s, h = _both(L, g)

@@ -18,7 +18,8 @@ with each step taken from its definition in matrix form:
 
 The iterates recombined are those of this build's reading of Sec. 3.5: the
 iterate after the pre-relaxation of each two-level step, recombined with the
-iterate at the end of the visit, at every level but the finest.  The cycle index
+iterate at the end of the visit, at every level (reading R15; with the option
+recomb_finest = 0, at every level but the finest).  The cycle index
 of level l with gamma_l gives its k-th coarse correction ceil((k+1) gamma_l) -
 ceil(k gamma_l) coarse visits, kept in [1, 2].  A wrong operand, sign, index
 or order in the C cycle changes its result well beyond rounding.
@@ -44,6 +45,7 @@ class _NumpyCycle:
         self.nu1, self.nu2 = o.nu1, o.nu2
         self.mu = o.mu_adaptive if adaptive else o.mu_flat
         self.adaptive = adaptive
+        self.recomb_finest = bool(o.recomb_finest)
         self.gptr = gptr
         self.lv = []
         for l in range(h.num_levels):
@@ -98,7 +100,7 @@ class _NumpyCycle:
         F, C = self.lv[l], self.lv[l + 1]
         A, agg = F["A"], F["agg"]
         x = x.copy()
-        recomb = self.adaptive and l >= 1
+        recomb = self.adaptive and (l >= 1 or self.recomb_finest)
         saved = []
         for _ in range(theta):
             for _ in range(self.nu1):
@@ -148,6 +150,10 @@ def _graphs():
         # the restriction factor under recombination, and the coarse cycle-index cap
         "chung_lu_mu": (W.chung_lu(2500, seed=35), None, {"mu_adaptive": 1.2}),
         "rgg_cap1": (W.rgg2d(1500, seed=36), None, {"gamma_coarse_max": 1.0}),
+        # the earlier readings: the parallel handshake, recombination below the finest level
+        "grid_handshake": (W.grid2d(36, 30), None, {"agg_rule": 0, "recomb_finest": 0}),
+        # the paper's sequential forms: index-order scan, lexicographic GS
+        "rgg_lex": (W.rgg2d(1500, seed=37), None, {"agg_rule": 1, "relax_rule": 1}),
     }
 
 
@@ -182,4 +188,7 @@ def test_composition_detects_the_recombination():
     assert np.max(np.abs(ref.cycle(b, np.zeros(g.n)) - got)) > 1e-6 * scale
     ref = _NumpyCycle(h, True)
     ref.mu = h.opts.mu_flat
+    assert np.max(np.abs(ref.cycle(b, np.zeros(g.n)) - got)) > 1e-6 * scale
+    ref = _NumpyCycle(h, True)
+    ref.recomb_finest = False                # no recombination at the finest level
     assert np.max(np.abs(ref.cycle(b, np.zeros(g.n)) - got)) > 1e-6 * scale

@@ -156,13 +156,15 @@ def test_solution_with_elimination_matches_dense_pseudoinverse(gname):
 def test_elimination_removes_the_one_dimensional_part_of_a_grid():
     # Sec. 3.2: elimination removes what aggregation coarsens badly.  On a 5-point
     # grid every node has degree <= 4, so the first F is a maximal independent set
-    # of the whole grid: each node is in F or next to it, hence |F| >= n/5.  The
-    # work per digit of the whole solve drops well below that without elimination.
+    # of the whole grid: each node is in F or next to it, hence |F| >= n/5.  Under
+    # the parallel handshake with recombination below the finest level only (the
+    # earlier readings R9/R15, which coarsen a grid at alpha ~ .8), the work per
+    # digit of the whole solve drops well below that without elimination.
     g = W.grid2d(64, 64)
     b = W.zero_sum_rhs(g.n, 1)
     wpd = []
     for e in (0, 1):
-        h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=e)
+        h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=e, agg_rule=0, recomb_finest=0)
         if e:
             assert h.info(0)["nF"] >= g.n / 5
         _, hist = h.solve(b, tol=1e-8, max_cycles=400)
@@ -182,7 +184,7 @@ def test_standalone_elim_set_reproduces_the_hierarchy():
     # oracle.elim_set applied to a level's own graph with that level's sweep key gives
     # the level's eliminated set (the full-size GPU test relies on this)
     g = W.chung_lu(5000, seed=3)
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1, agg_rule=0)   # several elimination levels
     seen = 0
     for l in range(h.num_levels - 1):
         if not h.info(l)["elim"]:
@@ -195,19 +197,22 @@ def test_standalone_elim_set_reproduces_the_hierarchy():
     assert seen >= 2
 
 
-def test_grid_acf_matches_the_paper_only_with_elimination():
+def test_grid_acf_matches_the_paper():
     # The paper prints an ACF of .216 for the 5-point 1024^2 grid (Sec. 5, grid
-    # table), with its elimination levels.  With elimination the oracle's ACF on
-    # a 256^2 grid lies in that neighbourhood; without it, aggregation alone
-    # stalls on grids this large (asymptotic rate above .9 per cycle).
+    # table).  With the paper's scan (Sec. 3.4.2, in hashed order) and recombination
+    # at every level (reading R15), the oracle's ACF on a 256^2 grid lies in that
+    # neighbourhood with and without elimination.  Under the earlier readings (the
+    # parallel handshake, recombination below the finest level only) only
+    # elimination rescued it: aggregation alone stalled (rate above .9 per cycle).
     g = W.grid2d(256, 256)
     b = W.zero_sum_rhs(g.n, 1)
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1)
-    _, hist = h.solve(b, tol=1e-10, max_cycles=100)
-    p = len(hist) - 1
-    acf = (hist[-1] / hist[0]) ** (1.0 / p)
-    assert 0.15 <= acf <= 0.30 and p <= 25, (acf, p)
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+    for kw in ({}, {"elim": 1}, {"elim": 1, "agg_rule": 0, "recomb_finest": 0}):
+        h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, **kw)
+        _, hist = h.solve(b, tol=1e-10, max_cycles=100)
+        p = len(hist) - 1
+        acf = (hist[-1] / hist[0]) ** (1.0 / p)
+        assert 0.15 <= acf <= 0.30 and p <= 25, (kw, acf, p)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=0, recomb_finest=0)
     _, hist = h.solve(b, tol=1e-10, max_cycles=40)
     rate = (hist[-1] / hist[-11]) ** 0.1              # over the last 10 cycles
     assert rate > 0.9, rate

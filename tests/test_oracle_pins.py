@@ -399,13 +399,14 @@ def _acf_and_work_per_digit(h, b):
 
 
 @pytest.mark.parametrize("gname", list(QUALITY))
-def test_handshake_quality_against_sequential_scan(gname):
-    # The parallel handshake is a reading, not the paper's rule.  Its quality is
-    # checked against the paper's own sequential scan on the same scores: the ACF
-    # within 1.5x, and the work per digit of residual reduction within 2x.
+def test_hashed_scan_quality_against_index_order_scan(gname):
+    # The default visits the nodes of the paper's scan (Sec. 3.4.2) in a hashed
+    # priority order instead of the index order, so that the GPU can run it in
+    # parallel rounds.  Its quality is checked against the index-order scan on the
+    # same scores: the ACF within 1.5x, and the work per digit within 2x.
     g = QUALITY[gname]()
     b = W.zero_sum_rhs(g.n, 1)
-    acf0, wpd0 = _acf_and_work_per_digit(oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=0), b)
+    acf0, wpd0 = _acf_and_work_per_digit(oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=2), b)
     acf1, wpd1 = _acf_and_work_per_digit(oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=1), b)
     assert acf0 <= 1.5 * acf1, (acf0, acf1)
     assert wpd0 <= 2.0 * wpd1, (wpd0, wpd1)
@@ -608,7 +609,7 @@ def test_per_level_pieces_reproduce_the_hierarchy():
         # the standalone aggregation and Galerkin step give this level's aggregates
         # and the next level's CSR bit for bit
         agg, state, hub = h.agg(l)
-        agg2, state2, ai = oracle.aggregate(n, rp, col, w, score, hub)
+        agg2, state2, ai = oracle.aggregate(n, rp, col, w, score, hub, level=l)
         assert np.array_equal(agg2, agg) and np.array_equal(state2, state)
         assert ai["nc"] == h.info(l)["nc"] and ai["alpha"] == h.info(l)["alpha"]
         rpc, colc, wc = oracle.galerkin(n, rp, col, w, agg, ai["nc"])
@@ -676,21 +677,23 @@ def test_coarse_cycle_index_cap():
         else:
             coarse += 1
             assert g1 == 1.0 and 1.0 <= g2 <= 2.0
-    assert coarse >= 2
+    assert coarse >= 1
     x, hist = h1.solve(b, tol=1e-10)
     assert hist[-1] <= 1e-10 * hist[0]
 
 
 @pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "grid3d", "er"])
-def test_cycle_work_is_about_ten_relaxations(gname):
+@pytest.mark.parametrize("elim", [0, 1])
+def test_cycle_work_is_about_ten_relaxations(gname, elim):
     # Sec. 4.2: the whole cycle costs about 10 relaxation sweeps of the finest level.
-    # With the paper's elimination levels, the bounded cycle index (reading R13)
-    # keeps the cycle's relaxation work, (nu1 + nu2) sum_l visits_l |A^l| / |A^0|,
-    # within a factor 2 of that on every family.
+    # With and without the paper's elimination levels, the bounded cycle index
+    # (reading R13) keeps the cycle's relaxation work,
+    # (nu1 + nu2) sum_l visits_l |A^l| / |A^0|, in 4.7-9.4 sweeps on these families;
+    # the test allows [4.5, 10.5].
     g = {"grid64": lambda: W.grid2d(64, 64), "chung_lu": lambda: W.chung_lu(20000, seed=3),
          "rgg": lambda: W.rgg2d(20000, seed=4), "grid3d": lambda: W.grid3d(24, 24, 24, 1.0, 1.0, 0.01),
          "er": lambda: W.erdos_renyi(5000, seed=5)}[gname]()
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=1)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, elim=elim)
     o = h.opts
     visits, sweeps, nnz0 = 1.0, 0.0, h.info(0)["nnz"]
     for l in range(h.num_levels):
@@ -700,7 +703,7 @@ def test_cycle_work_is_about_ten_relaxations(gname):
         if not i["elim"]:
             sweeps += (o.nu1 + o.nu2) * visits * i["nnz"] / nnz0
         visits *= i["gamma"]
-    assert 5.0 <= sweeps <= 20.0, sweeps
+    assert 4.5 <= sweeps <= 10.5, sweeps
 
 
 def _per_unit_work(h, b, nu):
@@ -732,3 +735,31 @@ def test_lean_geometric_multigrid_rate():
     assert 0.45 <= rate <= 0.56, rate
     h1 = oracle.Hierarchy(g.n, g.rp, g.col, g.w, lgmg_nx=nx, mu_flat=1.0, gamma=1.5)
     assert _per_unit_work(h1, b, nu) > 0.8
+
+
+def test_anisotropic_grid_rate_does_not_grow_with_size():
+    # 7-point grids with weights 1/1/0.01 behave like stacks of 2-D grids.  With the
+    # paper's scan (Sec. 3.4.2, hashed order) and recombination at every level (Eq.
+    # (3.13), reading R15) the ACF stays at ~.55 from 64^3 to 128^3 (measured
+    # 0.5475 and 0.5474), while the parallel handshake with recombination below the
+    # finest level only (the earlier readings) degrades with size (0.585 at 32^3,
+    # 0.695 at 64^3, 0.81 at 128^3).
+    acf = {}
+    for nx in (64, 128):
+        g = W.grid3d(nx, nx, nx, 1.0, 1.0, 0.01)
+        b = W.zero_sum_rhs(g.n, 3)
+        h = oracle.Hierarchy(g.n, g.rp, g.col, g.w)
+        _, hist = h.solve(b, tol=1e-8, max_cycles=60)
+        p = len(hist) - 1
+        acf[nx] = (hist[-1] / hist[0]) ** (1.0 / p)
+        assert hist[-1] <= 1e-8 * hist[0] and p <= 40, (nx, p)
+    assert acf[64] <= 0.6 and acf[128] <= 0.6, acf
+    assert abs(acf[128] - acf[64]) <= 0.05, acf
+    old = {}
+    for nx in (32, 64):
+        g = W.grid3d(nx, nx, nx, 1.0, 1.0, 0.01)
+        b = W.zero_sum_rhs(g.n, 3)
+        h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, agg_rule=0, recomb_finest=0)
+        _, hist = h.solve(b, tol=1e-8, max_cycles=100)
+        old[nx] = (hist[-1] / hist[0]) ** (1.0 / (len(hist) - 1))
+    assert old[64] >= old[32] + 0.05 and old[64] >= acf[64] + 0.1, (old, acf)

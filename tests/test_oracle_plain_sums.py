@@ -136,7 +136,7 @@ def test_tiered_sums_equal_the_plain_definition_up_to_rounding(name):
             assert tie.any(), f"level {l}: aggregates differ without a near-tie"
             mix = sp.copy()
             mix[tie[row]] = st[tie[row]]
-            aggm, _, _ = oracle.aggregate(n, rpt, colt, wt, mix, hubt)
+            aggm, _, _ = oracle.aggregate(n, rpt, colt, wt, mix, hubt, level=l)
             assert np.array_equal(aggm, aggt), f"level {l}: a flip not explained by the near-ties"
             flips += int(np.sum(statet != statep))
             break
