@@ -468,6 +468,11 @@ def main():
                     help="low-degree elimination levels (Sec. 3.2) in the hierarchy (default workload only)")
     ap.add_argument("--gamma-coarse-max", type=float, default=2.0,
                     help="cap of the cycle index at the coarse levels (Eq. (4.1) prints 2)")
+    ap.add_argument("--agg-rule", type=int, default=2, choices=[0, 1, 2],
+                    help="aggregation stages: 2 the paper's scan in hashed order (default), 1 in index order, "
+                         "0 the parallel handshake")
+    ap.add_argument("--recomb-finest", type=int, default=1, choices=[0, 1],
+                    help="1: the adaptive cycle recombines at the finest level too (default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -507,7 +512,8 @@ def main():
     x = torch.zeros_like(b)
     mopts, adaptive = method_opts(args.workload, g.n)
     opt = L.lamg_default_options(validate=1, max_cycles=2000, adaptive=int(adaptive),
-                                 gamma_coarse_max=args.gamma_coarse_max, elim=int(args.elim), **mopts)
+                                 gamma_coarse_max=args.gamma_coarse_max, elim=int(args.elim),
+                                 agg_rule=args.agg_rule, recomb_finest=args.recomb_finest, **mopts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
     def step(profile=False):
@@ -635,7 +641,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == L.LAMG_FP32_IR else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "tol": tol,
-                   "precision": prec_name, "gamma_coarse_max": args.gamma_coarse_max, "elim": bool(args.elim), "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
+                   "precision": prec_name, "gamma_coarse_max": args.gamma_coarse_max, "elim": bool(args.elim),
+                   "agg_rule": args.agg_rule, "recomb_finest": args.recomb_finest, "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
                    "rel_res": s0.rel_res, "time_to_tol_s": ms / 1e3,
                    "setup_s_host": s0.t_setup_s, "solve_s_host": s0.t_solve_s,
                    "model_bytes_per_cycle": s0.bytes_per_cycle32 if prec == L.LAMG_FP32_IR else s0.bytes_per_cycle,

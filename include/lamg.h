@@ -334,6 +334,25 @@ lamg_status lamg_barrier_selftest(int32_t hold_one_block, lamg_stream stream);
 lamg_status lamg_profile(lamg_handle h, int32_t enable, double *avg_ms, int64_t *count,
                          int64_t *bytes_per_launch);
 
+/* The cycle engine's op timer, an introspection aid with no counterpart in the
+ * paper.  mode 1: start timing on this handle (allocates one 128 KB table on the
+ * device, zeroed); block 0 then reads its clock around every op of every later
+ * engine launch of h, which adds a little time to each op.  mode 0: copy the
+ * rows of the table with a non-zero count into the caller's host arrays (at
+ * most cap rows; *n_rows gets the number of such rows, which may exceed cap),
+ * then zero the table; timing continues.  mode -1: stop and free the table.
+ * A row is (level, op type, single_block, count, total ns): op types are the
+ * engine's op codes 0..31 in the order OP_SWEEP, OP_SWEEP_RUN, OP_RESID,
+ * OP_RESTRICT, OP_ZERO, OP_COARSE, OP_PROLONG, OP_RECOMB_DOTS,
+ * OP_RECOMB_APPLY, OP_MEAN_PART, OP_MEAN_APPLY, OP_IR_PREP, OP_IR_UPDATE,
+ * OP_MEAN64_PART, OP_MEAN64_APPLY, OP_RES64, OP_NORM64_FIN, OP_SWEEP_SMEM,
+ * OP_GMEAN_PART, OP_GMEAN_APPLY, OP_GMEAN64_PART, OP_GMEAN64_APPLY, OP_GNORM64,
+ * OP_TAIL_PRE, OP_TAIL_RUN, OP_ELIM_RESTRICT, OP_ELIM_PROLONG, OP_ELIM_BACK;
+ * single_block 1 marks ops that block 0 ran alone.  The arrays may be NULL when
+ * cap is 0.  Errors: LAMG_ERR_ARG for a NULL handle or a bad mode. */
+lamg_status lamg_op_times(lamg_handle h, int32_t mode, int32_t cap, int32_t *level, int32_t *op,
+                          int32_t *single_block, int64_t *count, double *total_ns, int32_t *n_rows);
+
 /* Number of this library's kernel launches since it was loaded (a
  * cooperative engine launch counts once). */
 lamg_status lamg_launch_count(int64_t *count_host);

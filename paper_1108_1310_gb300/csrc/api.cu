@@ -377,6 +377,35 @@ lamg_status lamg_profile(lamg_handle h, int32_t enable, double *avg_ms, int64_t 
     });
 }
 
+lamg_status lamg_op_times(lamg_handle h, int32_t mode, int32_t cap, int32_t *level, int32_t *op,
+                          int32_t *single_block, int64_t *count, double *total_ns, int32_t *n_rows) {
+    return guarded([&] {
+        LAMG_REQUIRE(h, LAMG_ERR_ARG, "NULL handle");
+        LAMG_REQUIRE(mode >= -1 && mode <= 1, LAMG_ERR_ARG, "mode must be -1, 0 or 1");
+        std::vector<unsigned long long> t;
+        engine_op_times(h, mode, t);
+        if (mode != 0) return;
+        LAMG_REQUIRE(cap == 0 || (level && op && single_block && count && total_ns), LAMG_ERR_ARG,
+                     "NULL output array");
+        int32_t rows = 0;
+        for (int l = 0; l < 128; l++)
+            for (int ty = 0; ty < 32; ty++)
+                for (int sb = 0; sb < 2; sb++) {
+                    const int key = (l * 32 + ty) * 2 + sb;
+                    if (!t[2 * key + 1]) continue;
+                    if (rows < cap) {
+                        level[rows] = l;
+                        op[rows] = ty;
+                        single_block[rows] = sb;
+                        count[rows] = (int64_t)t[2 * key + 1];
+                        total_ns[rows] = (double)t[2 * key];
+                    }
+                    rows++;
+                }
+        if (n_rows) *n_rows = rows;
+    });
+}
+
 lamg_status lamg_launch_count(int64_t *count) {
     return guarded([&] {
         LAMG_REQUIRE(count, LAMG_ERR_ARG, "NULL argument");

@@ -672,20 +672,6 @@ void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &ou
         B.emit(OP_NORM64_FIN, 0, 0, 0, false);
         if (h->ngraphs > 1) B.emit(OP_GNORM64, 0, 0, 0, false);
     }
-    if (const char *e = std::getenv("LAMG_ENGINE_STATS"); e && e[0] == '1') {
-        int64_t grid_ops = 0, runs = 0, sb_ops = 0;
-        for (size_t i = 0; i < B.prog.size(); i++) {
-            if (B.prog[i].sb) {
-                sb_ops++;
-                if (i == 0 || !B.prog[i - 1].sb) runs++;
-            } else {
-                grid_ops++;
-            }
-        }
-        std::fprintf(stderr, "lamg-engine kind %d groups %d: %zu ops, %lld grid ops, %lld single-block runs (%lld ops), %lld barriers\n",
-                     kind, groups, B.prog.size(), (long long)grid_ops, (long long)runs, (long long)sb_ops,
-                     (long long)(grid_ops + runs));
-    }
     out.resize(B.prog.size() * 5);
     for (size_t i = 0; i < B.prog.size(); i++) {
         out[5 * i] = B.prog[i].type;
@@ -728,31 +714,23 @@ void engine_prepare(lamg_ctx *h) {
     h->eng_err.alloc(1);
     LAMG_CUDA(cudaMemset(h->eng_bar.get(), 0, 2 * sizeof(unsigned int)));
     LAMG_CUDA(cudaMemset(h->eng_err.get(), 0, sizeof(int32_t)));
-    if (const char *e = std::getenv("LAMG_ENGINE_PROFILE"); e && e[0] == '1') {
-        h->eng_optime.alloc(128 * 32 * 2 * 2);
-        LAMG_CUDA(cudaMemset(h->eng_optime.get(), 0, h->eng_optime.bytes()));
-    }
 }
 
-// Development aid (LAMG_ENGINE_PROFILE=1): print the accumulated op times.
-void engine_report(lamg_ctx *h) {
+// The engine's op timer (lamg_op_times): block 0's clock around every op, summed
+// per (level, op type, single-block flag) in eng_optime while it is allocated.
+void engine_op_times(lamg_ctx *h, int mode, std::vector<unsigned long long> &out) {
+    if (mode == 1) {
+        if (!h->eng_optime.get()) h->eng_optime.alloc(kOpTimeSlots);
+        LAMG_CUDA(cudaMemset(h->eng_optime.get(), 0, h->eng_optime.bytes()));
+        return;
+    }
+    if (mode == -1) {
+        h->eng_optime.release();
+        return;
+    }
+    out.assign(kOpTimeSlots, 0ull);
     if (!h->eng_optime.get()) return;
-    std::vector<unsigned long long> t(h->eng_optime.n);
-    LAMG_CUDA(cudaMemcpy(t.data(), h->eng_optime.get(), h->eng_optime.bytes(), cudaMemcpyDeviceToHost));
-    static const char *names[] = {"sweep", "sweep_run", "resid", "restrict", "zero", "coarse", "prolong",
-                                  "recomb_dots", "recomb_apply", "mean_part", "mean_apply", "ir_prep",
-                                  "ir_update", "mean64_part", "mean64_apply", "res64", "norm64", "sweep_smem",
-                                  "gmean_part", "gmean_apply", "gmean64_part", "gmean64_apply", "gnorm64",
-                                  "tail_pre", "tail_run", "elim_restrict", "elim_prolong", "elim_back"};
-    for (int l = 0; l < 128; l++)
-        for (int ty = 0; ty < (int)(sizeof(names) / sizeof(names[0])); ty++)
-            for (int sb = 0; sb < 2; sb++) {
-                const int key = (l * 32 + ty) * 2 + sb;
-                if (t[2 * key + 1])
-                    std::fprintf(stderr, "lamg-optime level %2d %-13s %s n=%8llu total %10.3f ms  per %8.2f us\n", l,
-                                 names[ty], sb ? "sb  " : "grid", t[2 * key + 1], t[2 * key] * 1e-6,
-                                 t[2 * key] * 1e-3 / t[2 * key + 1]);
-            }
+    LAMG_CUDA(cudaMemcpy(out.data(), h->eng_optime.get(), h->eng_optime.bytes(), cudaMemcpyDeviceToHost));
     LAMG_CUDA(cudaMemset(h->eng_optime.get(), 0, h->eng_optime.bytes()));
 }
 

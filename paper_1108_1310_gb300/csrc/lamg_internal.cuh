@@ -241,7 +241,6 @@ void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const
 // most tail_work(prec) entries joins a single-block run.  One SM streams FP32
 // rows from L2 faster than a grid-wide phase completes, up to a few hundred
 // KB; FP64 arithmetic on one SM is slow (1/64 rate), so its limits are lower.
-// LAMG_SB_WORK32/64 and LAMG_TAIL_WORK32/64 override them (tuning aid).
 int64_t sb_work(int prec);    // prec 0 = FP64, 1 = FP32
 int64_t tail_work(int prec);
 constexpr int64_t kSBWork = 16384;
@@ -250,7 +249,9 @@ constexpr int64_t kSBWork = 16384;
 void engine_prepare(lamg_ctx *h);
 void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s);
 bool engine_failed(lamg_ctx *h, cudaStream_t s);
-void engine_report(lamg_ctx *h);
+// op timer table: (level < 128) x (op type < 32) x (grid, single block) x (ns, count)
+constexpr int kOpTimeSlots = 128 * 32 * 2 * 2;
+void engine_op_times(lamg_ctx *h, int mode, std::vector<unsigned long long> &out);
 void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out, int groups = 0);
 bool engine_noalloc_ready(lamg_ctx *h, int adaptive);
 int32_t barrier_selftest(int32_t hold_one, cudaStream_t s);

@@ -24,28 +24,6 @@
 
 namespace lamg {
 
-// Phase timer for development: with LAMG_TIMING=1 in the environment every
-// phase of the setup synchronises the stream and prints its wall time.
-struct PhaseTimer {
-    bool on;
-    cudaStream_t s;
-    int level = 0;
-    std::chrono::steady_clock::time_point t;
-    explicit PhaseTimer(cudaStream_t st) : s(st) {
-        const char *e = std::getenv("LAMG_TIMING");
-        on = e && e[0] == '1';
-        t = std::chrono::steady_clock::now();
-    }
-    void mark(const char *what) {
-        if (!on) return;
-        cudaStreamSynchronize(s);
-        auto now = std::chrono::steady_clock::now();
-        std::fprintf(stderr, "lamg-timing level %d %-10s %9.3f ms\n", level, what,
-                     std::chrono::duration<double, std::milli>(now - t).count());
-        t = now;
-    }
-};
-
 constexpr unsigned kFull = 0xffffffffu;
 enum { ST_U = 0, ST_S = 1, ST_A = 2, ST_D = 3 };
 enum { M_THR = 0, M_WARP = 1, M_BLK = 2 };
@@ -1699,8 +1677,6 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
         colour_lex(L, s);
     } else if (relaxes) {
         const uint64_t key = colour_key(h->opt.seed, level);
-        PhaseTimer ct(s);
-        ct.level = level;
         {
         // wait counts, the first frontier, then all rounds in one cooperative launch
         Tmp<int32_t> deg(n, s), wait(n, s);
@@ -1740,7 +1716,6 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
         }
         LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "colouring: grid barrier timed out");
         batch_rounds = read_scalar(out.get(), s);
-        ct.mark("jp_rounds");
         }
     }
     L.jp_rounds = batch_rounds + fin_rounds;
@@ -1830,46 +1805,17 @@ static double relax_tvs(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, c
         LAMG_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), s));
         const int grid = coop_grid((const void *)k_tv_sweeps_coop, "TV sweep kernel");
         int32_t nsw = o.nu_tv, npl = (int32_t)(plan.size() / 3);
-        if (const char *e = std::getenv("LAMG_TIMING"); e && e[0] == '1') {
-            int singles = 0, maxdeg = 0;
-            for (int32_t q = 0; q < npl; q++) singles += plan[3 * q + 2];
-            std::vector<int32_t> hrp(n + 1);
-            LAMG_CUDA(cudaMemcpy(hrp.data(), L.rp.get(), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
-            for (int32_t u = 0; u < n; u++) maxdeg = std::max(maxdeg, hrp[u + 1] - hrp[u]);
-            std::fprintf(stderr, "lamg-timing level %d tv plan: %d phases (%d single-block runs), K %d, max degree %d\n",
-                         level, npl, singles, K, maxdeg);
-        }
         const int32_t *pp = dplan.get(), *cbp = L.cb_dev.get(), *rpp = L.rp.get(), *colp = L.col.get();
         const double *wp = L.w.get();
         unsigned int *barp = bar.get();
         int32_t *errp = err.get();
         int32_t Kv = K;
         double *gp = gsum.get();
-        const char *te = std::getenv("LAMG_TIMING");
-        const bool tprof = te && te[0] == '2';   // per-phase times (development aid)
-        Tmp<unsigned long long> ptime(tprof ? npl : 0, s);
-        if (tprof) LAMG_CUDA(cudaMemsetAsync(ptime.get(), 0, sizeof(unsigned long long) * npl, s));
-        unsigned long long *tp = ptime.get();
+        unsigned long long *tp = nullptr;   // per-phase clock (kernel support kept; off)
         void *args[] = {&nsw, &pp, &npl, &cbp, &ord, &rpp, &colp, &wp, &diag, &Kv, &X, &barp, &errp, &gp, &tp};
         LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_tv_sweeps_coop, dim3(grid), dim3(kBlk), args, 0, s));
         note_launch();
         LAMG_REQUIRE(read_scalar(err.get(), s) == 0, LAMG_ERR_TIMEOUT, "TV sweep: grid barrier timed out");
-        if (tprof) {
-            std::vector<unsigned long long> ht(npl);
-            LAMG_CUDA(cudaMemcpy(ht.data(), ptime.get(), sizeof(unsigned long long) * npl, cudaMemcpyDeviceToHost));
-            std::vector<int> idx(npl);
-            for (int q = 0; q < npl; q++) idx[q] = q;
-            std::sort(idx.begin(), idx.end(), [&](int a, int b) { return ht[a] > ht[b]; });
-            unsigned long long tot = 0;
-            for (auto v : ht) tot += v;
-            std::fprintf(stderr, "lamg-tvphase level %d total %.3f ms over %d phases\n", level, tot * 1e-6, npl);
-            for (int k = 0; k < std::min(npl, 12); k++) {
-                const int q = idx[k], c = plan[3 * q];
-                std::fprintf(stderr, "lamg-tvphase level %d colour %d single %d: %.1f us; rows thr %d warp %d blk %d, entries %d\n",
-                             level, c, plan[3 * q + 2], ht[q] * 1e-3, L.cb[4 * c + 1] - L.cb[4 * c],
-                             L.cb[4 * c + 2] - L.cb[4 * c + 1], L.cb[4 * c + 3] - L.cb[4 * c + 2], ent[c]);
-            }
-        }
         return INFINITY;
     }
     for (int sw = 1; sw <= o.nu_tv; sw++) {
@@ -2227,24 +2173,19 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
     int32_t nxl = o.lgmg_nx;   // Lean Geometric MG: the current grid side
     LAMG_REQUIRE(nxl >= 0 && (nxl == 0 || (int64_t)nxl * nxl == n), LAMG_ERR_ARG,
                  "lgmg_nx * lgmg_nx must equal n");
-    PhaseTimer pt(s);
-    pt.mark("ingest");
     int nagg = 0;   // aggregation levels so far (the TV count grows with them)
     for (int l = 0;; l++) {
         SetupLevel &L = h->sl[l];
         const int32_t nl = L.n;
         h->L = l + 1;
-        pt.level = l;
         Tiers T(nl, s);
         build_tiers(L.rp.get(), nl, T, s);
         Tmp<double> diag(nl, s), maxw(nl, s);
         L.hub.alloc(nl);
         LAUNCH3(k_node_stats, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
                 L.col.get(), L.w.get(), o.hub_factor, diag.get(), maxw.get(), L.hub.get());
-        pt.mark("stats");
         if (nl < o.n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
             colour_level(h, L, l, T, nxl, s);
-            pt.mark("colour");
             L.coarsest = 1;
             L.stop_reason = nl < o.n_coarsest ? 1 : 4;
             break;
@@ -2260,14 +2201,12 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
                         L.rp.get(), erow.get());
                 h->sl.emplace_back();   // capacity reserved: references stay valid
                 eliminate_level(h->sl[l], h->sl[l + 1], erow.get(), diag.get(), s);
-                pt.mark("eliminate");
                 continue;
             }
             L.nF = 0;
             L.cidx.release();
         }
         colour_level(h, L, l, T, nxl, s);
-        pt.mark("colour");
         if (nxl > 0) {   // Lean Geometric MG: 1:2 coarsening in both directions, 2x2 aggregates
             L.agg.alloc(nl);
             L.state.alloc(nl);
@@ -2281,7 +2220,6 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
                     erow.get());
             h->sl.emplace_back();
             galerkin_level(h->sl[l], h->sl[l + 1], erow.get(), s);
-            pt.mark("galerkin");
             nxl /= 2;
             continue;
         }
@@ -2292,7 +2230,6 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         L.K = K;
         Tmp<double> X((size_t)nl * K, s);
         L.tv_ratio = relax_tvs(h, L, l, T, diag.get(), X.get(), s);
-        pt.mark("tv");
         if (o.keep_setup_data) {
             L.tv.alloc((size_t)nl * K);
             LAMG_CUDA(cudaMemcpyAsync(L.tv.get(), X.get(), sizeof(double) * nl * K, cudaMemcpyDeviceToDevice, s));
@@ -2325,9 +2262,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
                 LAMG_CUDA(cudaMemcpyAsync(L.score.get(), score.get(), sizeof(double) * L.nnz,
                                           cudaMemcpyDeviceToDevice, s));
         }
-        pt.mark("scores");
         aggregate_level(h, L, l, T, score.get(), maxw.get(), s);
-        pt.mark("aggregate");
         if (L.alpha > o.alpha_stall) {
             L.coarsest = 1;
             L.stop_reason = 3;
@@ -2335,7 +2270,6 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         }
         h->sl.emplace_back();
         galerkin_level(h->sl[l], h->sl[l + 1], erow.get(), s);
-        pt.mark("galerkin");
         nagg++;
     }
     cycle_indices(h);

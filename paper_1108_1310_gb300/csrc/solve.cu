@@ -22,29 +22,27 @@
 namespace lamg {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRedBlocks = 608;     // 152 SMs x 4 blocks for reductions
+constexpr int kRedBlocksMax = 1024;  // reduction grid: 4 blocks per SM, at most this many
 constexpr int kRedThreads = 256;
 constexpr int64_t kTailWork32 = 2048;   // entries of a colour that the single-block sweep takes (FP32)
 constexpr int64_t kTailWork64 = 512;    // same for FP64 (one SM's FP64 rate is low on this GPU)
 constexpr int64_t kSBWork32 = 16384, kSBWork64 = 16384;
 
-static int64_t env_or(const char *name, int64_t dflt) {
-    const char *e = std::getenv(name);
-    return (e && *e) ? std::atoll(e) : dflt;
-}
-int64_t sb_work(int prec) {
-    static const int64_t v32 = env_or("LAMG_SB_WORK32", kSBWork32), v64 = env_or("LAMG_SB_WORK64", kSBWork64);
-    return prec == 1 ? v32 : v64;
-}
-int64_t tail_work(int prec) {
-    static const int64_t v32 = env_or("LAMG_TAIL_WORK32", kTailWork32), v64 = env_or("LAMG_TAIL_WORK64", kTailWork64);
-    return prec == 1 ? v32 : v64;
+int64_t sb_work(int prec) { return prec == 1 ? kSBWork32 : kSBWork64; }
+int64_t tail_work(int prec) { return prec == 1 ? kTailWork32 : kTailWork64; }
+
+// blocks of the two-pass reductions: 4 per SM of the current device
+static int red_blocks() {
+    int dev = 0, sms = 0;
+    LAMG_CUDA(cudaGetDevice(&dev));
+    LAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return std::max(1, std::min(kRedBlocksMax, 4 * sms));
 }
 
 // scratch layout (doubles)
 enum {
-    SC_PART = 0,                     // kRedBlocks * 8 partial sums
-    SC_ALPHA = kRedBlocks * 8,       // recombination coefficients per level (2 each)
+    SC_PART = 0,                     // up to kRedBlocksMax * 8 partial sums
+    SC_ALPHA = kRedBlocksMax * 8,    // recombination coefficients per level (2 each)
     SC_NORM = SC_ALPHA + 2 * 128,    // result slots
     SC_TOTAL = SC_NORM + 16
 };
@@ -490,9 +488,10 @@ __global__ void k_finish_sum(const double *__restrict__ part, int nb, double *__
 }
 
 static void reduce_to(const double *a, int32_t n, int mode, double *part, double *out, cudaStream_t s) {
-    k_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a, mode, part);
+    const int nb = red_blocks();
+    k_partial<<<nb, kRedThreads, 0, s>>>(n, a, mode, part);
     LAMG_CHECK_LAUNCH();
-    k_finish_sum<<<1, 256, 0, s>>>(part, kRedBlocks, out);
+    k_finish_sum<<<1, 256, 0, s>>>(part, nb, out);
     LAMG_CHECK_LAUNCH();
 }
 
@@ -775,7 +774,6 @@ void solve_device(lamg_ctx *h, const double *b, double *x, double tol, lamg_prec
     k_scatter_perm<<<ceil_div(n, 256), 256, 0, s>>>(n, V0.perm.get(), xb, x);
     LAMG_CHECK_LAUNCH();
     LAMG_CUDA(cudaStreamSynchronize(s));
-    engine_report(h);
     auto t1 = std::chrono::steady_clock::now();
     lamg_stats &L = h->last;
     L.levels = h->L;

@@ -68,6 +68,7 @@ def _load():
     P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     sig = {
         "lamg_default_options": (None, [P]),
+        "lamg_op_times": (I32, [P, I32, I32, P, P, P, P, P, P]),
         "lamg_last_error": (C.c_char_p, []),
         "lamg_setup": (I32, [I64, P, P, P, I32, P, P, P]),
         "lamg_setup_graphs": (I32, [I32, P, I64, P, P, P, I32, P, P, P]),
@@ -304,6 +305,28 @@ def lamg_profile(h, enable: bool):
     byt = C.c_int64(0)
     _check(_lib.lamg_profile(h, int(enable), C.byref(avg), C.byref(cnt), C.byref(byt)), "lamg_profile")
     return avg.value, cnt.value, byt.value
+
+
+OP_NAMES = ["sweep", "sweep_run", "resid", "restrict", "zero", "coarse", "prolong", "recomb_dots",
+            "recomb_apply", "mean_part", "mean_apply", "ir_prep", "ir_update", "mean64_part", "mean64_apply",
+            "res64", "norm64", "sweep_smem", "gmean_part", "gmean_apply", "gmean64_part", "gmean64_apply",
+            "gnorm64", "tail_pre", "tail_run", "elim_restrict", "elim_prolong", "elim_back"]
+
+
+def lamg_op_times(h, mode: int, cap: int = 8192):
+    """The engine's op timer: mode 1 starts it, -1 stops it, 0 returns the rows
+    (level, op name, single_block, count, total_ms) recorded since the last read."""
+    lv = np.zeros(cap, np.int32)
+    op = np.zeros(cap, np.int32)
+    sb = np.zeros(cap, np.int32)
+    cnt = np.zeros(cap, np.int64)
+    ns = np.zeros(cap, np.float64)
+    nr = C.c_int32(0)
+    _check(_lib.lamg_op_times(h, int(mode), cap, lv.ctypes.data, op.ctypes.data, sb.ctypes.data,
+                              cnt.ctypes.data, ns.ctypes.data, C.byref(nr)), "lamg_op_times")
+    k = min(nr.value, cap)
+    return [(int(lv[i]), OP_NAMES[op[i]] if op[i] < len(OP_NAMES) else str(op[i]), int(sb[i]), int(cnt[i]),
+             ns[i] * 1e-6) for i in range(k)]
 
 
 def lamg_launch_count() -> int:

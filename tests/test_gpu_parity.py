@@ -294,3 +294,24 @@ def test_size_limits_rejected_before_any_work(L):
     with pytest.raises(L.LamgError) as e:
         L.Solver(2, rp, col, w)
     assert e.value.status == L.LAMG_ERR_ARG
+
+
+def test_op_timer(L):
+    # the engine's op timer: rows appear after a solve, reading zeroes the table,
+    # and stopping frees it (a read then returns nothing)
+    g = W.chung_lu(6000, seed=13)
+    s = L.Solver.from_graph(g)
+    b = torch.tensor(W.zero_sum_rhs(g.n, 3), device="cuda")
+    L.lamg_op_times(s.h, 1)
+    s.solve(b, tol=1e-8, precision=L.LAMG_FP32_IR)
+    rows = L.lamg_op_times(s.h, 0)
+    names = {r[1] for r in rows}
+    assert {"resid", "restrict", "prolong", "ir_prep", "res64"} <= names, names
+    assert all(r[3] > 0 and r[4] >= 0.0 for r in rows)
+    assert L.lamg_op_times(s.h, 0) == []
+    L.lamg_op_times(s.h, -1)
+    s.solve(b, tol=1e-8)
+    assert L.lamg_op_times(s.h, 0) == []
+    with pytest.raises(L.LamgError):
+        L.lamg_op_times(s.h, 2)
+    s.close()
