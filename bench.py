@@ -1,10 +1,11 @@
 """LAMG benchmark: one step = lamg_setup + lamg_solve to relative residual 1e-8
-on a device-resident synthetic graph (default: Chung-Lu, n = 1M, degree
-exponent 2.5, mean degree 10, FP32 weights, FP32 cycles inside FP64 iterative
-refinement), timed with CUDA events.  Prints one JSON line.
+on a device-resident synthetic graph (default: the 256^3 7-point grid with
+weights 1/1/0.01, n = 16.8M, FP32 cycles inside FP64 iterative refinement),
+timed with CUDA events.  Prints one JSON line; the Chung-Lu n = 1M workload is
+measured too and reported under "secondary".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload chung_lu1m|grid256|grid64|grid1024] [--precision fp32ir|fp64] [--elim]
+                  [--workload grid256|chung_lu1m|grid64|grid1024|...] [--precision fp32ir|fp64] [--elim]
 
 Multi-GPU: the solve of one graph does not shard (each relaxation sweep would
 need a halo exchange); N GPUs run N independent replicas of the step.  The
@@ -16,9 +17,11 @@ ranks' units / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -42,10 +45,49 @@ WORKLOADS = {
                        "red-black GS, gamma 1.5 at every level, flat mu 2; FP32 cycles in FP64 IR to 1e-8"),
 }
 TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10, "grid1024": 1e-8, "torus1024_lgmg": 1e-8}
-# DRAM bytes (read + write) of one engine launch from one ncu capture of this
-# workload (profiles/k_engine_chung_lu1m_fp32ir.md); must be emptied
-# whenever the engine kernel changes.
-NCU_TRAFFIC = {("chung_lu1m", "fp32ir"): 1.452e9}
+# The DRAM bytes (read + write) of one engine launch come from the committed
+# ncu summary of the workload, profiles/k_engine_<workload>_<precision>.md,
+# which records them with a hash of the engine's sources at capture time; when
+# the sources have changed since, the figure is stale and reported as null.
+ENGINE_SOURCES = ("cycle.cu", "engine.cuh", "solve_rows.cuh", "solve.cu")
+
+
+def engine_sources_sha():
+    h = hashlib.sha256()
+    for f in ENGINE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1108_1310_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, prec_name):
+    """(bytes per engine launch, source) from the committed capture, or (None, why)."""
+    p = os.path.join(ROOT, "profiles", f"k_engine_{workload}_{prec_name}.md")
+    if not os.path.exists(p):
+        return None, "no ncu capture of this workload"
+    with open(p) as f:
+        txt = f.read()
+    m_sha = re.search(r"engine_sources_sha256_16:\s*`?([0-9a-f]{16})", txt)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*`?([0-9.eE+]+)", txt)
+    if not (m_sha and m_tr):
+        return None, "capture without a traffic line"
+    if m_sha.group(1) != engine_sources_sha():
+        return None, "engine sources changed since the capture"
+    return float(m_tr.group(1)), f"profiles/{os.path.basename(p)}"
+
+
+def host_cpu():
+    """Model name and logical core count of this host (the CPU baseline's machine)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
 # batched forms (many right-hand sides on one hierarchy; many graphs as one union)
 ADJOINT = {
     "knn500k_adjoint": "kNN graph n=500k, k=10, 16-D Gaussian-mixture points, Gaussian weights FP32, all components "
@@ -58,7 +100,7 @@ BATCHED = {
     "er500": "500 Erdos-Renyi graphs (LCC), n uniform in [1k, 200k], mean degree 8, unit weights, one zero-sum "
              "RHS each, as one block-diagonal union (lamg_setup_graphs); FP32 cycles in FP64 IR to 1e-8 per graph",
 }
-CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 250_000), "grid256": ("grid3d", 64), "grid64": ("grid2d", 64),
+CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), "grid64": ("grid2d", 64),
               "grid1024": ("grid2d", 256),
               "torus1024_lgmg": ("torus", 1024)}
 
@@ -93,12 +135,20 @@ def sample_graph(workload):
     return W.grid2d(size, size), f"{size}x{size} 5-point grid"
 
 
-def cpu_oracle_step(g, b, tol, workload="", gamma_coarse_max=2.0, elim=0):
+def method_options(args, workload, n):
+    """The method's options of this run, shared by the library and the oracle, and
+    whether the solve is adaptive."""
+    mopts, adaptive = method_opts(workload, n)
+    opts = dict(gamma_coarse_max=args.gamma_coarse_max, elim=int(args.elim), agg_rule=args.agg_rule,
+                recomb_finest=args.recomb_finest, n_coarsest=args.n_coarsest, **mopts)
+    return opts, adaptive
+
+
+def cpu_oracle_step(g, b, tol, opts, adaptive):
     """The oracle as it stands: FP64 setup + solve on one host core."""
     import oracle
-    opts, adaptive = method_opts(workload, g.n)
     t0 = time.perf_counter()
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma_coarse_max=gamma_coarse_max, elim=elim, **opts)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, **opts)
     x, hist = h.solve(b, tol=tol, max_cycles=500, adaptive=adaptive)
     t = time.perf_counter() - t0
     return t, len(hist) - 1
@@ -161,11 +211,12 @@ def run_reference(args):
     g, desc = sample_graph(args.workload)
     b = W.zero_sum_rhs(g.n, 2)
     tol = TOL[args.workload]
+    opts, adaptive = method_options(args, args.workload, g.n)
     for _ in range(min(args.warmup, 1)):
-        cpu_oracle_step(g, b, tol, args.workload, args.gamma_coarse_max, elim=int(args.elim))
+        cpu_oracle_step(g, b, tol, opts, adaptive)
     ts, cyc = [], []
     for _ in range(args.steps):
-        t, c = cpu_oracle_step(g, b, tol, args.workload, args.gamma_coarse_max, elim=int(args.elim))
+        t, c = cpu_oracle_step(g, b, tol, opts, adaptive)
         ts.append(t)
         cyc.append(c)
     tmean = sum(ts) / len(ts)
@@ -175,10 +226,9 @@ def run_reference(args):
         "unit": "edges*cycles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": min(args.warmup, 1),
         "ms_per_step": tmean * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": desc, "n": g.n, "m": g.m, "tol": tol,
-                   "gamma_coarse_max": args.gamma_coarse_max, "elim": bool(args.elim)},
+        "config": {"workload": args.workload, "sample": desc, "n": g.n, "m": g.m, "tol": tol, **opts},
         "cpu_baseline": {"value": value, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "host": host_cpu()},
         "e2e": {"value": value, "unit": "edges*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -460,19 +510,24 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu")
-    ap.add_argument("--workload", default="chung_lu1m", choices=list(WORKLOADS) + list(BATCHED) + list(ADJOINT))
+    ap.add_argument("--workload", default="grid256", choices=list(WORKLOADS) + list(BATCHED) + list(ADJOINT))
     ap.add_argument("--precision", default=None, choices=["fp32ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the Chung-Lu n = 1M measurement that the default run adds")
     ap.add_argument("--elim", action="store_true",
                     help="low-degree elimination levels (Sec. 3.2) in the hierarchy (default workload only)")
-    ap.add_argument("--gamma-coarse-max", type=float, default=2.0,
-                    help="cap of the cycle index at the coarse levels (Eq. (4.1) prints 2)")
+    ap.add_argument("--gamma-coarse-max", type=float, default=1.0,
+                    help="cap of the cycle index at the coarse levels; Eq. (4.1) prints 2 (the library's "
+                         "default), the benchmark runs 1: the same cycle counts at far fewer colour phases")
     ap.add_argument("--agg-rule", type=int, default=2, choices=[0, 1, 2],
                     help="aggregation stages: 2 the paper's scan in hashed order (default), 1 in index order, "
                          "0 the parallel handshake")
     ap.add_argument("--recomb-finest", type=int, default=1, choices=[0, 1],
                     help="1: the adaptive cycle recombines at the finest level too (default)")
+    ap.add_argument("--n-coarsest", type=int, default=150,
+                    help="coarsening stops below this many nodes (Sec. 4.1: 150)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -498,52 +553,69 @@ def main():
         return run_batched(args, L, W, torch, dev, stream, rank, world, dist)
     if args.workload in ADJOINT:
         return run_adjoint(args, L, W, torch, dev, stream, rank, world, dist)
-    gname, pdef, desc = WORKLOADS[args.workload]
-    prec_name = args.precision or pdef
+    line = run_single(args, args.workload, L, W, torch, dev, stream, rank, world, local, dist, full=True)
+    if rank == 0 and args.workload == "grid256" and not args.no_secondary:
+        # the power-law workload of the same metric, measured the same way (fewer steps)
+        sec = run_single(args, "chung_lu1m", L, W, torch, dev, stream, rank, world, local, dist, full=False)
+        line["secondary"] = {"chung_lu1m": {k: sec[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup")}
+                             | {k: sec["config"][k] for k in ("levels", "cycles", "acf", "rel_res", "setup_s_host",
+                                                              "solve_s_host")}
+                             | {"roofline_frac": (sec["roofline"] or {}).get("frac"),
+                                "fp64_vs_ir": sec["fp64_vs_ir"]}}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_single(args, workload, L, W, torch, dev, stream, rank, world, local, dist, full):
+    """One graph: setup + solve to tol per step.  full: also the end-to-end form,
+    the CPU baseline and the clocks; otherwise only the device-timed steps and the
+    FP64 comparison (a secondary workload of the same run)."""
+    gname, pdef, desc = WORKLOADS[workload]
+    prec_name = (args.precision if full else None) or pdef
     prec = L.LAMG_FP32_IR if prec_name == "fp32ir" else L.LAMG_FP64
-    tol = TOL[args.workload]
+    tol = TOL[workload]
+    steps, warmup = (args.steps, args.warmup) if full else (min(args.steps, 3), 3)
     g = W.config_graph(gname)
     b_host = W.zero_sum_rhs(g.n, 2)
-    w_dtype = torch.float32 if args.workload == "chung_lu1m" else torch.float64
+    w_dtype = torch.float32 if workload == "chung_lu1m" else torch.float64
     rp = torch.tensor(g.rp, device=dev)
     col = torch.tensor(g.col, device=dev)
     w = torch.tensor(g.w, device=dev).to(w_dtype)
     b = torch.tensor(b_host, device=dev)
     x = torch.zeros_like(b)
-    mopts, adaptive = method_opts(args.workload, g.n)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000, adaptive=int(adaptive),
-                                 gamma_coarse_max=args.gamma_coarse_max, elim=int(args.elim),
-                                 agg_rule=args.agg_rule, recomb_finest=args.recomb_finest, **mopts)
+    mopts, adaptive = method_options(args, workload, g.n)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, adaptive=int(adaptive), **mopts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
-    def step(profile=False):
+    def step():
         h = L.lamg_setup(g.n, rp, col, w, opt, stream)
-        if profile:
-            L.lamg_profile(h, True)
+        # CUDA events around the engine launches only (two per launch, on this stream)
+        L.lamg_profile(h, True)
         x.zero_()
         st = L.lamg_solve(h, b, x, tol, prec, stream)
-        prof = L.lamg_profile(h, False) if profile else None
+        prof = L.lamg_profile(h, False)
         L.lamg_free(h)
         return st, prof
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
         flush.fill_(1.0)
     torch.cuda.synchronize()
     # timed region: each step bracketed by CUDA events; L2 flushed between steps
-    evs = []
-    stats = []
+    evs, stats = [], []
     prof_ms, prof_cnt, prof_bytes = 0.0, 0, 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = L.lamg_launch_count()
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st, prof = step(profile=True)
+            st, prof = step()
             e1.record(stream)
             evs.append((e0, e1))
             stats.append(st)
@@ -563,33 +635,29 @@ def main():
     # plain FP64 on the same workload, same accuracy (context for the IR form)
     fp64 = None
     if prec == L.LAMG_FP32_IR:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         h = L.lamg_setup(g.n, rp, col, w, opt, stream)
-        x.zero_()
-        L.lamg_solve(h, b, x, tol, L.LAMG_FP64, stream)  # warm graph
-        x.zero_()
-        flush.fill_(1.0)
-        e0.record(stream)
-        st64 = L.lamg_solve(h, b, x, tol, L.LAMG_FP64, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        x.zero_()
-        flush.fill_(1.0)
-        e2 = torch.cuda.Event(enable_timing=True)
-        e3 = torch.cuda.Event(enable_timing=True)
-        e2.record(stream)
-        st32 = L.lamg_solve(h, b, x, tol, prec, stream)
-        e3.record(stream)
-        torch.cuda.synchronize()
-        fp64 = {"solve_ms_fp64": e0.elapsed_time(e1), "cycles_fp64": st64.cycles,
-                "solve_ms_fp32ir": e2.elapsed_time(e3), "cycles_fp32ir": st32.cycles,
-                "rel_res_fp64": st64.rel_res, "rel_res_fp32ir": st32.rel_res}
+        res = {}
+        for name, p in (("fp64", L.LAMG_FP64), ("fp32ir", prec)):
+            x.zero_()
+            L.lamg_solve(h, b, x, tol, p, stream)  # warm
+            x.zero_()
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stp = L.lamg_solve(h, b, x, tol, p, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = (e0.elapsed_time(e1), stp)
+        fp64 = {"solve_ms_fp64": res["fp64"][0], "cycles_fp64": res["fp64"][1].cycles,
+                "solve_ms_fp32ir": res["fp32ir"][0], "cycles_fp32ir": res["fp32ir"][1].cycles,
+                "rel_res_fp64": res["fp64"][1].rel_res, "rel_res_fp32ir": res["fp32ir"][1].rel_res}
         L.lamg_free(h)
 
-    # end to end through the host-array API: graph + b from pinned host memory, x back
+    # end to end through the host-array API, the same K steps: the graph and b from
+    # pinned host memory, setup, solve, x back to the host; mean over the steps
     e2e = None
-    if not args.no_e2e:
+    if full and not args.no_e2e:
         rp_h = torch.tensor(g.rp).pin_memory()
         col_h = torch.tensor(g.col).pin_memory()
         w_h = torch.tensor(g.w).to(w_dtype).pin_memory()
@@ -598,8 +666,8 @@ def main():
         rp_d, col_d, w_d = torch.empty_like(rp), torch.empty_like(col), torch.empty_like(w)
         h2d = rp_h.numel() * 8 + col_h.numel() * 4 + w_h.numel() * w_h.element_size() + b_h.numel() * 8
         d2h = x_h.numel() * 8
-        tt = []
-        for it in range(2):
+        tt, cyc_e = [], []
+        for it in range(warmup + steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -610,39 +678,49 @@ def main():
             x_h.zero_()
             st = L.lamg_solve_host(h, b_h.numpy(), x_h.numpy(), tol, prec, stream)
             torch.cuda.synchronize()
-            tt.append(time.perf_counter() - t0)
             L.lamg_free(h)
-        te = min(tt)
-        e2e = {"value": world * g.m * st.cycles / te, "unit": "edges*cycles/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": te * 1e3}
+            if it >= warmup:
+                tt.append(time.perf_counter() - t0)
+                cyc_e.append(st.cycles)
+        te = sum(tt) / len(tt)
+        e2e = {"value": world * g.m * (sum(cyc_e) / len(cyc_e)) / te, "unit": "edges*cycles/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": te * 1e3,
+               "steps": steps, "statistic": "mean over the timed steps"}
 
     peak, peak_kind = load_peaks()
     roof = None
     if prof_cnt:
         avg = prof_ms / prof_cnt
         achieved = prof_bytes / (avg / 1e3) / 1e9
+        traffic, tsrc = profiled_traffic(workload, prec_name)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if args.elim else NCU_TRAFFIC.get((args.workload, prec_name)), "kernel": "cycle engine (one launch = one refinement step: ir_inner FP32 cycles + FP64 residual)",
+                "traffic": traffic, "traffic_source": tsrc,
+                "kernel": "cycle engine k_engine (one launch = one refinement step: ir_inner FP32 cycles + FP64 "
+                          "update, projection and residual)" if prec == L.LAMG_FP32_IR else
+                          "cycle engine k_engine (one launch = one FP64 cycle + residual)",
                 "bytes_per_launch": prof_bytes, "avg_ms": avg, "launches": prof_cnt,
-                "peak_kind": f"{peak_kind} hbm_gbs"}
+                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sg, sdesc = sample_graph(args.workload)
+    if full and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sg, sdesc = sample_graph(workload)
         sb = W.zero_sum_rhs(sg.n, 2)
-        t, c = cpu_oracle_step(sg, sb, tol, args.workload, args.gamma_coarse_max, elim=int(args.elim))
+        sopts, sadaptive = method_options(args, workload, sg.n)
+        t, c = cpu_oracle_step(sg, sb, tol, sopts, sadaptive)
+        same = sg.n == g.n and sg.m == g.m
         cpu = {"value": sg.m * c / t, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
-               "sample": f"{sdesc}, FP64 setup + solve to {tol:g}, {t:.1f} s"}
+               "sample": f"{sdesc}, FP64 setup + solve to {tol:g} with the same options: {c} cycles in {t:.1f} s"
+                         + ("" if same else "; rate per edge*cycle extrapolated to the full workload"),
+               "host": host_cpu()}
 
     s0 = stats[-1]
-    line = {
+    return {
         "metric": "edges*cycles/s (LAMG setup + solve to tol)",
-        "value": value, "unit": "edges*cycles/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "value": value, "unit": "edges*cycles/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == L.LAMG_FP32_IR else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "tol": tol,
-                   "precision": prec_name, "gamma_coarse_max": args.gamma_coarse_max, "elim": bool(args.elim),
-                   "agg_rule": args.agg_rule, "recomb_finest": args.recomb_finest, "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
+        "config": {"workload": workload, "desc": desc, "n": g.n, "m": g.m, "tol": tol,
+                   "precision": prec_name, **mopts, "levels": s0.levels, "cycles": cycles, "acf": s0.acf,
                    "rel_res": s0.rel_res, "time_to_tol_s": ms / 1e3,
                    "setup_s_host": s0.t_setup_s, "solve_s_host": s0.t_solve_s,
                    "model_bytes_per_cycle": s0.bytes_per_cycle32 if prec == L.LAMG_FP32_IR else s0.bytes_per_cycle,
@@ -654,10 +732,6 @@ def main():
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
-    if rank == 0:
-        print(json.dumps(line))
-    if dist:
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -193,6 +193,36 @@ __device__ __forceinline__ int32_t reduce_best(double bs, int32_t bv) {
     return rv[32];
 }
 
+// the preferred (score, index) pair of the tier, in every thread
+template <int M>
+__device__ __forceinline__ void reduce_best_pair(double &bs, int32_t &bv) {
+    if (M == M_THR) return;
+    for (int o = 16; o; o >>= 1) {
+        const double os = __shfl_xor_sync(kFull, bs, o);
+        const int32_t ov = __shfl_xor_sync(kFull, bv, o);
+        best_merge(bs, bv, os, ov);
+    }
+    if (M == M_WARP) return;
+    __shared__ double rs[33];
+    __shared__ int32_t rv[33];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { rs[threadIdx.x >> 5] = bs; rv[threadIdx.x >> 5] = bv; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double ss = rs[threadIdx.x];
+        int32_t v = rv[threadIdx.x];
+        for (int o = 16; o; o >>= 1) {
+            const double os = __shfl_xor_sync(kFull, ss, o);
+            const int32_t ov = __shfl_xor_sync(kFull, v, o);
+            best_merge(ss, v, os, ov);
+        }
+        if (threadIdx.x == 0) { rs[32] = ss; rv[32] = v; }
+    }
+    __syncthreads();
+    bs = rs[32];
+    bv = rv[32];
+}
+
 // Row addressing.  THR: thread i takes list[i] (or i when list is NULL) of n
 // rows; kernels skip rows above the thread tier.  WARP / BLK: one warp /
 // block per list entry.
@@ -1227,49 +1257,27 @@ __global__ void k_resolve(int32_t n, const int32_t *__restrict__ state, const in
 // The paper's aggregation scan (Sec. 3.4.2; agg_rule 1 and 2).  One stage visits
 // the undecided nodes in the order of rank (0 first); a node u that is still
 // undecided at its turn joins its best admissible neighbour that is a seed or
-// undecided (the largest score; an undecided one becomes a seed).  Parallel
-// rounds reproduce the sequential stage exactly.  A node is active while it is
-// undecided and has not had its turn.  u decides in a round when no active node
-// of smaller rank is a neighbour of u or a neighbour of an undecided neighbour of
-// u: only such nodes can change the states that u reads (its own, its
-// neighbours'), and states S, A and D never change again.  Nodes deciding in the
-// same round are then at least three edges apart, or share only seeds, so their
-// decisions commute.
+// undecided (the largest score, ties to the lower index; an undecided one
+// becomes a seed).  Parallel rounds reproduce the sequential stage exactly.
+//
+// A node is active while it is undecided and has not had its turn.  u's choice
+// is the first of its candidates, in its order of preference, that has not
+// become an associate; whether a candidate is a seed or undecided does not
+// change the choice, and a candidate becomes an associate only by its own turn.
+// Candidates ranked after u's best seed candidate never matter (a seed stays a
+// seed).  So u's decision is fixed once no active neighbour v of smaller rank
+//   (a) is a candidate of u preferred to u's best seed candidate (v may still
+//       become an associate), or
+//   (b) has u as a candidate preferred to v's own best seed candidate (v may
+//       still make u a seed).
+// Nodes deciding in the same round cannot touch each other's candidates or
+// themselves, so their decisions commute.  Every round decides at least the
+// active node of smallest rank.
 // ---------------------------------------------------------------------------
 
-constexpr int32_t kRankNone = 0x7fffffff;
-
-// (a, b): the two smallest ranks seen, a < b
-__device__ __forceinline__ void min2_merge(int32_t &a, int32_t &b, int32_t oa, int32_t ob) {
-    const int32_t lo = min(a, oa), hi = max(a, oa);
-    b = min(hi, min(b, ob));
-    a = lo;
-}
-
-template <int M>
-__device__ __forceinline__ void reduce_min2(int32_t &a, int32_t &b) {
-    if (M == M_THR) return;
-    for (int o = 16; o; o >>= 1) {
-        const int32_t oa = __shfl_xor_sync(kFull, a, o), ob = __shfl_xor_sync(kFull, b, o);
-        min2_merge(a, b, oa, ob);
-    }
-    if (M == M_WARP) return;
-    __shared__ int32_t ra[32], rb[32];
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) { ra[threadIdx.x >> 5] = a; rb[threadIdx.x >> 5] = b; }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        a = ra[threadIdx.x];
-        b = rb[threadIdx.x];
-        for (int o = 16; o; o >>= 1) {
-            const int32_t oa = __shfl_xor_sync(kFull, a, o), ob = __shfl_xor_sync(kFull, b, o);
-            min2_merge(a, b, oa, ob);
-        }
-        if (threadIdx.x == 0) { ra[0] = a; rb[0] = b; }
-    }
-    __syncthreads();
-    a = ra[0];
-    b = rb[0];
+// (s1, v1) preferred to (s2, v2): larger score, ties to the lower index; v2 < 0 is none
+__device__ __forceinline__ bool pref(double s1, int32_t v1, double s2, int32_t v2) {
+    return v2 < 0 || s1 > s2 || (s1 == s2 && v1 < v2);
 }
 
 // rank of each node in the scan order: by decreasing splitmix64(key + u), ties to
@@ -1292,37 +1300,58 @@ __global__ void k_scan_stage_init(int32_t n, const int32_t *__restrict__ state, 
     const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u < n) done[u] = state[u] != ST_U ? 1 : 0;
 }
-
-// per undecided node v: the two smallest ranks among its active neighbours
-template <int M>
-__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_scan_top2(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
-                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            const int32_t *__restrict__ rank, const int32_t *__restrict__ state,
-                            const uint8_t *__restrict__ done, int32_t *__restrict__ r1,
-                            int32_t *__restrict__ r2) {
-    int32_t v;
-    if (!get_row<M>(n, list, nlist, v)) return;
-    const int32_t s = rp[v], e = rp[v + 1];
-    if (M == M_THR && e - s > kLongRow) return;
-    if (state[v] != ST_U) return;   // read only for undecided v
-    int32_t a = kRankNone, b = kRankNone;
-    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
-        const int32_t w = col[j];
-        if (state[w] == ST_U && !done[w]) min2_merge(a, b, rank[w], kRankNone);
+// rev[j]: the entry (v -> u) of entry j = (u -> v); rows are sorted by column
+__global__ void k_rev_entries(int64_t nnz, const int32_t *__restrict__ erow, const int32_t *__restrict__ rp,
+                              const int32_t *__restrict__ col, int32_t *__restrict__ rev) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nnz) return;
+    const int32_t u = erow[j], v = col[j];
+    int32_t lo = rp[v], hi = rp[v + 1] - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (col[mid] < u) lo = mid + 1;
+        else hi = mid;
     }
-    reduce_min2<M>(a, b);
-    if (tlane<M>() == 0) { r1[v] = a; r2[v] = b; }
+    // a symmetric graph has col[lo] == u; otherwise (an unchecked input) -1
+    rev[j] = (lo < rp[v + 1] && col[lo] == u) ? lo : -1;
+}
+
+// per active node: its preferred seed candidate (score, index), or index -1
+template <int M>
+__global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_scan_bests(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
+                             const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const double *__restrict__ score, const int32_t *__restrict__ state,
+                             const uint8_t *__restrict__ done, double *__restrict__ bs_out,
+                             int32_t *__restrict__ bv_out) {
+    int32_t u;
+    if (!get_row<M>(n, list, nlist, u)) return;
+    const int32_t s = rp[u], e = rp[u + 1];
+    if (M == M_THR && e - s > kLongRow) return;
+    if (state[u] != ST_U || done[u]) return;   // read only for active nodes
+    double bs = -1.0;
+    int32_t bv = -1;
+    for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
+        const int32_t v = col[j];
+        const double sc = score[j];
+        if (sc >= 0.0 && state[v] == ST_S) best_merge(bs, bv, sc, v);
+    }
+    reduce_best_pair<M>(bs, bv);
+    if (tlane<M>() == 0) {
+        bv_out[u] = bv;
+        bs_out[u] = bs;
+    }
 }
 
 // per active node u: whether it decides this round, and its decision:
-// dec[u] = -2 (waits, or not active), -1 (no admissible neighbour), else the seed
+// dec[u] = -2 (waits, or not active), -1 (no candidate), else the chosen node
 template <int M>
 __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_scan_decide(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                               const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                              const double *__restrict__ score, const int32_t *__restrict__ rank,
-                              const int32_t *__restrict__ state, const uint8_t *__restrict__ done,
-                              const int32_t *__restrict__ r1, const int32_t *__restrict__ r2,
-                              int32_t *__restrict__ dec, int32_t *__restrict__ waiting) {
+                              const int32_t *__restrict__ rev, const double *__restrict__ score,
+                              const int32_t *__restrict__ rank, const int32_t *__restrict__ state,
+                              const uint8_t *__restrict__ done, const double *__restrict__ bs_seed,
+                              const int32_t *__restrict__ bv_seed, int32_t *__restrict__ dec,
+                              int32_t *__restrict__ waiting) {
     int32_t u;
     if (!get_row<M>(n, list, nlist, u)) return;
     const int32_t s = rp[u], e = rp[u + 1];
@@ -1332,19 +1361,23 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_scan_decide(int32_t
         return;
     }
     const int32_t ru = rank[u];
+    const double su = bs_seed[u];
+    const int32_t vu = bv_seed[u];
     bool blocked = false;
     double bs = -1.0;
     int32_t bv = -1;
     for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
         const int32_t v = col[j];
         const int32_t sv = state[v];
-        if (sv == ST_U) {
-            if (!done[v] && rank[v] < ru) blocked = true;
-            const int32_t m = r1[v] == ru ? r2[v] : r1[v];
-            if (m < ru) blocked = true;
-        }
         const double sc = score[j];
-        if (sc >= 0.0 && (sv == ST_U || sv == ST_S)) best_merge(bs, bv, sc, v);
+        const bool cand = sc >= 0.0 && (sv == ST_U || sv == ST_S);
+        if (sv == ST_U && !done[v] && rank[v] < ru) {
+            if (cand && pref(sc, v, su, vu)) blocked = true;                      // (a)
+            const int32_t rj = rev[j];
+            if (rj < 0) blocked = true;   // no reverse entry: wait for v (exact, conservative)
+            else if (score[rj] >= 0.0 && pref(score[rj], u, bs_seed[v], bv_seed[v])) blocked = true;  // (b)
+        }
+        if (cand) best_merge(bs, bv, sc, v);
     }
     blocked = reduce_any<M>(blocked);
     bv = reduce_best<M>(bs, bv);
@@ -1884,10 +1917,19 @@ static void aggregate_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &
     Tmp<unsigned long long> cnt(1, s);
     const bool scan = o.agg_rule != 0;
     const int max_stages = scan ? std::min(o.max_rounds, 2) : o.max_rounds;
-    Tmp<int32_t> rank(scan ? n : 0, s), r1(scan ? n : 0, s), r2(scan ? n : 0, s), dec(scan ? n : 0, s),
-        waiting(scan ? 1 : 0, s);
+    Tmp<int32_t> rank(scan ? n : 0, s), bvs(scan ? n : 0, s), dec(scan ? n : 0, s), waiting(scan ? 1 : 0, s),
+        rev(scan ? L.nnz : 0, s);
+    Tmp<double> bss(scan ? n : 0, s);
     Tmp<uint8_t> done(scan ? n : 0, s);
     if (scan) {
+        if (L.nnz > 0) {
+            Tmp<int32_t> erow(L.nnz, s);
+            LAUNCH3(k_entry_rows, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                    erow.get());
+            k_rev_entries<<<ceil_div(L.nnz, 256), 256, 0, s>>>(L.nnz, erow.get(), L.rp.get(), L.col.get(),
+                                                                rev.get());
+            LAMG_CHECK_LAUNCH();
+        }
         if (o.agg_rule == 1) {   // the paper's index order
             k_iota<<<ceil_div(n, 256), 256, 0, s>>>(n, rank.get());
             LAMG_CHECK_LAUNCH();
@@ -1910,11 +1952,11 @@ static void aggregate_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &
                 // every round decides at least the active node of smallest rank
                 LAMG_REQUIRE(round <= (int64_t)n, LAMG_ERR_CUDA, "aggregation scan: rounds did not converge");
                 LAMG_CUDA(cudaMemsetAsync(waiting.get(), 0, sizeof(int32_t), s));
-                LAUNCH3(k_scan_top2, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
-                        L.col.get(), rank.get(), state.get(), done.get(), r1.get(), r2.get());
+                LAUNCH3(k_scan_bests, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
+                        L.col.get(), score, state.get(), done.get(), bss.get(), bvs.get());
                 LAUNCH3(k_scan_decide, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s,
-                        L.rp.get(), L.col.get(), score, rank.get(), state.get(), done.get(), r1.get(), r2.get(),
-                        dec.get(), waiting.get());
+                        L.rp.get(), L.col.get(), rev.get(), score, rank.get(), state.get(), done.get(), bss.get(),
+                        bvs.get(), dec.get(), waiting.get());
                 k_scan_apply<<<ceil_div(n, 256), 256, 0, s>>>(n, dec.get(), state.get(), done.get(), seed.get(),
                                                               changed.get());
                 LAMG_CHECK_LAUNCH();
