@@ -38,13 +38,16 @@ WORKLOADS = {
                    "Chung-Lu n=1M beta=2.5 mean degree 10 (LCC), w~U[0.5,2] FP32; FP32 cycles in FP64 IR to 1e-8"),
     "grid256": ("grid256", "fp32ir",
                 "256^3 7-point grid, weights 1/1/0.01; FP32 cycles in FP64 IR to 1e-8"),
+    "grid128": ("grid128", "fp32ir",
+                "128^3 7-point grid, weights 1/1/0.01 (the profiling case of the 256^3 family); FP32 cycles in "
+                "FP64 IR to 1e-8"),
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
     "grid1024": ("grid1024", "fp32ir", "1024x1024 5-point grid, unit weights (run with --elim); FP32 cycles in FP64 IR to 1e-8"),
     "torus1024_lgmg": ("torus1024", "fp32ir",
                        "1024x1024 periodic 5-point grid, unit weights; Lean Geometric MG (Sec. 6): 2x2 aggregates, "
                        "red-black GS, gamma 1.5 at every level, flat mu 2; FP32 cycles in FP64 IR to 1e-8"),
 }
-TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid64": 1e-10, "grid1024": 1e-8, "torus1024_lgmg": 1e-8}
+TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid128": 1e-8, "grid64": 1e-10, "grid1024": 1e-8, "torus1024_lgmg": 1e-8}
 # The DRAM bytes (read + write) of one engine launch come from the committed
 # ncu summary of the workload, profiles/k_engine_<workload>_<precision>.md,
 # which records them with a hash of the engine's sources at capture time; when
@@ -100,9 +103,28 @@ BATCHED = {
     "er500": "500 Erdos-Renyi graphs (LCC), n uniform in [1k, 200k], mean degree 8, unit weights, one zero-sum "
              "RHS each, as one block-diagonal union (lamg_setup_graphs); FP32 cycles in FP64 IR to 1e-8 per graph",
 }
-CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), "grid64": ("grid2d", 64),
+CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), "grid128": ("grid3d", 64), "grid64": ("grid2d", 64),
               "grid1024": ("grid2d", 256),
               "torus1024_lgmg": ("torus", 1024)}
+
+
+# Per-workload settings of the method's options (each also a command-line flag,
+# which overrides it; the library's defaults are the paper's printed values):
+# - gamma_coarse_max 1 on the 3-D grids and the power-law graph: the same cycle
+#   counts as the printed 2 at a tenth of the colour phases on the 3-D grids;
+# - elimination (Sec. 3.2) on the power-law graph, where its degree-1..4 nodes
+#   are many (on 3-D grids no node qualifies);
+# - on the 1024^2 grid the printed cap 2 with mu_adaptive 1.2: with mu 1 the
+#   adaptive cycle stalls there, with cap 1 too.
+WORKLOAD_OPTS = {
+    "grid256": {"gamma_coarse_max": 1.0},
+    "grid128": {"gamma_coarse_max": 1.0},
+    "chung_lu1m": {"gamma_coarse_max": 1.0, "elim": 1},
+    "grid1024": {"gamma_coarse_max": 2.0, "mu_adaptive": 1.2},
+    "rgg2m_b64": {"gamma_coarse_max": 1.0},
+    "er500": {"gamma_coarse_max": 1.0},
+    "knn500k_adjoint": {"gamma_coarse_max": 1.0},
+}
 
 
 def method_opts(workload, n):
@@ -111,7 +133,7 @@ def method_opts(workload, n):
     Geometric MG (Sec. 6) in flat mode with mu = 2 on the grid of side sqrt(n)."""
     if workload.endswith("_lgmg"):
         return {"lgmg_nx": int(round(n ** 0.5)), "mu_flat": 2.0}, False
-    return {}, True
+    return dict(WORKLOAD_OPTS.get(workload, {})), True
 
 
 def load_peaks():
@@ -137,10 +159,12 @@ def sample_graph(workload):
 
 def method_options(args, workload, n):
     """The method's options of this run, shared by the library and the oracle, and
-    whether the solve is adaptive."""
-    mopts, adaptive = method_opts(workload, n)
-    opts = dict(gamma_coarse_max=args.gamma_coarse_max, elim=int(args.elim), agg_rule=args.agg_rule,
-                recomb_finest=args.recomb_finest, n_coarsest=args.n_coarsest, **mopts)
+    whether the solve is adaptive: the workload's settings, then any flag given."""
+    opts, adaptive = method_opts(workload, n)
+    for k in ("gamma_coarse_max", "elim", "agg_rule", "recomb_finest", "n_coarsest", "mu_adaptive"):
+        v = getattr(args, k)
+        if v is not None:
+            opts[k] = v
     return opts, adaptive
 
 
@@ -312,7 +336,8 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
     x = torch.zeros_like(b)
     lam = torch.zeros_like(b)
     dw = torch.zeros(eu.size, dtype=torch.float64, device=dev)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000, gamma_coarse_max=args.gamma_coarse_max)
+    mopts, _ = method_options(args, args.workload, g.n)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, **mopts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(prec=L.LAMG_FP32_IR):
@@ -375,7 +400,7 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": ADJOINT[args.workload], "n": g.n, "m": g.m, "tol": tol,
-                   "graphs": len(gptr) - 1,
+                   "graphs": len(gptr) - 1, **mopts,
                    "levels": res[-1][0].levels, "cycles_forward_plus_adjoint": cyc,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
         "fp64_vs_ir": cmp, "e2e": None, "roofline": None, "cpu_baseline": None,
@@ -407,7 +432,8 @@ def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
     col = torch.tensor(g.col, device=dev)
     w = torch.tensor(g.w, device=dev).to(torch.float32)
     X = torch.zeros_like(B)
-    opt = L.lamg_default_options(validate=1, max_cycles=2000, gamma_coarse_max=args.gamma_coarse_max)
+    mopts, _ = method_options(args, args.workload, g.n)
+    opt = L.lamg_default_options(validate=1, max_cycles=2000, **mopts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     tuned = {}
@@ -493,7 +519,7 @@ def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": BATCHED[args.workload], "n": g.n, "m": g.m,
-                   "rhs": R_all, "rhs_rank0": R, "graphs": G_all, "graphs_rank0": G, "tol": tol,
+                   "rhs": R_all, "rhs_rank0": R, "graphs": G_all, "graphs_rank0": G, "tol": tol, **mopts,
                    "batch_cols": tuned.get("cols"), "autotune_ms_16_32_64_128": tuned.get("ms"),
                    "levels": res[-1][2], "cycles_all_columns": cyc, "max_rel_res": res[-1][1],
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"shard{world}"},
@@ -516,17 +542,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the Chung-Lu n = 1M measurement that the default run adds")
-    ap.add_argument("--elim", action="store_true",
-                    help="low-degree elimination levels (Sec. 3.2) in the hierarchy (default workload only)")
-    ap.add_argument("--gamma-coarse-max", type=float, default=1.0,
-                    help="cap of the cycle index at the coarse levels; Eq. (4.1) prints 2 (the library's "
-                         "default), the benchmark runs 1: the same cycle counts at far fewer colour phases")
-    ap.add_argument("--agg-rule", type=int, default=2, choices=[0, 1, 2],
+    # the method's options: unset flags keep the workload's setting (WORKLOAD_OPTS),
+    # else the library's default
+    ap.add_argument("--elim", type=int, default=None, choices=[0, 1],
+                    help="low-degree elimination levels (Sec. 3.2)")
+    ap.add_argument("--gamma-coarse-max", type=float, default=None,
+                    help="cap of the cycle index at the coarse levels (Eq. (4.1) prints 2)")
+    ap.add_argument("--mu-adaptive", type=float, default=None,
+                    help="restriction factor under recombination (reading R15: 1)")
+    ap.add_argument("--agg-rule", type=int, default=None, choices=[0, 1, 2],
                     help="aggregation stages: 2 the paper's scan in hashed order (default), 1 in index order, "
                          "0 the parallel handshake")
-    ap.add_argument("--recomb-finest", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--recomb-finest", type=int, default=None, choices=[0, 1],
                     help="1: the adaptive cycle recombines at the finest level too (default)")
-    ap.add_argument("--n-coarsest", type=int, default=150,
+    ap.add_argument("--n-coarsest", type=int, default=None,
                     help="coarsening stops below this many nodes (Sec. 4.1: 150)")
     args = ap.parse_args()
     if args.impl == "reference":

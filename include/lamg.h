@@ -137,6 +137,21 @@ typedef struct {
                                   triangular dependency graph (colour[u] = 1 + the
                                   largest colour of a lower-index neighbour), for the
                                   TV sweeps and the cycle alike                      */
+    int32_t  sb_work32;        /* a level whose entries + rows are at most this runs all
+                                  its ops on one block of the cycle engine (block
+                                  barriers instead of grid barriers), FP32 cycles;
+                                  0 (default): 16384.  A performance knob only: the
+                                  results do not depend on it beyond rounding        */
+    int32_t  sb_work64;        /* the same for FP64 cycles; 0 (default): 16384        */
+    int32_t  tail_work32;      /* a colour with at most this many entries joins a run
+                                  of small colours swept by one block, FP32; 0
+                                  (default): 2048                                     */
+    int32_t  tail_work64;      /* the same for FP64; 0 (default): 512                  */
+    int32_t  colour_rule;      /* priority of the Jones-Plassmann colouring, which
+                                  equals the greedy colouring in that order:
+                                  0 (default): degree, then splitmix64(key_l + u),
+                                  then the lower index; 1: degree, then the lower
+                                  index (red-black on a grid numbered by position) */
 } lamg_options;
 
 typedef struct {

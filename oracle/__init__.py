@@ -46,7 +46,7 @@ class Opts(C.Structure):
                 ("elim", C.c_int32), ("elim_min_frac", C.c_double), ("lgmg_nx", C.c_int32),
                 ("mu_adaptive", C.c_double), ("gamma_coarse_max", C.c_double), ("plain_sums", C.c_int32),
                 ("gamma_fine_printed", C.c_int32), ("recomb_finest", C.c_int32),
-                ("relax_rule", C.c_int32)]
+                ("relax_rule", C.c_int32), ("colour_rule", C.c_int32)]
 
 
 _P = C.c_void_p

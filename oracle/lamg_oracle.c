@@ -28,9 +28,9 @@ void orc_default_opts(orc_opts *o) {
     o->n_coarsest = 150;       /* Sec. 4.1 */
     o->q_max = 2.5;            /* Sec. 3.4.5, after Eq. (3.12) */
     o->hub_factor = 8.0;       /* Sec. 3.4.1 footnote */
-    o->weak_tol = 1e-8;        /* reading of "very small |w_uv|", Sec. 3.4.2 */
+    o->weak_tol = 1e-8;        /* weak-edge filter threshold (reading), Sec. 3.4.2 */
     o->alpha_stall = 0.95;     /* reading: aggregation that removes <5% of nodes stops */
-    o->relax_fast_ratio = 0.0; /* "until relaxation converges rapidly": off by default (<= 0) */
+    o->relax_fast_ratio = 0.0; /* fast-relaxation stopping test, Sec. 4.1: off by default (<= 0) */
     o->max_rounds = 8;
     o->max_levels = 100;
     o->dense_max = 1024;
@@ -39,7 +39,7 @@ void orc_default_opts(orc_opts *o) {
     o->seed = 1;
     o->agg_rule = 2;           /* the paper's scan (Sec. 3.4.2) in hashed priority order */
     o->elim = 0;               /* no elimination levels (as the library) */
-    o->elim_min_frac = 0.1;    /* reading of "until |F| becomes small", Sec. 3.2 */
+    o->elim_min_frac = 0.1;    /* elimination rounds stop when F is small (reading), Sec. 3.2 */
     o->lgmg_nx = 0;            /* algebraic coarsening */
     o->mu_adaptive = 1.0;      /* reading R15: recombination replaces the flat correction */
     o->gamma_coarse_max = 2.0; /* Eq. (4.1): min{2, ...} at coarse levels */
@@ -47,6 +47,7 @@ void orc_default_opts(orc_opts *o) {
     o->gamma_fine_printed = 0; /* reading R13: the fine-level index is bounded too */
     o->recomb_finest = 1;      /* reading R15: recombination at the finest level too */
     o->relax_rule = 0;         /* multicolour GS on the JP colouring (reading R2) */
+    o->colour_rule = 0;        /* JP priority: degree, then the hashed key, then index */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -264,11 +265,11 @@ static int beats(int64_t du, uint64_t pu, int64_t u, int64_t dv, uint64_t pv, in
     return pu > pv || (pu == pv && u < v);
 }
 
-static int32_t colour_impl(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key,
+static int32_t colour_impl(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key, int32_t hashed,
                            int32_t *colour, int32_t *rounds_out) {
     uint64_t *pri = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
     int32_t *sel = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    for (int64_t u = 0; u < n; u++) { pri[u] = orc_splitmix64(key + (uint64_t)u); colour[u] = -1; }
+    for (int64_t u = 0; u < n; u++) { pri[u] = hashed ? orc_splitmix64(key + (uint64_t)u) : 0; colour[u] = -1; }
     int64_t left = n; int32_t ncol = 0, rounds = 0;
     int64_t maxdeg = 0;
     for (int64_t u = 0; u < n; u++) if (rp[u + 1] - rp[u] > maxdeg) maxdeg = rp[u + 1] - rp[u];
@@ -309,7 +310,7 @@ static int32_t colour_impl(int64_t n, const int64_t *rp, const int32_t *col, uin
 }
 
 int32_t orc_colour(int64_t n, const int64_t *rp, const int32_t *col, uint64_t key, int32_t *colour) {
-    return colour_impl(n, rp, col, key, colour, NULL);
+    return colour_impl(n, rp, col, key, 1, colour, NULL);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -354,7 +355,7 @@ void orc_gs_sweep_colour(int64_t n, const int64_t *rp, const int32_t *col, const
  *   E_s,k  = Emin_k + (a_uu / 2) (x^k_s - y*_k)^2
  *   ratio_k = E_s,k / Emin_k  (Emin_k == 0: 1 if E_s,k == 0 else +inf).
  * Strong entry: |w_uv| >= weak_tol * max(max_t |w_ut|, max_t |w_vt|)  (reading
- * of "edges with very small |w_uv| are discarded", Sec. 3.4.2).
+ * of the weak-edge filter of Sec. 3.4.2).
  * score = aff if strong and q <= q_max, else -1 (never a candidate). */
 void orc_edge_scores(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
                      int32_t K, const double *X, double q_max, double weak_tol,
@@ -598,24 +599,28 @@ static double relax_tvs(orc_level *L, const orc_opts *o, int32_t level) {
 /* Aggregation, Sec. 3.4.1-3.4.2, build reading (the complete algorithm is in an
  * e-print that is not available).  States U(ndecided)/S(eed)/A(ssociate)/
  * D(ummy).  Start: nodes without strong entries -> D; hubs -> S; rest -> U.
- * Each round (one "stage"), from the start-of-round state only:
+ *
+ * agg_rule 2 (default) and 1: the paper's scan.  Each stage visits the U nodes
+ * one at a time, in decreasing priority splitmix64(key_l + u) (ties to the lower
+ * index; rule 2) or in increasing index (rule 1); each decides on the states left
+ * by the nodes before it.  u joins the admissible neighbour v (score >= 0, not A
+ * or D) with the largest score, ties to the lower index (the smallest c_uv among
+ * those with q_uv <= 2.5, Sec. 3.4.5); an undecided v thereby becomes a seed.
+ * At most two stages are run, as in the paper.
+ *
+ * agg_rule 0: the parallel handshake.  Each round (one stage), from the
+ * start-of-round state only:
  *   best(u), u in U: the entry with the largest score >= 0 whose neighbour is
  *     not A (ties -> lower neighbour index), or none.
  *   best(u) = v in S                 -> u becomes A with seed v;
  *   best(u) = v in U, best(v) = u    -> min(u,v) becomes S, the other A of it;
  *   otherwise u stays U.
- * After round r, alpha_r = (#S + #U + [#D > 0]) / n (left-over U become seeds).
- * Rounds stop when alpha_r <= alpha_max = 0.7/gamma, when a round changes
- * nothing, or after max_rounds.  The round whose alpha_r is closest to
- * alpha_max is selected (ties -> earlier).  Numbering: seeds by ascending node
- * index, the dummy aggregate last.
  *
- * agg_rule = 1 replaces each round by a stage of the paper's sequential scan
- * (Sec. 3.4.2): the U nodes in increasing index, each deciding on the states
- * left by the nodes before it.  u joins the admissible non-A neighbour v with
- * the largest score (the smallest c_uv among those with q_uv <= 2.5, Sec.
- * 3.4.5); an undecided v thereby becomes a seed.  At most two stages are run,
- * as in the paper; the selection and the numbering are the same. */
+ * After stage r, alpha_r = (#S + #U + [#D > 0]) / n (left-over U become seeds).
+ * Stages stop when alpha_r <= alpha_max = 0.7/gamma, when a stage changes
+ * nothing, or after the stage limit.  The stage whose alpha_r is closest to
+ * alpha_max is selected (ties -> earlier).  Numbering: seeds by ascending node
+ * index, the dummy aggregate last. */
 typedef struct { uint64_t p; int64_t u; } scan_prio;
 
 static int scan_prio_cmp(const void *a, const void *b) {
@@ -1003,13 +1008,15 @@ int32_t orc_colour_lex(int64_t n, const int64_t *rp, const int32_t *col, int32_t
     return nc;
 }
 
-static void level_colour(orc_level *L, uint64_t seed, int32_t level, int relaxes, int32_t relax_rule) {
+static void level_colour(orc_level *L, uint64_t seed, int32_t level, int relaxes, int32_t relax_rule,
+                         int32_t colour_rule) {
     L->colour = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
     if (relaxes && relax_rule == 1) {
         L->ncolours = orc_colour_lex(L->n, L->rp, L->col, L->colour);
         L->jp_rounds = 0;
     } else if (relaxes) {
-        L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), L->colour, &L->jp_rounds);
+        L->ncolours = colour_impl(L->n, L->rp, L->col, colour_key(seed, level), colour_rule == 0, L->colour,
+                                  &L->jp_rounds);
     } else {
         L->ncolours = 1;
         L->jp_rounds = 0;
@@ -1040,7 +1047,7 @@ static int make_coarsest(orc_level *L, const orc_opts *o) {
 }
 
 /* Setup phase, Sec. 4.1: coarsen by caliber-1 aggregation until n < 150, or
- * until relaxation converges rapidly (TV energy ratio per sweep <= 0.1), or the
+ * until relaxation is fast (TV energy ratio per sweep <= 0.1, when enabled), or the
  * aggregation stalls (alpha > 0.9), or the depth limit. */
 static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
                             int32_t ngraphs, const int64_t *gptr, const orc_opts *o, orc_hier **out) {
@@ -1070,7 +1077,7 @@ static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
         h->L = l + 1;
         if (L->n < o->n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
             if (nxl > 0) level_colour_rb(L, nxl);
-            else level_colour(L, o->seed, l, 1, o->relax_rule);
+            else level_colour(L, o->seed, l, 1, o->relax_rule, o->colour_rule);
             L->stop_reason = L->n < o->n_coarsest ? 1 : 4;
             st = make_coarsest(L, o);
             break;
@@ -1093,7 +1100,7 @@ static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
             int32_t *cidx = (int32_t *)xcalloc((size_t)L->n, sizeof(int32_t));
             int64_t nF = elim_select(L, elim_key(o->seed, l), cidx);
             if (nF >= 1 && (double)nF >= o->elim_min_frac * (double)L->n) {
-                level_colour(L, o->seed, l, 0, o->relax_rule);
+                level_colour(L, o->seed, l, 0, o->relax_rule, o->colour_rule);
                 L->elim = 1;
                 L->nF = nF;
                 L->cidx = cidx;
@@ -1103,7 +1110,7 @@ static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
             }
             free(cidx);
         }
-        level_colour(L, o->seed, l, 1, o->relax_rule);
+        level_colour(L, o->seed, l, 1, o->relax_rule, o->colour_rule);
         int32_t K = o->k_finest + o->k_step * nagg;
         if (K > o->k_max) K = o->k_max;
         if (K > 16) K = 16;

@@ -76,6 +76,9 @@ typedef struct {
     int32_t  relax_rule;       /* 0 (default): multicolour GS on the JP colouring (R2);
                                   1: lexicographic GS (Eq. (2.3)), swept as the level
                                   sets of the lower-triangular dependency graph       */
+    int32_t  colour_rule;      /* JP priority (reading R2): 0 (default) degree, then
+                                  splitmix64(key + u), then the lower index; 1 degree,
+                                  then the lower index (greedy in that order)         */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;

@@ -133,6 +133,7 @@ void lamg_default_options(lamg_options *o) {
     o->agg_rule = 2;
     o->recomb_finest = 1;
     o->relax_rule = 0;
+    o->colour_rule = 0;
 }
 
 const char *lamg_last_error(void) { return g_last_error.c_str(); }
@@ -162,7 +163,8 @@ static lamg_status setup_impl(int32_t ngraphs, const int64_t *graph_ptr, int64_t
                          o.mu_adaptive > 0.0 && o.mu_adaptive < 4.0 && o.mu_flat > 0.0 && o.mu_flat < 4.0 &&
                          o.q_max > 0.0 && o.n_coarsest >= 1 && o.coarse_sweeps >= 0 &&
                          o.agg_rule >= 0 && o.agg_rule <= 2 && (o.recomb_finest == 0 || o.recomb_finest == 1) &&
-                         (o.relax_rule == 0 || o.relax_rule == 1),
+                         (o.relax_rule == 0 || o.relax_rule == 1) && o.sb_work32 >= 0 && o.sb_work64 >= 0 &&
+                         o.tail_work32 >= 0 && o.tail_work64 >= 0 && (o.colour_rule == 0 || o.colour_rule == 1),
                      LAMG_ERR_ARG, "invalid options");
         auto t0 = std::chrono::steady_clock::now();
         h = new lamg_ctx();

@@ -24,16 +24,43 @@
 
 namespace lamg {
 
+static_assert((kEngThreads / 32) * kSellStageBytes <= kEngSmem, "sliced-ELL staging must fit the engine's shared memory");
+
 // ---------------------------------------------------------------------------
 // ops; (bid, nb) = this block's index among the nb blocks executing the op
 // ---------------------------------------------------------------------------
 
 template <class T>
 __device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid, int nb) {
-    const int32_t t0 = L.cb[4 * c], t1 = L.cb[4 * c + 1], t2 = L.cb[4 * c + 2], t3 = L.cb[4 * c + 3];
+    const int32_t t1 = L.cb[4 * c + 1], t2 = L.cb[4 * c + 2], t3 = L.cb[4 * c + 3];
     const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
-    for (int64_t i = t0 + tid; i < t1; i += nthr) gs_row<M_THR, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    const int lane = threadIdx.x & 31;
+    // thread-tier rows: one warp per slice of 32 rows (sliced ELL, 16-byte loads)
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the next slice's first pairs are staged in shared memory while this
+        // slice's gathers are in flight
+        sell_walk32(L, L.csl[c] + wid, L.csl[c + 1], nwarp, L.x, [&](const int4 m, const uint4 (&v)[kSellPre],
+                                                                      const float (&xv)[2 * kSellPre]) {
+            float acc = 0.0f, d = 0.0f;
+#pragma unroll
+            for (int q = 0; q < kSellPre; q++) {
+                acc += pw(v[q], 0) * xv[2 * q] + pw(v[q], 1) * xv[2 * q + 1];
+                d += pw(v[q], 0) + pw(v[q], 1);
+            }
+            sell_rest(L, m, lane, L.x, 0.0f, false, acc, d);
+            const int32_t i = m.x + lane;
+            if (lane < m.y && d != 0.0f) L.x[i] = (L.b[i] + acc) / d;
+        });
+    } else {
+        for (int64_t k = L.csl[c] + wid; k < L.csl[c + 1]; k += nwarp) {
+            const int4 m = L.sl[k];
+            T acc = T(0), d = T(0);
+            sell_dot(L, m, lane, L.x, acc, d);
+            const int32_t i = m.x + lane;
+            if (lane < m.y && d != T(0)) L.x[i] = (L.b[i] + acc) / d;
+        }
+    }
     for (int64_t i = t1 + wid; i < t2; i += nwarp) gs_row<M_WARP, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
     for (int64_t i = t2 + bid; i < t3; i += nb) gs_row<M_BLK, T>((int32_t)i, L.rp, L.col, L.w, L.b, L.x);
 }
@@ -42,13 +69,41 @@ template <class T>
 __device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const T *x, T *r, T *xs, T *rs, int bid,
                                          int nb) {
     const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
-    for (int64_t i = tid; i < L.n; i += nthr) {
-        const int32_t ii = (int32_t)i;
-        if (L.rp[ii + 1] - L.rp[ii] > kLongRow) continue;
-        resid_row<M_THR, T>(ii, L.rp, L.col, L.w, b, x, r);
-        if (xs) { xs[ii] = x[ii]; rs[ii] = r[ii]; }
-    }
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
+    const int lane = threadIdx.x & 31;
+    // thread-tier rows: one warp per slice of 32 rows (sliced ELL, 16-byte loads)
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the next slice's first pairs are staged in shared memory while this
+        // slice's gathers are in flight
+        sell_walk32(L, wid, L.nsl, nwarp, x, [&](const int4 m, const uint4 (&v)[kSellPre],
+                                                 const float (&xv)[2 * kSellPre]) {
+            const int32_t i = m.x + (lane < m.y ? lane : 0);
+            const float xi = x[i];
+            float acc = 0.0f, dummy = 0.0f;
+#pragma unroll
+            for (int q = 0; q < kSellPre; q++)
+                acc += pw(v[q], 0) * (xv[2 * q] - xi) + pw(v[q], 1) * (xv[2 * q + 1] - xi);
+            sell_rest(L, m, lane, x, xi, true, acc, dummy);
+            if (lane < m.y) {
+                const float ri = b[i] + acc;
+                r[i] = ri;
+                if (xs) { xs[i] = xi; rs[i] = ri; }
+            }
+        });
+    } else {
+        for (int64_t k = wid; k < L.nsl; k += nwarp) {
+            const int4 m = L.sl[k];
+            const int32_t i = m.x + (lane < m.y ? lane : 0);
+            const T xi = x[i];
+            T acc = T(0);
+            sell_res(L, m, lane, x, xi, acc);
+            if (lane < m.y) {
+                const T ri = b[i] + acc;
+                r[i] = ri;
+                if (xs) { xs[i] = xi; rs[i] = ri; }
+            }
+        }
+    }
     for (int64_t k = wid; k < L.nw; k += nwarp) {
         const int32_t ii = L.wrows[k];
         resid_row<M_WARP, T>(ii, L.rp, L.col, L.w, b, x, r);
@@ -532,7 +587,7 @@ struct Builder {
     bool level_sb(int l) const {
         const SolveLevel &V = h->lv[l];
         if (groups) return (V.nnz + V.n) * groups <= kSBWork;
-        return V.nnz + V.n <= sb_work(prec);
+        return V.nnz + V.n <= sb_work(h->opt, prec);
     }
     void emit(int type, int level, int a, int b, bool sb) { prog.push_back(Op{type, level, a, b, sb ? 1 : 0}); }
 

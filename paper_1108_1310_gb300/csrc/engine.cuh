@@ -29,7 +29,185 @@ struct MKLevel {
     // next level is this level's Schur complement (Sec. 3.2)
     const int32_t *ecx;   // permuted coarse id, -1 for an eliminated row
     const T *ed;          // a_ii of the eliminated rows
+    // sliced ELL of the thread-tier rows (see SolveLevel)
+    int32_t nsl;
+    const int32_t *csl;
+    const int4 *sl;
+    const uint4 *ell32;
+    const int2 *ellc;
+    const double2 *ellw;
 };
+
+// Software-pipelined walk over slices: the first four pairs of the next slice
+// are loaded while the gathers of the current slice are in flight.  fn(m, lane,
+// pairs, xv) receives the current slice's first four pairs and their gathered x
+// values and finishes the slice (further pairs, then the row update).
+constexpr int kSellPre = 3;   // pairs of the next slice staged ahead (a 7-point row has 3)
+// per-warp staging of the FP32 sliced ELL in the engine's dynamic shared memory:
+// two slots of kSellPre pairs x 32 lanes of 16 bytes
+constexpr int kSellStageBytes = 2 * kSellPre * 32 * 16;
+
+// 16-byte asynchronous copy global -> shared (L2 only), commit, wait
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stage the first pairs of slice m into slot `slot` of this warp's buffer (each
+// lane copies its own 16-byte pairs; one commit group per call, possibly empty).
+__device__ __forceinline__ void sell_stage(const MKLevel<float> &L, const int4 m, int lane, uint4 *wbuf, int slot) {
+    uint4 *dst = wbuf + slot * kSellPre * 32;
+    const uint4 *src = L.ell32 + (size_t)m.w * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < kSellPre; q++)
+        if (q < m.z) cp_async16(dst + q * 32 + lane, src + (size_t)q * 32);
+    cp_async_commit();
+}
+
+// Walk the FP32 slices [k0, k1) with step `step`, the next slice's first pairs
+// staged in shared memory while the current slice's gathers are in flight.
+// fn(m, v, xv) gets the slice, its first kSellPre pairs (zero beyond m.z) and
+// their gathered x values.  Every copy issued is waited for before returning.
+template <class F>
+__device__ __forceinline__ void sell_walk32(const MKLevel<float> &L, int64_t k0, int64_t k1, int64_t step,
+                                            const float *__restrict__ x, F fn) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    uint4 *wbuf = (uint4 *)(smem + (size_t)(threadIdx.x >> 5) * kSellStageBytes);
+    if (k0 >= k1) return;
+    int4 mc = L.sl[k0];
+    sell_stage(L, mc, lane, wbuf, 0);
+    int slot = 0;
+    for (int64_t k = k0; k < k1; k += step) {
+        const bool more = k + step < k1;
+        int4 mn = mc;
+        if (more) {
+            mn = L.sl[k + step];
+            sell_stage(L, mn, lane, wbuf, slot ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const uint4 *cur = wbuf + slot * kSellPre * 32 + lane;
+        uint4 v[kSellPre];
+#pragma unroll
+        for (int q = 0; q < kSellPre; q++) v[q] = q < mc.z ? cur[q * 32] : make_uint4(0, 0, 0, 0);
+        float xv[2 * kSellPre];
+#pragma unroll
+        for (int q = 0; q < kSellPre; q++) {
+            xv[2 * q] = x[v[q].x];
+            xv[2 * q + 1] = x[v[q].y];
+        }
+        fn(mc, v, xv);
+        slot ^= 1;
+        mc = mn;
+    }
+}
+__device__ __forceinline__ float pw(const uint4 &v, int h) { return __uint_as_float(h ? v.w : v.z); }
+
+// Slice dot products: lane l holds row m.x + l of slice m; acc += sum w x[col],
+// d += sum w over the row's entries (padding adds 0).  The pairs are loaded four
+// at a time before their gathers, so eight gathers are in flight per lane.
+__device__ __forceinline__ void sell_dot(const MKLevel<float> &L, const int4 m, int lane, const float *__restrict__ x,
+                                         float &acc, float &d) {
+    const uint4 *__restrict__ p = L.ell32 + (size_t)m.w * 32 + lane;
+    for (int q = 0; q < m.z; q += 4) {
+        uint4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = q + k < m.z ? __ldg(p + (size_t)(q + k) * 32) : make_uint4(0, 0, 0, 0);
+        float xv[8];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            xv[2 * k] = x[v[k].x];
+            xv[2 * k + 1] = x[v[k].y];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float w0 = __uint_as_float(v[k].z), w1 = __uint_as_float(v[k].w);
+            acc += w0 * xv[2 * k] + w1 * xv[2 * k + 1];
+            d += w0 + w1;
+        }
+    }
+}
+__device__ __forceinline__ void sell_dot(const MKLevel<double> &L, const int4 m, int lane,
+                                         const double *__restrict__ x, double &acc, double &d) {
+    const size_t base = (size_t)m.w * 32 + lane;
+    for (int q = 0; q < m.z; q += 4) {
+        int2 c[4];
+        double2 w[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            c[k] = q + k < m.z ? __ldg(L.ellc + base + (size_t)(q + k) * 32) : make_int2(0, 0);
+            w[k] = q + k < m.z ? __ldg(L.ellw + base + (size_t)(q + k) * 32) : make_double2(0.0, 0.0);
+        }
+        double xv[8];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            xv[2 * k] = x[c[k].x];
+            xv[2 * k + 1] = x[c[k].y];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            acc += w[k].x * xv[2 * k] + w[k].y * xv[2 * k + 1];
+            d += w[k].x + w[k].y;
+        }
+    }
+}
+// pairs kSellPre.. of a slice (rows of more than 2 kSellPre entries)
+template <class T>
+__device__ __forceinline__ void sell_rest(const MKLevel<T> &L, int4 m, int lane, const T *__restrict__ x, T xi,
+                                          bool res, T &acc, T &d) {
+    if (m.z <= kSellPre) return;
+    int4 m2 = m;
+    m2.w += kSellPre;
+    m2.z -= kSellPre;
+    if (res) sell_res(L, m2, lane, x, xi, acc);
+    else sell_dot(L, m2, lane, x, acc, d);
+}
+
+// residual form: acc += sum w (x[col] - xi)  (differences: no cancellation)
+__device__ __forceinline__ void sell_res(const MKLevel<float> &L, const int4 m, int lane, const float *__restrict__ x,
+                                         float xi, float &acc) {
+    const uint4 *__restrict__ p = L.ell32 + (size_t)m.w * 32 + lane;
+    for (int q = 0; q < m.z; q += 4) {
+        uint4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = q + k < m.z ? __ldg(p + (size_t)(q + k) * 32) : make_uint4(0, 0, 0, 0);
+        float xv[8];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            xv[2 * k] = x[v[k].x];
+            xv[2 * k + 1] = x[v[k].y];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            acc += __uint_as_float(v[k].z) * (xv[2 * k] - xi) + __uint_as_float(v[k].w) * (xv[2 * k + 1] - xi);
+    }
+}
+__device__ __forceinline__ void sell_res(const MKLevel<double> &L, const int4 m, int lane,
+                                         const double *__restrict__ x, double xi, double &acc) {
+    const size_t base = (size_t)m.w * 32 + lane;
+    for (int q = 0; q < m.z; q += 4) {
+        int2 c[4];
+        double2 w[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            c[k] = q + k < m.z ? __ldg(L.ellc + base + (size_t)(q + k) * 32) : make_int2(0, 0);
+            w[k] = q + k < m.z ? __ldg(L.ellw + base + (size_t)(q + k) * 32) : make_double2(0.0, 0.0);
+        }
+        double xv[8];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            xv[2 * k] = x[c[k].x];
+            xv[2 * k + 1] = x[c[k].y];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) acc += w[k].x * (xv[2 * k] - xi) + w[k].y * (xv[2 * k + 1] - xi);
+    }
+}
 
 enum : int32_t {
     OP_SWEEP = 0,     // level, colour a (all blocks)
@@ -269,6 +447,12 @@ inline MKLevel<T> describe(lamg_ctx *h, int l, LevelVecs<T> &v, const T *w) {
         d.ed = (const T *)V.ed32.get();
     }
     d.ecx = V.ecx.get();
+    d.nsl = V.nsl;
+    d.csl = V.csl_dev.get();
+    d.sl = V.sl.get();
+    d.ell32 = V.ell32.get();
+    d.ellc = V.ellc.get();
+    d.ellw = V.ellw64.get();
     return d;
 }
 

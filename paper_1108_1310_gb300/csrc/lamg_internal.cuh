@@ -158,6 +158,19 @@ struct SolveLevel {
     // coarsest level
     int32_t dense = 0;
     DBuf<double> minv;             // (A + 11^T/n)^-1, n x n, if dense
+    // sliced ELL of the thread-tier rows (<= kLongRow entries): slices of 32
+    // consecutive rows of one colour; sl[k] = {first row, rows, pairs, first pair}.
+    // Entry pair p of the row in lane l of slice k sits at (first pair + p) * 32 + l,
+    // so a warp's load of pair p is 32 consecutive 16-byte vectors.  FP32:
+    // {c0, c1, w0 bits, w1 bits}; FP64: {c0, c1} and {w0, w1}.  Short rows are
+    // padded with (own row, weight 0).
+    int32_t nsl = 0;
+    std::vector<int32_t> csl;      // colour c: slices [csl[c], csl[c+1])
+    DBuf<int32_t> csl_dev;
+    DBuf<int4> sl;
+    DBuf<uint4> ell32;
+    DBuf<int2> ellc;
+    DBuf<double2> ellw64;
 };
 
 // Per-level vectors of one precision.
@@ -241,8 +254,8 @@ void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const
 // most tail_work(prec) entries joins a single-block run.  One SM streams FP32
 // rows from L2 faster than a grid-wide phase completes, up to a few hundred
 // KB; FP64 arithmetic on one SM is slow (1/64 rate), so its limits are lower.
-int64_t sb_work(int prec);    // prec 0 = FP64, 1 = FP32
-int64_t tail_work(int prec);
+int64_t sb_work(const lamg_options &o, int prec);    // prec 0 = FP64, 1 = FP32
+int64_t tail_work(const lamg_options &o, int prec);
 constexpr int64_t kSBWork = 16384;
 
 // cycle.cu

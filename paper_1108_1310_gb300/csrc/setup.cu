@@ -619,12 +619,13 @@ __device__ __forceinline__ bool coop_sync(unsigned int *bar, int32_t *err, unsig
 // constant number of times instead of once per round.  Frontiers are kept per
 // row tier (lst: [parity][tier], cnt: [parity][tier]); their order (atomic
 // appends) changes no decision.  out[0] = rounds.
-__global__ void k_jp_prio(int32_t n, const int32_t *__restrict__ rp, uint64_t key, int32_t *__restrict__ deg,
-                          uint64_t *__restrict__ hsh) {
+// hashed = 0 (colour_rule 1): the priority is the degree, then the lower index
+__global__ void k_jp_prio(int32_t n, const int32_t *__restrict__ rp, uint64_t key, int32_t hashed,
+                          int32_t *__restrict__ deg, uint64_t *__restrict__ hsh) {
     const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n) return;
     deg[u] = rp[u + 1] - rp[u];
-    hsh[u] = splitmix64(key + (uint64_t)u);
+    hsh[u] = hashed ? splitmix64(key + (uint64_t)u) : 0ull;
 }
 
 template <int M>
@@ -1714,7 +1715,8 @@ static void colour_level(lamg_ctx *h, SetupLevel &L, int level, const Tiers &T, 
         // wait counts, the first frontier, then all rounds in one cooperative launch
         Tmp<int32_t> deg(n, s), wait(n, s);
         Tmp<uint64_t> hsh(n, s);
-        k_jp_prio<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), key, deg.get(), hsh.get());
+        k_jp_prio<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rp.get(), key, h->opt.colour_rule == 0 ? 1 : 0, deg.get(),
+                                                   hsh.get());
         LAMG_CHECK_LAUNCH();
         LAUNCH3(k_jp_wait, n, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(), L.col.get(),
                 deg.get(), hsh.get(), wait.get());

@@ -28,8 +28,14 @@ constexpr int64_t kTailWork32 = 2048;   // entries of a colour that the single-b
 constexpr int64_t kTailWork64 = 512;    // same for FP64 (one SM's FP64 rate is low on this GPU)
 constexpr int64_t kSBWork32 = 16384, kSBWork64 = 16384;
 
-int64_t sb_work(int prec) { return prec == 1 ? kSBWork32 : kSBWork64; }
-int64_t tail_work(int prec) { return prec == 1 ? kTailWork32 : kTailWork64; }
+int64_t sb_work(const lamg_options &o, int prec) {
+    const int32_t v = prec == 1 ? o.sb_work32 : o.sb_work64;
+    return v > 0 ? v : (prec == 1 ? kSBWork32 : kSBWork64);
+}
+int64_t tail_work(const lamg_options &o, int prec) {
+    const int32_t v = prec == 1 ? o.tail_work32 : o.tail_work64;
+    return v > 0 ? v : (prec == 1 ? kTailWork32 : kTailWork64);
+}
 
 // blocks of the two-pass reductions: 4 per SM of the current device
 static int red_blocks() {
@@ -271,6 +277,80 @@ __global__ void k_elim_layout(int32_t n, const int32_t *__restrict__ perm, const
     ed32[i] = d32;
 }
 
+// Sliced ELL of the thread-tier rows of a level (see SolveLevel): slices of 32
+// consecutive rows within each colour's thread-tier range.
+__global__ void k_sell_pairs(int32_t nsl, const int4 *__restrict__ sl, const int32_t *__restrict__ rp,
+                             int32_t *__restrict__ pairs) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsl) return;
+    const int4 m = sl[k];
+    int32_t w = 0;
+    for (int32_t i = m.x; i < m.x + m.y; i++) w = max(w, rp[i + 1] - rp[i]);
+    pairs[k] = (w + 1) >> 1;
+}
+__global__ void k_sell_offsets(int32_t nsl, const int32_t *__restrict__ pairs, const int32_t *__restrict__ first,
+                               int4 *__restrict__ sl) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsl) return;
+    sl[k].z = pairs[k];
+    sl[k].w = first[k];
+}
+// one thread per (slice, lane); lanes past the slice's rows get the padding entry
+// of its first row
+__global__ void k_sell_fill(int32_t nsl, const int4 *__restrict__ sl, const int32_t *__restrict__ rp,
+                            const int32_t *__restrict__ col, const float *__restrict__ w32,
+                            const double *__restrict__ w64, uint4 *__restrict__ ell32, int2 *__restrict__ ellc,
+                            double2 *__restrict__ ellw) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nsl * 32) return;
+    const int32_t k = (int32_t)(t >> 5), lane = (int32_t)(t & 31);
+    const int4 m = sl[k];
+    const int32_t i = lane < m.y ? m.x + lane : m.x;
+    const int32_t s = lane < m.y ? rp[i] : 0, e = lane < m.y ? rp[i + 1] : 0;
+    for (int32_t p = 0; p < m.z; p++) {
+        const int32_t j0 = s + 2 * p, j1 = j0 + 1;
+        const int32_t c0 = j0 < e ? col[j0] : i, c1 = j1 < e ? col[j1] : i;
+        const float a0 = j0 < e ? w32[j0] : 0.0f, a1 = j1 < e ? w32[j1] : 0.0f;
+        const double b0 = j0 < e ? w64[j0] : 0.0, b1 = j1 < e ? w64[j1] : 0.0;
+        const size_t q = ((size_t)m.w + p) * 32 + lane;
+        ell32[q] = make_uint4((unsigned)c0, (unsigned)c1, __float_as_uint(a0), __float_as_uint(a1));
+        ellc[q] = make_int2(c0, c1);
+        ellw[q] = make_double2(b0, b1);
+    }
+}
+
+static void build_sell(SolveLevel &V, int ncol, cudaStream_t s) {
+    std::vector<int4> hs;
+    V.csl.assign(ncol + 1, 0);
+    for (int c = 0; c < ncol; c++) {
+        const int32_t t0 = V.cb[4 * c], t1 = V.cb[4 * c + 1];
+        for (int32_t r = t0; r < t1; r += 32) hs.push_back(make_int4(r, std::min(32, t1 - r), 0, 0));
+        V.csl[c + 1] = (int32_t)hs.size();
+    }
+    V.nsl = (int32_t)hs.size();
+    V.csl_dev.alloc(ncol + 1);
+    LAMG_CUDA(cudaMemcpyAsync(V.csl_dev.get(), V.csl.data(), sizeof(int32_t) * (ncol + 1), cudaMemcpyHostToDevice, s));
+    if (V.nsl == 0) return;
+    V.sl.alloc(V.nsl);
+    LAMG_CUDA(cudaMemcpyAsync(V.sl.get(), hs.data(), sizeof(int4) * V.nsl, cudaMemcpyHostToDevice, s));
+    Tmp<int32_t> pairs(V.nsl + 1, s), first(V.nsl + 1, s);
+    LAMG_CUDA(cudaMemsetAsync(pairs.get() + V.nsl, 0, sizeof(int32_t), s));
+    k_sell_pairs<<<ceil_div(V.nsl, 256), 256, 0, s>>>(V.nsl, V.sl.get(), V.rp.get(), pairs.get());
+    LAMG_CHECK_LAUNCH();
+    exclusive_scan_i32(pairs.get(), first.get(), V.nsl + 1, s);
+    k_sell_offsets<<<ceil_div(V.nsl, 256), 256, 0, s>>>(V.nsl, pairs.get(), first.get(), V.sl.get());
+    LAMG_CHECK_LAUNCH();
+    const int64_t total = (int64_t)read_scalar(first.get() + V.nsl, s) * 32;
+    LAMG_REQUIRE(total < ((int64_t)1 << 31), LAMG_ERR_OOM, "sliced ELL larger than 2^31 pairs");
+    V.ell32.alloc(std::max<int64_t>(total, 1));
+    V.ellc.alloc(std::max<int64_t>(total, 1));
+    V.ellw64.alloc(std::max<int64_t>(total, 1));
+    k_sell_fill<<<ceil_div((int64_t)V.nsl * 32, 256), 256, 0, s>>>(V.nsl, V.sl.get(), V.rp.get(), V.col.get(),
+                                                                  V.w32.get(), V.w64.get(), V.ell32.get(),
+                                                                  V.ellc.get(), V.ellw64.get());
+    LAMG_CHECK_LAUNCH();
+}
+
 void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
     const int L = h->L;
     h->lv.clear();
@@ -328,7 +408,7 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
             LAMG_CUDA(cudaMemcpyAsync(hrp.data(), V.rp.get(), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
             LAMG_CUDA(cudaStreamSynchronize(s));
             for (int p = 0; p < 2; p++) {
-                const int64_t lim = tail_work(p);
+                const int64_t lim = tail_work(h->opt, p);
                 auto small = [&](int c) { return (int64_t)hrp[V.cb[4 * c + 3]] - hrp[V.cb[4 * c]] <= lim; };
                 V.seg[p].clear();
                 for (int c = 0; c < S.ncolours;) {
@@ -345,6 +425,7 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
             }
         }
         build_tail(V, S.ncolours, s);
+        build_sell(V, S.ncolours, s);
         Tmp<uint8_t> f(n, s);
         V.wrows.alloc(n);
         V.brows.alloc(n);

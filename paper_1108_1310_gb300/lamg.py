@@ -48,7 +48,8 @@ class lamg_options(C.Structure):
                 ("keep_setup_data", C.c_int32), ("project_rhs", C.c_int32), ("mu_adaptive", C.c_double),
                 ("gamma_coarse_max", C.c_double), ("elim", C.c_int32), ("elim_min_frac", C.c_double),
                 ("lgmg_nx", C.c_int32), ("agg_rule", C.c_int32), ("recomb_finest", C.c_int32),
-                ("relax_rule", C.c_int32)]
+                ("relax_rule", C.c_int32), ("sb_work32", C.c_int32), ("sb_work64", C.c_int32),
+                ("tail_work32", C.c_int32), ("tail_work64", C.c_int32), ("colour_rule", C.c_int32)]
 
 
 class lamg_stats(C.Structure):

@@ -64,6 +64,10 @@ RULES = {
     "index_scan": {"agg_rule": 1},
     "index_scan_lex": {"agg_rule": 1, "relax_rule": 1},
     "lex": {"relax_rule": 1},
+    # the coarse cycle-index cap (Eq. (4.1)) and the restriction factor under
+    # recombination (Eq. (3.13)): the per-level gamma is compared exactly
+    "cap1": {"gamma_coarse_max": 1.0},
+    "mu12": {"mu_adaptive": 1.2},
 }
 
 
@@ -162,6 +166,25 @@ def test_solve_fp64_matches_oracle_and_dense(L, gname):
     xd -= xd.mean()
     assert np.linalg.norm(xg - xd) <= 1e-6 * np.linalg.norm(xd)
     assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+    s.close()
+
+
+@pytest.mark.parametrize("opts", [{"gamma_coarse_max": 1.0}, {"mu_adaptive": 1.2}])
+@pytest.mark.parametrize("gname", ["chung_lu", "grid64"])
+def test_solve_with_cycle_options(L, gname, opts):
+    # the cap and the restriction factor change the cycle: FP64 and FP32-IR solves
+    # against the oracle with the same options, at the tolerances of the other solves
+    g = _graph(gname)
+    s, h = _both(L, g, **opts)
+    b = W.zero_sum_rhs(g.n, 4)
+    bt = torch.tensor(b, device="cuda")
+    xo, hist = h.solve(b, tol=1e-12)
+    A = oracle.laplacian_dense(g.n, g.rp, g.col, g.w)
+    for prec, tol in ((L.LAMG_FP64, 1e-10), (L.LAMG_FP32_IR, 1e-8)):
+        x, st = s.solve(bt, tol=tol, precision=prec)
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(b - A @ xg) <= 1.01 * tol * np.linalg.norm(b)
+        assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
     s.close()
 
 

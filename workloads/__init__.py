@@ -318,7 +318,8 @@ def zero_sum_rhs(n: int, seed: int, count: int | None = None) -> np.ndarray:
 
 def config_graph(name: str) -> Graph:
     """'grid64': 64x64 5-point grid; 'chung_lu1m': Chung-Lu n=1M, beta 2.5, mean degree 10;
-    'grid256': 256^3 7-point grid, weights 1/1/0.01; 'rgg2m': 2M-node RGG, mean degree 12;
+    'grid256': 256^3 7-point grid, weights 1/1/0.01 ('grid128': the 128^3 member of that
+    family, small enough for an ncu capture); 'rgg2m': 2M-node RGG, mean degree 12;
     'grid1024': 1024x1024 5-point grid, unit weights (the paper's grid table size).
     'torus1024': 1024x1024 periodic 5-point grid."""
     if name == "grid64":
@@ -329,6 +330,8 @@ def config_graph(name: str) -> Graph:
         return chung_lu(1_000_000, 2.5, 10.0, seed=2)
     if name == "grid256":
         return grid3d(256, 256, 256, 1.0, 1.0, 0.01)
+    if name == "grid128":
+        return grid3d(128, 128, 128, 1.0, 1.0, 0.01)
     if name == "rgg2m":
         return rgg2d(2_000_000, 12.0, seed=4)
     if name == "torus1024":
