@@ -117,8 +117,8 @@ CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), 
 # - on the 1024^2 grid the printed cap 2 with mu_adaptive 1.2: with mu 1 the
 #   adaptive cycle stalls there, with cap 1 too.
 WORKLOAD_OPTS = {
-    "grid256": {"gamma_coarse_max": 1.0},
-    "grid128": {"gamma_coarse_max": 1.0},
+    "grid256": {"gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
+    "grid128": {"gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
     "chung_lu1m": {"gamma_coarse_max": 1.0, "elim": 1},
     "grid1024": {"gamma_coarse_max": 2.0, "mu_adaptive": 1.2},
     "rgg2m_b64": {"gamma_coarse_max": 1.0},
@@ -161,7 +161,7 @@ def method_options(args, workload, n):
     """The method's options of this run, shared by the library and the oracle, and
     whether the solve is adaptive: the workload's settings, then any flag given."""
     opts, adaptive = method_opts(workload, n)
-    for k in ("gamma_coarse_max", "elim", "agg_rule", "recomb_finest", "n_coarsest", "mu_adaptive"):
+    for k in ("gamma_coarse_max", "elim", "agg_rule", "recomb_finest", "n_coarsest", "mu_adaptive", "colour_rule"):
         v = getattr(args, k)
         if v is not None:
             opts[k] = v
@@ -171,8 +171,10 @@ def method_options(args, workload, n):
 def cpu_oracle_step(g, b, tol, opts, adaptive):
     """The oracle as it stands: FP64 setup + solve on one host core."""
     import oracle
+    # the method's options (performance knobs of the GPU engine are not the oracle's)
+    mopts = {k: v for k, v in opts.items() if k in dict(oracle.Opts._fields_)}
     t0 = time.perf_counter()
-    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, **opts)
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, **mopts)
     x, hist = h.solve(b, tol=tol, max_cycles=500, adaptive=adaptive)
     t = time.perf_counter() - t0
     return t, len(hist) - 1
@@ -542,6 +544,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the Chung-Lu n = 1M measurement that the default run adds")
+    ap.add_argument("--op-times", default=None, metavar="PATH",
+                    help="after the timed region, time one more solve with the engine's op timer "
+                         "(lamg_op_times) and write its table to PATH")
     # the method's options: unset flags keep the workload's setting (WORKLOAD_OPTS),
     # else the library's default
     ap.add_argument("--elim", type=int, default=None, choices=[0, 1],
@@ -557,6 +562,8 @@ def main():
                     help="1: the adaptive cycle recombines at the finest level too (default)")
     ap.add_argument("--n-coarsest", type=int, default=None,
                     help="coarsening stops below this many nodes (Sec. 4.1: 150)")
+    ap.add_argument("--colour-rule", type=int, default=None, choices=[0, 1],
+                    help="JP priority: 0 degree then hash (default), 1 degree then index (red-black on grids)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -585,22 +592,25 @@ def main():
     line = run_single(args, args.workload, L, W, torch, dev, stream, rank, world, local, dist, full=True)
     if rank == 0 and args.workload == "grid256" and not args.no_secondary:
         # the power-law workload of the same metric, measured the same way (fewer steps)
-        sec = run_single(args, "chung_lu1m", L, W, torch, dev, stream, rank, world, local, dist, full=False)
+        sec = run_single(args, "chung_lu1m", L, W, torch, dev, stream, rank, world, local, dist, full=False,
+                         cpu=True)
         line["secondary"] = {"chung_lu1m": {k: sec[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup")}
                              | {k: sec["config"][k] for k in ("levels", "cycles", "acf", "rel_res", "setup_s_host",
-                                                              "solve_s_host")}
+                                                              "solve_s_host", "gamma_coarse_max", "elim")}
                              | {"roofline_frac": (sec["roofline"] or {}).get("frac"),
-                                "fp64_vs_ir": sec["fp64_vs_ir"]}}
+                                "fp64_vs_ir": sec["fp64_vs_ir"], "cpu_baseline": sec["cpu_baseline"]}}
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
 
-def run_single(args, workload, L, W, torch, dev, stream, rank, world, local, dist, full):
-    """One graph: setup + solve to tol per step.  full: also the end-to-end form,
-    the CPU baseline and the clocks; otherwise only the device-timed steps and the
-    FP64 comparison (a secondary workload of the same run)."""
+def run_single(args, workload, L, W, torch, dev, stream, rank, world, local, dist, full, cpu=None):
+    """One graph: setup + solve to tol per step.  full: also the end-to-end form
+    and the CPU baseline; otherwise only the device-timed steps and the FP64
+    comparison (a secondary workload of the same run), and the CPU baseline if
+    cpu is set."""
+    cpu_leg = full if cpu is None else cpu
     gname, pdef, desc = WORKLOADS[workload]
     prec_name = (args.precision if full else None) or pdef
     prec = L.LAMG_FP32_IR if prec_name == "fp32ir" else L.LAMG_FP64
@@ -683,6 +693,26 @@ def run_single(args, workload, L, W, torch, dev, stream, rank, world, local, dis
                 "rel_res_fp64": res["fp64"][1].rel_res, "rel_res_fp32ir": res["fp32ir"][1].rel_res}
         L.lamg_free(h)
 
+    if full and args.op_times and rank == 0:
+        # one more solve with the engine's op timer (outside the timed region)
+        h = L.lamg_setup(g.n, rp, col, w, opt, stream)
+        x.zero_()
+        L.lamg_solve(h, b, x, tol, prec, stream)
+        L.lamg_op_times(h, 1)
+        x.zero_()
+        sto = L.lamg_solve(h, b, x, tol, prec, stream)
+        rows = L.lamg_op_times(h, 0)
+        L.lamg_op_times(h, -1)
+        lv = [L.lamg_level_info(h, l) for l in range(sto.levels)]
+        L.lamg_free(h)
+        with open(args.op_times, "w") as f:
+            f.write(f"# engine op times: {workload}, {prec_name}, {sto.cycles} cycles, block 0's clock\n")
+            for l, i in enumerate(lv):
+                f.write(f"# level {l}: n {i['n']} nnz {i['nnz']} colours {i['ncolours']} gamma {i['gamma']:.3f}\n")
+            f.write("level\top\tsingle_block\tcount\ttotal_ms\tper_us\n")
+            for r in sorted(rows, key=lambda r: -r[4]):
+                f.write(f"{r[0]}\t{r[1]}\t{r[2]}\t{r[3]}\t{r[4]:.3f}\t{1e3 * r[4] / r[3]:.2f}\n")
+
     # end to end through the host-array API, the same K steps: the graph and b from
     # pinned host memory, setup, solve, x back to the host; mean over the steps
     e2e = None
@@ -731,7 +761,7 @@ def run_single(args, workload, L, W, torch, dev, stream, rank, world, local, dis
                 "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
 
     cpu = None
-    if full and rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if cpu_leg and rank == 0 and world == 1 and not args.no_cpu_baseline:
         sg, sdesc = sample_graph(workload)
         sb = W.zero_sum_rhs(sg.n, 2)
         sopts, sadaptive = method_options(args, workload, sg.n)

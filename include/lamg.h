@@ -152,6 +152,13 @@ typedef struct {
                                   0 (default): degree, then splitmix64(key_l + u),
                                   then the lower index; 1: degree, then the lower
                                   index (red-black on a grid numbered by position) */
+    int32_t  negative_weights; /* 1: accept graphs with negative edge weights (Sec. 5,
+                                  grids with negative weights): every weight nonzero
+                                  and finite, every row's sum of weights positive
+                                  (else LAMG_ERR_BAD_WEIGHT); the Laplacian should be
+                                  positive semi-definite.  The energy-ratio test uses
+                                  |w_uv| in the nodal energies.  0 (default): weights
+                                  must be positive                                   */
 } lamg_options;
 
 typedef struct {

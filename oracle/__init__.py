@@ -46,7 +46,8 @@ class Opts(C.Structure):
                 ("elim", C.c_int32), ("elim_min_frac", C.c_double), ("lgmg_nx", C.c_int32),
                 ("mu_adaptive", C.c_double), ("gamma_coarse_max", C.c_double), ("plain_sums", C.c_int32),
                 ("gamma_fine_printed", C.c_int32), ("recomb_finest", C.c_int32),
-                ("relax_rule", C.c_int32), ("colour_rule", C.c_int32)]
+                ("relax_rule", C.c_int32), ("colour_rule", C.c_int32),
+                ("negative_weights", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -65,6 +66,7 @@ def lib():
                 "orc_canon_sum": (_D, [_P, _I64]),
                 "orc_canon_sum_global": (_D, [_P, _I64]),
                 "orc_validate": (_I32, [_I64, _P, _P, _P]),
+                "orc_validate_signed": (_I32, [_I64, _P, _P, _P]),
                 "orc_validate_graphs": (_I32, [_I64, _P, _P, _P, _I32, _P]),
                 "orc_laplacian_dense": (None, [_I64, _P, _P, _P, _P]),
                 "orc_colour": (_I32, [_I64, _P, _P, _U64, _P]),
@@ -138,9 +140,10 @@ def validate_graphs(n, rp, col, w, gptr) -> int:
     return int(lib().orc_validate_graphs(n, _p(rp), _p(col), _p(w), len(gp) - 1, _p(gp)))
 
 
-def validate(n, rp, col, w) -> int:
+def validate(n, rp, col, w, signed=False) -> int:
     rp, col, w = _csr(rp, col, w)
-    return int(lib().orc_validate(n, _p(rp), _p(col), _p(w)))
+    f = lib().orc_validate_signed if signed else lib().orc_validate
+    return int(f(n, _p(rp), _p(col), _p(w)))
 
 
 def laplacian_dense(n, rp, col, w):

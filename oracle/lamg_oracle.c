@@ -48,6 +48,7 @@ void orc_default_opts(orc_opts *o) {
     o->recomb_finest = 1;      /* reading R15: recombination at the finest level too */
     o->relax_rule = 0;         /* multicolour GS on the JP colouring (reading R2) */
     o->colour_rule = 0;        /* JP priority: degree, then the hashed key, then index */
+    o->negative_weights = 0;   /* positive weights only (as the library) */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -171,7 +172,7 @@ static int64_t find_entry(const int64_t *rp, const int32_t *col, int64_t u, int3
  * With several graphs (block-diagonal union, nodes of graph g in
  * [gptr[g], gptr[g+1])), no edge may join two graphs (ORC_ERR_ARG) and every
  * graph must be connected (ORC_ERR_DISCONNECTED). */
-static int32_t validate_core(int64_t n, const int64_t *rp, const int32_t *col, const double *w) {
+static int32_t validate_core(int64_t n, const int64_t *rp, const int32_t *col, const double *w, int32_t signed_w) {
     if (n < 1 || rp[0] != 0) return ORC_ERR_ARG;
     for (int64_t u = 0; u < n; u++) {
         if (rp[u + 1] < rp[u]) return ORC_ERR_ARG;
@@ -181,8 +182,15 @@ static int32_t validate_core(int64_t n, const int64_t *rp, const int32_t *col, c
         }
     }
     for (int64_t u = 0; u < n; u++)
-        for (int64_t e = rp[u]; e < rp[u + 1]; e++)
-            if (!(w[e] > 0.0) || !isfinite(w[e])) return ORC_ERR_BAD_WEIGHT;
+        for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
+            if (!isfinite(w[e])) return ORC_ERR_BAD_WEIGHT;
+            if (signed_w ? !(w[e] != 0.0) : !(w[e] > 0.0)) return ORC_ERR_BAD_WEIGHT;
+        }
+    /* signed weights (Sec. 5, grids with negative weights): Gauss-Seidel divides by
+     * a_uu = sum_v w_uv, so every row with entries needs a positive sum */
+    if (signed_w)
+        for (int64_t u = 0; u < n; u++)
+            if (rp[u + 1] > rp[u] && !(orc_canon_sum(w + rp[u], rp[u + 1] - rp[u]) > 0.0)) return ORC_ERR_BAD_WEIGHT;
     for (int64_t u = 0; u < n; u++)
         for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
             int64_t f = find_entry(rp, col, col[e], (int32_t)u);
@@ -212,12 +220,12 @@ static int32_t components(int64_t n, const int64_t *rp, const int32_t *col, int3
     return nc;
 }
 
-int32_t orc_validate_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
-                            int32_t ngraphs, const int64_t *gptr) {
+static int32_t validate_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                               int32_t ngraphs, const int64_t *gptr, int32_t signed_w) {
     if (ngraphs < 1 || gptr[0] != 0 || gptr[ngraphs] != n) return ORC_ERR_ARG;
     for (int32_t g = 0; g < ngraphs; g++)
         if (gptr[g + 1] <= gptr[g]) return ORC_ERR_ARG;
-    int32_t st = validate_core(n, rp, col, w);
+    int32_t st = validate_core(n, rp, col, w, signed_w);
     if (st != ORC_OK) return st;
     for (int32_t g = 0; g < ngraphs; g++)
         for (int64_t u = gptr[g]; u < gptr[g + 1]; u++)
@@ -229,10 +237,21 @@ int32_t orc_validate_graphs(int64_t n, const int64_t *rp, const int32_t *col, co
     return nc == ngraphs ? ORC_OK : ORC_ERR_DISCONNECTED;
 }
 
+int32_t orc_validate_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
+                            int32_t ngraphs, const int64_t *gptr) {
+    return validate_graphs(n, rp, col, w, ngraphs, gptr, 0);
+}
+
 int32_t orc_validate(int64_t n, const int64_t *rp, const int32_t *col, const double *w) {
     if (n < 1) return ORC_ERR_ARG;
     int64_t gptr[2] = {0, n};
     return orc_validate_graphs(n, rp, col, w, 1, gptr);
+}
+
+int32_t orc_validate_signed(int64_t n, const int64_t *rp, const int32_t *col, const double *w) {
+    if (n < 1) return ORC_ERR_ARG;
+    int64_t gptr[2] = {0, n};
+    return validate_graphs(n, rp, col, w, 1, gptr, 1);
 }
 
 /* Eq. (1.2): a_uu = sum of incident weights, a_uv = -w_uv. */
@@ -368,7 +387,13 @@ void orc_edge_scores(int64_t n, const int64_t *rp, const int32_t *col, const dou
     int64_t maxdeg = 0;
     for (int64_t u = 0; u < n; u++) if (rp[u + 1] - rp[u] > maxdeg) maxdeg = rp[u + 1] - rp[u];
     double *t = (double *)malloc(sizeof(double) * (size_t)(maxdeg + 1));
-    diag_canon(n, rp, w, diag);
+    /* the nodal energies use |w_uv| (reading R22): identical for positive weights,
+     * and with negative weights min_y E_u stays non-negative, so the ratio keeps
+     * its meaning of an energy inflation */
+    for (int64_t u = 0; u < n; u++) {
+        for (int64_t e = rp[u]; e < rp[u + 1]; e++) t[e - rp[u]] = fabs(w[e]);
+        diag[u] = orc_canon_sum(t, rp[u + 1] - rp[u]);
+    }
     for (int64_t u = 0; u < n; u++) {
         double s = 0.0;
         for (int k = 0; k < K; k++) s = s + X[u * K + k] * X[u * K + k];
@@ -378,12 +403,12 @@ void orc_edge_scores(int64_t n, const int64_t *rp, const int32_t *col, const dou
         maxw[u] = m;
         int64_t deg = rp[u + 1] - rp[u];
         for (int k = 0; k < K; k++) {
-            for (int64_t e = rp[u]; e < rp[u + 1]; e++) t[e - rp[u]] = w[e] * X[(int64_t)col[e] * K + k];
+            for (int64_t e = rp[u]; e < rp[u + 1]; e++) t[e - rp[u]] = fabs(w[e]) * X[(int64_t)col[e] * K + k];
             double B = orc_canon_sum(t, deg);
             double y = B / diag[u];
             for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
                 double d = y - X[(int64_t)col[e] * K + k];
-                t[e - rp[u]] = w[e] * (d * d);
+                t[e - rp[u]] = fabs(w[e]) * (d * d);
             }
             ystar[u * K + k] = y;
             emin[u * K + k] = 0.5 * orc_canon_sum(t, deg);
@@ -1052,7 +1077,7 @@ static int make_coarsest(orc_level *L, const orc_opts *o) {
 static int32_t setup_graphs(int64_t n, const int64_t *rp, const int32_t *col, const double *w,
                             int32_t ngraphs, const int64_t *gptr, const orc_opts *o, orc_hier **out) {
     *out = NULL;
-    int32_t st = orc_validate_graphs(n, rp, col, w, ngraphs, gptr);
+    int32_t st = validate_graphs(n, rp, col, w, ngraphs, gptr, o->negative_weights);
     if (st != ORC_OK) return st;
     orc_hier *h = (orc_hier *)calloc(1, sizeof(orc_hier));
     h->o = *o;

@@ -79,6 +79,9 @@ typedef struct {
     int32_t  colour_rule;      /* JP priority (reading R2): 0 (default) degree, then
                                   splitmix64(key + u), then the lower index; 1 degree,
                                   then the lower index (greedy in that order)         */
+    int32_t  negative_weights; /* 1: accept nonzero weights of either sign whose rows
+                                  have a positive sum (Sec. 5, grids with negative
+                                  weights); 0 (default): positive weights only       */
 } orc_opts;
 
 typedef struct orc_hier orc_hier;
@@ -94,6 +97,8 @@ uint64_t orc_splitmix64(uint64_t key);
 double   orc_canon_sum(const double *t, int64_t len);
 double   orc_canon_sum_global(const double *t, int64_t len);
 int32_t  orc_validate(int64_t n, const int64_t *rp, const int32_t *col, const double *w);
+/* the same for signed weights: nonzero and finite, every row's sum positive */
+int32_t  orc_validate_signed(int64_t n, const int64_t *rp, const int32_t *col, const double *w);
 /* Several graphs as one block-diagonal union: graph g owns nodes
  * [gptr[g], gptr[g+1]).  No edge may join two graphs (ORC_ERR_ARG); each graph
  * must be connected (ORC_ERR_DISCONNECTED). */

@@ -134,6 +134,7 @@ void lamg_default_options(lamg_options *o) {
     o->recomb_finest = 1;
     o->relax_rule = 0;
     o->colour_rule = 0;
+    o->negative_weights = 0;
 }
 
 const char *lamg_last_error(void) { return g_last_error.c_str(); }
@@ -164,7 +165,8 @@ static lamg_status setup_impl(int32_t ngraphs, const int64_t *graph_ptr, int64_t
                          o.q_max > 0.0 && o.n_coarsest >= 1 && o.coarse_sweeps >= 0 &&
                          o.agg_rule >= 0 && o.agg_rule <= 2 && (o.recomb_finest == 0 || o.recomb_finest == 1) &&
                          (o.relax_rule == 0 || o.relax_rule == 1) && o.sb_work32 >= 0 && o.sb_work64 >= 0 &&
-                         o.tail_work32 >= 0 && o.tail_work64 >= 0 && (o.colour_rule == 0 || o.colour_rule == 1),
+                         o.tail_work32 >= 0 && o.tail_work64 >= 0 && (o.colour_rule == 0 || o.colour_rule == 1) &&
+                         (o.negative_weights == 0 || o.negative_weights == 1),
                      LAMG_ERR_ARG, "invalid options");
         auto t0 = std::chrono::steady_clock::now();
         h = new lamg_ctx();
@@ -172,7 +174,8 @@ static lamg_status setup_impl(int32_t ngraphs, const int64_t *graph_ptr, int64_t
         h->gptr.assign(graph_ptr, graph_ptr + ngraphs + 1);
         h->opt = o;
         cudaStream_t s = (cudaStream_t)stream;
-        if (h->opt.validate) validate_graph(n, row_ptr, col, w, w_is_fp32, s, ngraphs, graph_ptr);
+        if (h->opt.validate)
+            validate_graph(n, row_ptr, col, w, w_is_fp32, s, ngraphs, graph_ptr, h->opt.negative_weights);
         build_hierarchy(h, n, row_ptr, col, w, w_is_fp32, s);
         build_solve_layout(h, s);
         h->n = n;

@@ -40,14 +40,9 @@ __device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid
     if constexpr (sizeof(T) == 4) {
         // FP32: the next slice's first pairs are staged in shared memory while this
         // slice's gathers are in flight
-        sell_walk32(L, L.csl[c] + wid, L.csl[c + 1], nwarp, L.x, [&](const int4 m, const uint4 (&v)[kSellPre],
-                                                                      const float (&xv)[2 * kSellPre]) {
+        sell_walk32(L, L.csl[c] + wid, L.csl[c + 1], nwarp, [&](const int4 m, const uint4 *st) {
             float acc = 0.0f, d = 0.0f;
-#pragma unroll
-            for (int q = 0; q < kSellPre; q++) {
-                acc += pw(v[q], 0) * xv[2 * q] + pw(v[q], 1) * xv[2 * q + 1];
-                d += pw(v[q], 0) + pw(v[q], 1);
-            }
+            sell_row32(L, m, lane, st, L.x, 0.0f, false, acc, d);
             sell_rest(L, m, lane, L.x, 0.0f, false, acc, d);
             const int32_t i = m.x + lane;
             if (lane < m.y && d != 0.0f) L.x[i] = (L.b[i] + acc) / d;
@@ -75,14 +70,11 @@ __device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const 
     if constexpr (sizeof(T) == 4) {
         // FP32: the next slice's first pairs are staged in shared memory while this
         // slice's gathers are in flight
-        sell_walk32(L, wid, L.nsl, nwarp, x, [&](const int4 m, const uint4 (&v)[kSellPre],
-                                                 const float (&xv)[2 * kSellPre]) {
+        sell_walk32(L, wid, L.nsl, nwarp, [&](const int4 m, const uint4 *st) {
             const int32_t i = m.x + (lane < m.y ? lane : 0);
             const float xi = x[i];
             float acc = 0.0f, dummy = 0.0f;
-#pragma unroll
-            for (int q = 0; q < kSellPre; q++)
-                acc += pw(v[q], 0) * (xv[2 * q] - xi) + pw(v[q], 1) * (xv[2 * q + 1] - xi);
+            sell_row32(L, m, lane, st, x, xi, true, acc, dummy);
             sell_rest(L, m, lane, x, xi, true, acc, dummy);
             if (lane < m.y) {
                 const float ri = b[i] + acc;

@@ -42,10 +42,11 @@ struct MKLevel {
 // are loaded while the gathers of the current slice are in flight.  fn(m, lane,
 // pairs, xv) receives the current slice's first four pairs and their gathered x
 // values and finishes the slice (further pairs, then the row update).
-constexpr int kSellPre = 3;   // pairs of the next slice staged ahead (a 7-point row has 3)
+constexpr int kSellStage = 6;   // pairs of a slice staged in shared memory (rows of up to 12 entries)
+constexpr int kSellChunk = 3;   // staged pairs moved to registers at a time (a 7-point row has 3)
 // per-warp staging of the FP32 sliced ELL in the engine's dynamic shared memory:
-// two slots of kSellPre pairs x 32 lanes of 16 bytes
-constexpr int kSellStageBytes = 2 * kSellPre * 32 * 16;
+// two slots of kSellStage pairs x 32 lanes of 16 bytes
+constexpr int kSellStageBytes = 2 * kSellStage * 32 * 16;
 
 // 16-byte asynchronous copy global -> shared (L2 only), commit, wait
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
@@ -59,21 +60,20 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Stage the first pairs of slice m into slot `slot` of this warp's buffer (each
 // lane copies its own 16-byte pairs; one commit group per call, possibly empty).
 __device__ __forceinline__ void sell_stage(const MKLevel<float> &L, const int4 m, int lane, uint4 *wbuf, int slot) {
-    uint4 *dst = wbuf + slot * kSellPre * 32;
+    uint4 *dst = wbuf + slot * kSellStage * 32;
     const uint4 *src = L.ell32 + (size_t)m.w * 32 + lane;
 #pragma unroll
-    for (int q = 0; q < kSellPre; q++)
+    for (int q = 0; q < kSellStage; q++)
         if (q < m.z) cp_async16(dst + q * 32 + lane, src + (size_t)q * 32);
     cp_async_commit();
 }
 
 // Walk the FP32 slices [k0, k1) with step `step`, the next slice's first pairs
-// staged in shared memory while the current slice's gathers are in flight.
-// fn(m, v, xv) gets the slice, its first kSellPre pairs (zero beyond m.z) and
-// their gathered x values.  Every copy issued is waited for before returning.
+// staged in shared memory while the current slice is processed.  fn(m, st)
+// gets the slice and this lane's staged pairs (st[q * 32], q < min(m.z,
+// kSellStage)).  Every copy issued is waited for before returning.
 template <class F>
-__device__ __forceinline__ void sell_walk32(const MKLevel<float> &L, int64_t k0, int64_t k1, int64_t step,
-                                            const float *__restrict__ x, F fn) {
+__device__ __forceinline__ void sell_walk32(const MKLevel<float> &L, int64_t k0, int64_t k1, int64_t step, F fn) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     uint4 *wbuf = (uint4 *)(smem + (size_t)(threadIdx.x >> 5) * kSellStageBytes);
@@ -91,21 +91,38 @@ __device__ __forceinline__ void sell_walk32(const MKLevel<float> &L, int64_t k0,
         } else {
             cp_async_wait<0>();
         }
-        const uint4 *cur = wbuf + slot * kSellPre * 32 + lane;
-        uint4 v[kSellPre];
-#pragma unroll
-        for (int q = 0; q < kSellPre; q++) v[q] = q < mc.z ? cur[q * 32] : make_uint4(0, 0, 0, 0);
-        float xv[2 * kSellPre];
-#pragma unroll
-        for (int q = 0; q < kSellPre; q++) {
-            xv[2 * q] = x[v[q].x];
-            xv[2 * q + 1] = x[v[q].y];
-        }
-        fn(mc, v, xv);
+        fn(mc, (const uint4 *)(wbuf + slot * kSellStage * 32 + lane));
         slot ^= 1;
         mc = mn;
     }
 }
+
+// The dot products of a staged slice row: acc += sum w x[col] (res: w (x[col] - xi)),
+// d += sum w; staged pairs in chunks of kSellChunk, the rest (rows of more than
+// 2 kSellStage entries) from global memory.
+__device__ __forceinline__ void sell_row32(const MKLevel<float> &L, const int4 m, int lane, const uint4 *st,
+                                           const float *__restrict__ x, float xi, bool res, float &acc, float &d) {
+    const int nst = min(m.z, kSellStage);
+    for (int q0 = 0; q0 < nst; q0 += kSellChunk) {
+        uint4 v[kSellChunk];
+#pragma unroll
+        for (int q = 0; q < kSellChunk; q++) v[q] = q0 + q < nst ? st[(q0 + q) * 32] : make_uint4(0, 0, 0, 0);
+        float xv[2 * kSellChunk];
+#pragma unroll
+        for (int q = 0; q < kSellChunk; q++) {
+            xv[2 * q] = x[v[q].x];
+            xv[2 * q + 1] = x[v[q].y];
+        }
+#pragma unroll
+        for (int q = 0; q < kSellChunk; q++) {
+            const float w0 = __uint_as_float(v[q].z), w1 = __uint_as_float(v[q].w);
+            if (res) acc += w0 * (xv[2 * q] - xi) + w1 * (xv[2 * q + 1] - xi);
+            else acc += w0 * xv[2 * q] + w1 * xv[2 * q + 1];
+            d += w0 + w1;
+        }
+    }
+}
+
 __device__ __forceinline__ float pw(const uint4 &v, int h) { return __uint_as_float(h ? v.w : v.z); }
 
 // Slice dot products: lane l holds row m.x + l of slice m; acc += sum w x[col],
@@ -156,14 +173,14 @@ __device__ __forceinline__ void sell_dot(const MKLevel<double> &L, const int4 m,
         }
     }
 }
-// pairs kSellPre.. of a slice (rows of more than 2 kSellPre entries)
+// pairs kSellStage.. of a slice (rows of more than 2 kSellStage entries)
 template <class T>
 __device__ __forceinline__ void sell_rest(const MKLevel<T> &L, int4 m, int lane, const T *__restrict__ x, T xi,
                                           bool res, T &acc, T &d) {
-    if (m.z <= kSellPre) return;
+    if (m.z <= kSellStage) return;
     int4 m2 = m;
-    m2.w += kSellPre;
-    m2.z -= kSellPre;
+    m2.w += kSellStage;
+    m2.z -= kSellStage;
     if (res) sell_res(L, m2, lane, x, xi, acc);
     else sell_dot(L, m2, lane, x, acc, d);
 }

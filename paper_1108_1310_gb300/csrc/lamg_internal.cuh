@@ -247,7 +247,8 @@ namespace lamg {
 void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32_t *col,
                      const void *w, int32_t w_is_fp32, cudaStream_t s);
 void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
-                    int32_t w_is_fp32, cudaStream_t s, int32_t ngraphs = 1, const int64_t *gptr = nullptr);
+                    int32_t w_is_fp32, cudaStream_t s, int32_t ngraphs = 1, const int64_t *gptr = nullptr,
+                    int32_t signed_w = 0);
 
 // Single-block thresholds of the cycle engine: a level whose n + nnz is at most
 // sb_work(prec) runs every op on one block (no grid barrier); a colour of at

@@ -288,21 +288,26 @@ __global__ void k_w_to_64(const void *__restrict__ in, int32_t is32, double *__r
 
 enum { VF_ARG = 1, VF_WEIGHT = 2, VF_SYM = 4 };
 
+// signed_w = 0: weights positive and finite; 1 (negative_weights): nonzero and
+// finite, and each row with entries has a positive sum (Gauss-Seidel divides by it)
 __global__ void k_validate_rows(int64_t n, const int64_t *__restrict__ rp,
                                 const int32_t *__restrict__ col, const double *__restrict__ w,
-                                int32_t *flags) {
+                                int32_t signed_w, int32_t *flags) {
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n) return;
     int64_t s = rp[u], e = rp[u + 1];
     int f = 0;
     if (e < s) f |= VF_ARG;
+    double sum = 0.0;
     for (int64_t i = s; i < e && !(f & VF_ARG); i++) {
         int32_t v = col[i];
         if (v < 0 || v >= n || v == u) f |= VF_ARG;
         if (i > s && v <= col[i - 1]) f |= VF_ARG;
         double x = w[i];
-        if (!(x > 0.0) || !isfinite(x)) f |= VF_WEIGHT;
+        if (!isfinite(x) || (signed_w ? !(x != 0.0) : !(x > 0.0))) f |= VF_WEIGHT;
+        sum += x;
     }
+    if (signed_w && e > s && !(f & VF_ARG) && !(sum > 0.0)) f |= VF_WEIGHT;
     if (f) atomicOr(flags, f);
 }
 
@@ -405,7 +410,7 @@ void graph_ids(int64_t n, const int64_t *gptr_dev, int32_t G, int32_t *gid, cuda
 }
 
 void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
-                    int32_t w_is_fp32, cudaStream_t s, int32_t ngraphs, const int64_t *gptr) {
+                    int32_t w_is_fp32, cudaStream_t s, int32_t ngraphs, const int64_t *gptr, int32_t signed_w) {
     int64_t rp_n[2];
     LAMG_CUDA(cudaMemcpyAsync(&rp_n[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     LAMG_CUDA(cudaMemcpyAsync(&rp_n[1], row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -421,12 +426,14 @@ void validate_graph(int64_t n, const int64_t *row_ptr, const int32_t *col, const
     }
     Tmp<int32_t> flags(1, s);
     LAMG_CUDA(cudaMemsetAsync(flags.get(), 0, sizeof(int32_t), s));
-    k_validate_rows<<<ceil_div(n, 256), 256, 0, s>>>(n, row_ptr, col, w64.get(), flags.get());
+    k_validate_rows<<<ceil_div(n, 256), 256, 0, s>>>(n, row_ptr, col, w64.get(), signed_w, flags.get());
     LAMG_CHECK_LAUNCH();
     int32_t f = read_scalar(flags.get(), s);
     LAMG_REQUIRE(!(f & VF_ARG), LAMG_ERR_ARG,
                  "malformed CSR: columns must be in range, strictly increasing, no self loops");
-    LAMG_REQUIRE(!(f & VF_WEIGHT), LAMG_ERR_BAD_WEIGHT, "weights must be positive and finite");
+    LAMG_REQUIRE(!(f & VF_WEIGHT), LAMG_ERR_BAD_WEIGHT,
+                 signed_w ? "weights must be nonzero and finite, with positive row sums"
+                          : "weights must be positive and finite");
     if (nnz) {
         k_validate_sym<<<ceil_div(nnz, 256), 256, 0, s>>>(n, nnz, row_ptr, col, w64.get(), flags.get());
         LAMG_CHECK_LAUNCH();
@@ -467,7 +474,7 @@ template <int M>
 __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_stats(int32_t n, const int32_t *__restrict__ list, int32_t nlist,
                              const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                              const double *__restrict__ w, double hub_factor,
-                             double *__restrict__ diag, double *__restrict__ maxw,
+                             double *__restrict__ diag, double *__restrict__ adiag, double *__restrict__ maxw,
                              uint8_t *__restrict__ hub) {
     int32_t u;
     if (!get_row<M>(n, list, nlist, u)) return;
@@ -489,6 +496,7 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_stats(int32_t 
     m = reduce_max<M>(m);
     if (tlane<M>() != 0) return;
     diag[u] = d;
+    adiag[u] = s1;   // sum of |w_uv|: the energy-ratio test's diagonal (equals d for positive weights)
     maxw[u] = m;
     const double lhs = (double)deg * s1;
     const double rhs = hub_factor * s2;
@@ -1103,7 +1111,9 @@ static double canon_sum_global(const double *t, int64_t len, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Affinity and energy ratio (Eqs. (3.5), (3.12)); the reading of Eq. (3.12):
 // q_us = max_k E_u(x^k; x^k_s) / min_y E_u(x^k; y), with
-// Emin = 1/2 sum_v w_uv (y* - x_v)^2 and E_s = Emin + a_uu (x_s - y*)^2 / 2.
+// Emin = 1/2 sum_v |w_uv| (y* - x_v)^2 and E_s = Emin + a+_uu (x_s - y*)^2 / 2,
+// a+_uu = sum_v |w_uv| (the nodal energies use |w|: the same numbers for
+// positive weights, and non-negative energies for signed ones).
 // ---------------------------------------------------------------------------
 
 template <int M>
@@ -1130,7 +1140,7 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_pre(int32_t n,
 #pragma unroll
     for (int k = 0; k < 16; k++) acc[k] = 0.0;
     for (int32_t j = s + lane; j < e; j += tstride<M>()) {
-        const double wj = w[j];
+        const double wj = fabs(w[j]);
         const double *xv = X + (int64_t)col[j] * K;
 #pragma unroll
         for (int k = 0; k < 16; k++)
@@ -1143,7 +1153,7 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_pre(int32_t n,
         acc[k] = 0.0;
     }
     for (int32_t j = s + lane; j < e; j += tstride<M>()) {
-        const double wj = w[j];
+        const double wj = fabs(w[j]);
         const double *xv = X + (int64_t)col[j] * K;
 #pragma unroll
         for (int k = 0; k < 16; k++)
@@ -2224,10 +2234,10 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         h->L = l + 1;
         Tiers T(nl, s);
         build_tiers(L.rp.get(), nl, T, s);
-        Tmp<double> diag(nl, s), maxw(nl, s);
+        Tmp<double> diag(nl, s), adiag(nl, s), maxw(nl, s);
         L.hub.alloc(nl);
         LAUNCH3(k_node_stats, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
-                L.col.get(), L.w.get(), o.hub_factor, diag.get(), maxw.get(), L.hub.get());
+                L.col.get(), L.w.get(), o.hub_factor, diag.get(), adiag.get(), maxw.get(), L.hub.get());
         if (nl < o.n_coarsest || l + 1 >= maxl || (nxl > 0 && (nxl % 2 != 0 || nxl < 6))) {
             colour_level(h, L, l, T, nxl, s);
             L.coarsest = 1;
@@ -2286,7 +2296,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         // per-node TV quantities, then per-entry affinity / energy ratio / score
         Tmp<double> XX(nl, s), ystar((size_t)nl * K, s), emin((size_t)nl * K, s);
         LAUNCH3(k_node_pre, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
-                L.col.get(), L.w.get(), diag.get(), K, X.get(), XX.get(), ystar.get(), emin.get());
+                L.col.get(), L.w.get(), adiag.get(), K, X.get(), XX.get(), ystar.get(), emin.get());
         Tmp<int32_t> erow(L.nnz, s);
         LAUNCH3(k_entry_rows, nl, (const int32_t *)nullptr, T.w.get(), T.nw, T.b.get(), T.nb, s, L.rp.get(),
                 erow.get());
@@ -2298,7 +2308,7 @@ void build_hierarchy(lamg_ctx *h, int64_t n, const int64_t *row_ptr, const int32
         }
         if (L.nnz) {
             k_scores<<<ceil_div(L.nnz, 256), 256, 0, s>>>(L.nnz, erow.get(), L.col.get(), L.w.get(), K, X.get(),
-                                                         XX.get(), ystar.get(), emin.get(), diag.get(),
+                                                         XX.get(), ystar.get(), emin.get(), adiag.get(),
                                                          maxw.get(), o.q_max, o.weak_tol, L.aff.get(),
                                                          L.q.get(), score.get());
             LAMG_CHECK_LAUNCH();

@@ -49,7 +49,8 @@ class lamg_options(C.Structure):
                 ("gamma_coarse_max", C.c_double), ("elim", C.c_int32), ("elim_min_frac", C.c_double),
                 ("lgmg_nx", C.c_int32), ("agg_rule", C.c_int32), ("recomb_finest", C.c_int32),
                 ("relax_rule", C.c_int32), ("sb_work32", C.c_int32), ("sb_work64", C.c_int32),
-                ("tail_work32", C.c_int32), ("tail_work64", C.c_int32), ("colour_rule", C.c_int32)]
+                ("tail_work32", C.c_int32), ("tail_work64", C.c_int32), ("colour_rule", C.c_int32),
+                ("negative_weights", C.c_int32)]
 
 
 class lamg_stats(C.Structure):

@@ -68,6 +68,8 @@ RULES = {
     # recombination (Eq. (3.13)): the per-level gamma is compared exactly
     "cap1": {"gamma_coarse_max": 1.0},
     "mu12": {"mu_adaptive": 1.2},
+    # the colouring's priority without the hash: greedy in (degree, index) order
+    "colour_greedy": {"colour_rule": 1},
 }
 
 

@@ -121,6 +121,42 @@ def grid2d(nx: int, ny: int, wx: float = 1.0, wy: float = 1.0) -> Graph:
                       f"grid{nx}x{ny}")
 
 
+def grid2d_stencil(nx: int, kind: str) -> Graph:
+    """nx x nx grid Laplacians with negative weights (Sec. 5, grids with negative
+    weights), free boundary (Neumann); node (i, j) = i + nx j, i along x.  Edge
+    weights w_uv = -a_uv, so A = D - W has zero row sums:
+      '13pt':  the 13-point 4th-order stencil [1 -16 60 -16 1] / 12 along x and y:
+               w = 16/12 between neighbours at distance 1, w = -1/12 at distance 2;
+      'rot_c': Eq. (5.1) with alpha = -pi/4, eps = 1e-2, the 5-point U_xx, U_yy and
+               the alignment-agnostic cross term (1/4h^2)[-1 0 1; 0 0 0; 1 0 -1],
+               halved: w = .2525 to the four axis neighbours, .12375 to the NW and
+               SE neighbours, -.12375 to the NE and SW neighbours (centre 1.01);
+      'rot_d': the same with the cross term aligned to the NE/SW neighbours,
+               (1/2h^2)[0 -1 1; -1 2 -1; 1 -1 0], halved: w = .5 to the axis
+               neighbours and -.2475 to the NE and SW neighbours (centre 1.505)."""
+    i, j = np.meshgrid(np.arange(nx), np.arange(nx), indexing="xy")
+    i, j = i.ravel(), j.ravel()
+    idx = i + nx * j
+    if kind == "13pt":
+        offs = [((1, 0), 16.0 / 12.0), ((0, 1), 16.0 / 12.0), ((2, 0), -1.0 / 12.0), ((0, 2), -1.0 / 12.0)]
+    elif kind == "rot_c":
+        a, b, c = 0.505, -0.99, 0.505           # cos^2 + eps sin^2, (1 - eps) sin 2alpha, eps cos^2 + sin^2
+        offs = [((1, 0), a / 2), ((0, 1), c / 2), ((-1, 1), -b / 8), ((1, 1), b / 8)]
+    elif kind == "rot_d":
+        a, b, c = 0.505, -0.99, 0.505
+        offs = [((1, 0), (a - b / 2) / 2), ((0, 1), (c - b / 2) / 2), ((1, 1), b / 4)]
+    else:
+        raise ValueError(kind)
+    us, vs, ws = [], [], []
+    for (di, dj), wt in offs:
+        ok = (i + di >= 0) & (i + di < nx) & (j + dj >= 0) & (j + dj < nx)
+        us.append(idx[ok])
+        vs.append((i + di + nx * (j + dj))[ok])
+        ws.append(np.full(int(ok.sum()), wt))
+    u, v, w = np.concatenate(us), np.concatenate(vs), np.concatenate(ws)
+    return from_edges(nx * nx, np.minimum(u, v), np.maximum(u, v), w, f"grid{nx}_{kind}")
+
+
 def grid2d_periodic(nx: int) -> Graph:
     """5-point nx x nx grid Laplacian with periodic boundary (a torus), unit
     weights; node id = i + nx*j; nx >= 3."""
