@@ -43,11 +43,17 @@ WORKLOADS = {
                 "FP64 IR to 1e-8"),
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
     "grid1024": ("grid1024", "fp32ir", "1024x1024 5-point grid, unit weights (run with --elim); FP32 cycles in FP64 IR to 1e-8"),
+    "grid1024_13pt": ("grid1024_13pt", "fp32ir",
+                      "1024x1024 13-point 4th-order grid (negative weights, Sec. 5 grid table (b)); FP32 cycles "
+                      "in FP64 IR to 1e-8"),
+    "grid1024_rot_c": ("grid1024_rot_c", "fp32ir",
+                       "1024x1024 anisotropic-rotated grid, agnostic cross term (negative weights, Sec. 5 grid "
+                       "table (c)); FP32 cycles in FP64 IR to 1e-8"),
     "torus1024_lgmg": ("torus1024", "fp32ir",
                        "1024x1024 periodic 5-point grid, unit weights; Lean Geometric MG (Sec. 6): 2x2 aggregates, "
                        "red-black GS, gamma 1.5 at every level, flat mu 2; FP32 cycles in FP64 IR to 1e-8"),
 }
-TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid128": 1e-8, "grid64": 1e-10, "grid1024": 1e-8, "torus1024_lgmg": 1e-8}
+TOL = {"chung_lu1m": 1e-8, "grid256": 1e-8, "grid128": 1e-8, "grid1024_13pt": 1e-8, "grid1024_rot_c": 1e-8, "grid64": 1e-10, "grid1024": 1e-8, "torus1024_lgmg": 1e-8}
 # The DRAM bytes (read + write) of one engine launch come from the committed
 # ncu summary of the workload, profiles/k_engine_<workload>_<precision>.md,
 # which records them with a hash of the engine's sources at capture time; when
@@ -103,7 +109,8 @@ BATCHED = {
     "er500": "500 Erdos-Renyi graphs (LCC), n uniform in [1k, 200k], mean degree 8, unit weights, one zero-sum "
              "RHS each, as one block-diagonal union (lamg_setup_graphs); FP32 cycles in FP64 IR to 1e-8 per graph",
 }
-CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), "grid128": ("grid3d", 64), "grid64": ("grid2d", 64),
+CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), "grid128": ("grid3d", 64),
+              "grid1024_13pt": ("stencil:13pt", 256), "grid1024_rot_c": ("stencil:rot_c", 128), "grid64": ("grid2d", 64),
               "grid1024": ("grid2d", 256),
               "torus1024_lgmg": ("torus", 1024)}
 
@@ -115,15 +122,16 @@ CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), 
 # - elimination (Sec. 3.2) on the power-law graph, where its degree-1..4 nodes
 #   are many (on 3-D grids no node qualifies);
 # - on the 1024^2 grid the printed cap 2 with mu_adaptive 1.2: with mu 1 the
-#   adaptive cycle stalls there, with cap 1 too.
+#   adaptive cycle stalls there, with cap 1 too;
+# - the other workloads run the library's defaults (cap 1 slows RGGs, 11 -> 18
+#   cycles on a 200k-node one, and can stall them).
 WORKLOAD_OPTS = {
     "grid256": {"gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
     "grid128": {"gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
     "chung_lu1m": {"gamma_coarse_max": 1.0, "elim": 1},
     "grid1024": {"gamma_coarse_max": 2.0, "mu_adaptive": 1.2},
-    "rgg2m_b64": {"gamma_coarse_max": 1.0},
-    "er500": {"gamma_coarse_max": 1.0},
-    "knn500k_adjoint": {"gamma_coarse_max": 1.0},
+    "grid1024_13pt": {"negative_weights": 1},
+    "grid1024_rot_c": {"negative_weights": 1, "recomb_finest": 0},
 }
 
 
@@ -154,6 +162,9 @@ def sample_graph(workload):
         return W.grid3d(size, size, size, 1.0, 1.0, 0.01), f"{size}^3 7-point grid, weights 1/1/0.01"
     if kind == "torus":
         return W.grid2d_periodic(size), f"{size}x{size} periodic 5-point grid, Lean Geometric MG"
+    if kind.startswith("stencil:"):
+        st = kind.split(":")[1]
+        return W.grid2d_stencil(size, st), f"{size}x{size} grid, stencil {st}"
     return W.grid2d(size, size), f"{size}x{size} 5-point grid"
 
 
@@ -342,11 +353,20 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
     opt = L.lamg_default_options(validate=1, max_cycles=2000, **mopts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(prec=L.LAMG_FP32_IR):
+    prof = {"ms": 0.0, "n": 0, "bytes": 0}
+
+    def step(prec=L.LAMG_FP32_IR, profile=False):
         h = L.lamg_setup_graphs(gptr, rp, col, w, opt, stream)
+        if profile:
+            L.lamg_profile(h, True)
         x.zero_()
         st = L.lamg_solve(h, b, x, tol, prec, stream)
         sa = L.lamg_adjoint(h, x, gx, lam, eut, evt, dw, tol=tol, precision=prec, stream=stream)
+        if profile:
+            ms, n, byt = L.lamg_profile(h, False)
+            prof["ms"] += ms * n
+            prof["n"] += n
+            prof["bytes"] = byt
         L.lamg_free(h)
         return st, sa
 
@@ -364,7 +384,7 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res.append(step())
+            res.append(step(profile=True))
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -374,6 +394,12 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
         dist.barrier()
     ms = slowest_rank_ms(sum(times) / len(times), dist, dev)
     cyc = sum(r[0].cycles + r[1].cycles for r in res) / len(res)
+    roof = roofline_line(prof, "knn500k_adjoint", "fp32ir",
+                         "cycle engine k_engine (forward and adjoint refinement steps: ir_inner FP32 cycles + FP64 "
+                         "update, projection and residual)")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_adjoint(W, mopts, tol)
     # forward and adjoint solves timed alone on one hierarchy, FP32 IR and plain FP64
     h = L.lamg_setup_graphs(gptr, rp, col, w, opt, stream)
     cmp = {}
@@ -405,11 +431,77 @@ def run_adjoint(args, L, W, torch, dev, stream, rank, world, dist=None):
                    "graphs": len(gptr) - 1, **mopts,
                    "levels": res[-1][0].levels, "cycles_forward_plus_adjoint": cyc,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
-        "fp64_vs_ir": cmp, "e2e": None, "roofline": None, "cpu_baseline": None,
+        "fp64_vs_ir": cmp, "e2e": None, "roofline": roof, "cpu_baseline": cpu,
         "clocks": clk.summary(), "gpu_launches": launches,
     }
     if rank == 0:
         print(json.dumps(line))
+
+
+def roofline_line(prof, workload, prec_name, kernel):
+    """The roofline object of an engine: model bytes per launch over its average
+    CUDA-event time, against the HBM peak; traffic from the committed capture."""
+    if not prof["n"]:
+        return None
+    peak, peak_kind = load_peaks()
+    avg = prof["ms"] / prof["n"]
+    achieved = prof["bytes"] / (avg / 1e3) / 1e9
+    traffic, tsrc = profiled_traffic(workload, prec_name)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_source": tsrc, "kernel": kernel, "bytes_per_launch": prof["bytes"],
+            "avg_ms": avg, "launches": prof["n"], "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
+
+
+def cpu_baseline_adjoint(W, mopts, tol):
+    """The oracle's forward solve and adjoint on a 150k-point sample of the kNN family."""
+    import oracle
+    g, gptr, _, _ = W.knn_gmm(150_000, dim=16, k=10, seed=6, components=True)
+    rng = np.random.default_rng(6)
+    b = np.zeros(g.n)
+    lab = rng.permutation(g.n)[: g.n // 100]
+    b[lab] = rng.normal(size=lab.size)
+    for c in range(len(gptr) - 1):
+        sl = slice(gptr[c], gptr[c + 1])
+        b[sl] -= b[sl].mean()
+    gx = rng.normal(size=g.n)
+    eu, ev, _ = g.edges()
+    om = {k: v for k, v in mopts.items() if k in dict(oracle.Opts._fields_)}
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gptr=gptr, **om)
+    x, hist = h.solve(b, tol=tol, max_cycles=500)
+    lam, dw = h.adjoint(x, gx, eu, ev, tol=tol, max_cycles=500)
+    t = time.perf_counter() - t0
+    cyc = len(hist) - 1
+    return {"value": g.m * cyc * 2 / t, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
+            "sample": f"kNN n={g.n} (150k points of the same mixture), setup + forward solve + adjoint to {tol:g}, "
+                      f"{t:.1f} s; forward cycles counted twice", "host": host_cpu()}
+
+
+def cpu_baseline_batched(W, workload, mopts, tol):
+    """The oracle on a sample of a batched workload: 2 columns on a 200k-node RGG, or a
+    union of 8 Erdos-Renyi graphs of the same size distribution."""
+    import oracle
+    om = {k: v for k, v in mopts.items() if k in dict(oracle.Opts._fields_)}
+    t0 = time.perf_counter()
+    if workload == "rgg2m_b64":
+        g = W.rgg2d(200_000, 12.0, seed=4)
+        B = W.zero_sum_rhs(g.n, 3, count=2)
+        h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, **om)
+        cyc = 0
+        for c in range(B.shape[1]):
+            _, hist = h.solve(np.ascontiguousarray(B[:, c]), tol=tol, max_cycles=500)
+            cyc += len(hist) - 1
+        desc = "200k-node RGG of the same family, 2 right-hand sides"
+    else:
+        g, gptr = W.er_batch(8, 1000, 200_000, seed=7)
+        b = W.zero_sum_rhs_graphs(gptr, 3)
+        h = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gptr=gptr, **om)
+        _, hist = h.solve(b, tol=tol, max_cycles=500)
+        cyc = len(hist) - 1
+        desc = "union of the first 8 Erdos-Renyi graphs of the same generator"
+    t = time.perf_counter() - t0
+    return {"value": g.m * cyc / t, "unit": "edges*cycles/s", "cores": 1, "kind": "oracle",
+            "sample": f"{desc}, setup + solve to {tol:g}, {cyc} cycles in {t:.1f} s", "host": host_cpu()}
 
 
 def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
@@ -459,9 +551,18 @@ def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
         st = L.lamg_solve(h, B, X, tol, prec, stream)
         return st.cycles, st.rel_res, st.levels
 
-    def step():
+    prof = {"ms": 0.0, "n": 0, "bytes": 0}
+
+    def step(profile=False):
         h = setup()
+        if profile:
+            L.lamg_profile(h, True)
         r = solve(h, L.LAMG_FP32_IR)
+        if profile:
+            ms_, n_, byt = L.lamg_profile(h, False)
+            prof["ms"] += ms_ * n_
+            prof["n"] += n_
+            prof["bytes"] = byt
         L.lamg_free(h)
         return r
 
@@ -479,7 +580,7 @@ def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res.append(step())
+            res.append(step(profile=True))
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -489,6 +590,12 @@ def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
         dist.barrier()
     ms = slowest_rank_ms(sum(times) / len(times), dist, dev)
     cyc = sum(r[0] for r in res) / len(res)
+    roof = roofline_line(prof, args.workload, "fp32ir",
+                         "batched cycle engine k_engine4 (one launch = one refinement step of a column chunk)"
+                         if R > 1 else "cycle engine k_engine on the union (one launch = one refinement step)")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_batched(W, args.workload, mopts, tol)
     units = total_units(g.m * cyc, dist, dev)     # edges*cycles of all ranks' shares per step
 
     def timed(fn):
@@ -525,7 +632,7 @@ def run_batched(args, L, W, torch, dev, stream, rank, world, dist=None):
                    "batch_cols": tuned.get("cols"), "autotune_ms_16_32_64_128": tuned.get("ms"),
                    "levels": res[-1][2], "cycles_all_columns": cyc, "max_rel_res": res[-1][1],
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"shard{world}"},
-        "fp64_vs_ir": cmp, "e2e": None, "roofline": None, "cpu_baseline": None,
+        "fp64_vs_ir": cmp, "e2e": None, "roofline": roof, "cpu_baseline": cpu,
         "clocks": clk.summary(), "gpu_launches": launches,
     }
     if rank == 0:

@@ -36,9 +36,6 @@ static lamg_status guarded(F &&f) {
     }
 }
 
-static int64_t level_bytes(const SolveLevel &V, int wb) {
-    return V.nnz * (4 + wb) + (int64_t)(V.n + 1) * 4 + (int64_t)V.n * wb * 3;
-}
 
 // Two-level steps per level in one cycle, by replaying the schedule of the
 // cycle (the k-th coarse correction of level l runs ceil((k+1) g) - ceil(k g)
@@ -63,30 +60,35 @@ static void count_steps(lamg_ctx *h, int l, int theta, std::vector<int32_t> &vis
 // sweeps, a residual (sweep bytes + r write), restriction (r read + member
 // index + b^c, x^c writes), the prolongation (agg + x read/write + x^c
 // gather); plus the coarsest solves (dense inverse read, or its sweeps).
-static int64_t cycle_bytes(lamg_ctx *h, int wb) {
+// Algorithmic bytes of one cycle with `cols` right-hand sides: matrix bytes once,
+// vector bytes once per column (the batched engine reads each entry once for all
+// the columns of a run).
+int64_t cycle_bytes(lamg_ctx *h, int wb, int cols) {
     const int L = h->L;
-    if (L == 1) {
-        const SolveLevel &C = h->lv[0];
-        return C.dense ? (int64_t)C.n * C.n * 8 : h->opt.coarse_sweeps * level_bytes(C, wb);
-    }
+    auto level_bytes = [&](const SolveLevel &V) {
+        return (double)V.nnz * (4 + wb) + (double)(V.n + 1) * 4 + (double)cols * V.n * wb * 3;
+    };
+    auto coarse_bytes = [&](const SolveLevel &C) {
+        return C.dense ? (double)C.n * C.n * 8 + (double)cols * C.n * 16 : h->opt.coarse_sweeps * level_bytes(C);
+    };
+    if (L == 1) return (int64_t)coarse_bytes(h->lv[0]);
     std::vector<int32_t> visits(L, 0);
     std::vector<double> steps(L, 0.0);
     count_steps(h, 0, 1, visits, steps);
     double total = 0.0;
     for (int l = 0; l + 1 < L; l++) {
         const SolveLevel &V = h->lv[l];
-        const double sw = (double)level_bytes(V, wb);
-        const double res = sw + (double)V.n * wb;
-        const double rst = (double)V.n * (wb + 4) + (double)h->lv[l + 1].n * 2 * wb;
-        const double pro = (double)V.n * (4 + 2 * wb);
+        const double sw = level_bytes(V);
+        const double res = sw + (double)cols * V.n * wb;
+        const double rst = (double)V.n * 4 + (double)cols * ((double)V.n * wb + (double)h->lv[l + 1].n * 2 * wb);
+        const double pro = (double)V.n * 4 + (double)cols * V.n * 2 * wb;
         if (V.elim) {   // no sweeps; restriction and back-substitution are one CSR pass together
-            total += steps[l] * (res + sw + (double)h->lv[l + 1].n * 2 * wb + pro);
+            total += steps[l] * (res + sw + (double)cols * h->lv[l + 1].n * 2 * wb + pro);
             continue;
         }
         total += steps[l] * ((h->opt.nu1 + h->opt.nu2) * sw + res + rst + pro);
     }
-    const SolveLevel &C = h->lv[L - 1];
-    total += steps[L - 1] * (C.dense ? (double)C.n * C.n * 8 : h->opt.coarse_sweeps * (double)level_bytes(C, wb));
+    total += steps[L - 1] * coarse_bytes(h->lv[L - 1]);
     return (int64_t)total;
 }
 
@@ -187,8 +189,8 @@ static lamg_status setup_impl(int32_t ngraphs, const int64_t *graph_ptr, int64_t
         h->last.levels = h->L;
         h->last.t_setup_s = h->t_setup_s;
         h->last.nnz_total = tot;
-        h->last.bytes_per_cycle = cycle_bytes(h, 8);
-        h->last.bytes_per_cycle32 = cycle_bytes(h, 4);
+        h->last.bytes_per_cycle = cycle_bytes(h, 8, 1);
+        h->last.bytes_per_cycle32 = cycle_bytes(h, 4, 1);
     });
     if (st != LAMG_OK) {
         if (h) { release_solve(h); delete h; }

@@ -785,6 +785,17 @@ static void batch_run(lamg_ctx *h, int kind, int adaptive, cudaStream_t s) {
     L0.r = M.r64.get();
     const double mu = adaptive ? h->opt.mu_adaptive : h->opt.mu_flat;
     LAMG_CUDA(cudaMemsetAsync(M.bar.get(), 0, 2 * sizeof(unsigned int), s));  // the barrier counts from 0
+    const bool timed = h->prof_on && kind != 3;
+    if (timed) {   // CUDA events around the engine launch (lamg_profile)
+        if (h->prof_ev.size() < 2) {
+            for (int k = 0; k < 2; k++) {
+                cudaEvent_t e;
+                LAMG_CUDA(cudaEventCreate(&e));
+                h->prof_ev.push_back(e);
+            }
+        }
+        LAMG_CUDA(cudaEventRecord(h->prof_ev[0], s));
+    }
     if (kind == 1) {
         MRArgs<float> a{(const Op *)M.prog[slot].get(), 0, M.len[slot], (const MKLevel<float> *)M.lv32.get(), L0,
                         (float)mu, M.ld, M.groups, lg, M.part.get(), M.bar.get(), M.err.get()};
@@ -797,6 +808,17 @@ static void batch_run(lamg_ctx *h, int kind, int adaptive, cudaStream_t s) {
         LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine4<double>, dim3(M.grid), dim3(kEngThreads), args, 0, s));
     }
     note_launch();
+    if (timed) {
+        LAMG_CUDA(cudaEventRecord(h->prof_ev[1], s));
+        // the launch's algorithmic bytes: its cycles on ld columns plus the FP64
+        // residual of every column
+        const SolveLevel &V = h->lv[0];
+        const int64_t res64 = V.nnz * 12 + (int64_t)(V.n + 1) * 4 + (int64_t)V.n * 24 * M.ld;
+        M.prof_bytes = kind == 1 ? std::max(1, h->opt.ir_inner) * cycle_bytes(h, 4, M.ld) + res64 +
+                                       (int64_t)V.n * 32 * M.ld
+                                 : cycle_bytes(h, 8, M.ld) + res64;
+        M.prof_pending = 1;
+    }
     k_norm4<<<1, 1024, 0, s>>>(M.part.get(), M.grid, M.ld, M.out.get());
     LAMG_CHECK_LAUNCH();
 }
@@ -809,6 +831,14 @@ static bool batch_read(lamg_ctx *h, std::vector<double> &out, cudaStream_t s) {
     LAMG_CUDA(cudaMemcpyAsync(out.data(), M.out.get(), sizeof(double) * M.ld, cudaMemcpyDeviceToHost, s));
     LAMG_CUDA(cudaMemcpyAsync(&e, M.err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LAMG_CUDA(cudaStreamSynchronize(s));
+    if (M.prof_pending) {
+        float ms = 0.f;
+        LAMG_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[0], h->prof_ev[1]));
+        h->prof_ms += ms;
+        h->prof_count++;
+        h->prof_bytes = M.prof_bytes;
+        M.prof_pending = 0;
+    }
     if (e) {
         LAMG_CUDA(cudaMemsetAsync(M.err.get(), 0, sizeof(int32_t), s));
         LAMG_CUDA(cudaMemsetAsync(M.bar.get(), 0, 2 * sizeof(unsigned int), s));

@@ -169,9 +169,9 @@ __device__ __forceinline__ void tail_pre_row(int32_t i, const MKLevel<T> &L) {
 }
 
 template <class T>
-__device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
+__device__ void exec_op(const EngineArgs<T> &a, const MKLevel<T> *slv, const Op &op, int bid, int nb) {
     const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
-    const MKLevel<T> &L = a.lv[op.level];
+    const MKLevel<T> &L = lvl(a, slv, op.level);
     switch (op.type) {
         case OP_SWEEP:
             sweep_colour<T>(L, op.a, bid, nb);
@@ -189,7 +189,7 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             break;
         }
         case OP_RESTRICT:
-            restrict_op<T>(L, a.lv[op.level + 1], a.mu, bid, nb);
+            restrict_op<T>(L, lvl(a, slv, op.level + 1), a.mu, bid, nb);
             break;
         case OP_ZERO:
             for (int64_t i = tid; i < L.n; i += nthr) L.x[i] = T(0);
@@ -206,7 +206,7 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             break;
         }
         case OP_PROLONG: {
-            const MKLevel<T> &C = a.lv[op.level + 1];
+            const MKLevel<T> &C = lvl(a, slv, op.level + 1);
             for (int64_t i = tid; i < L.n; i += nthr) L.x[i] += C.x[L.pagg[i]];
             break;
         }
@@ -335,7 +335,7 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             break;
         case OP_ELIM_RESTRICT: {
             // the eliminated rows have degree <= 4: thread tier; warp/block-tier rows are kept rows
-            const MKLevel<T> &C = a.lv[op.level + 1];
+            const MKLevel<T> &C = lvl(a, slv, op.level + 1);
             for (int64_t i = tid; i < L.n; i += nthr) {
                 const int32_t ii = (int32_t)i;
                 if (L.ecx[ii] < 0 || L.rp[ii + 1] - L.rp[ii] > kLongRow) continue;
@@ -353,7 +353,7 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
             break;
         }
         case OP_ELIM_PROLONG: {
-            const MKLevel<T> &C = a.lv[op.level + 1];
+            const MKLevel<T> &C = lvl(a, slv, op.level + 1);
             for (int64_t i = tid; i < L.n; i += nthr) {
                 const int32_t c = L.ecx[i];
                 if (c >= 0) L.x[i] += C.x[c];
@@ -514,6 +514,14 @@ __device__ void exec_op(const EngineArgs<T> &a, const Op &op, int bid, int nb) {
 
 template <class T>
 __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
+    __shared__ MKLevel<T> slv[kLvShared];
+    {
+        static_assert(sizeof(MKLevel<T>) % 4 == 0, "level descriptors are copied as 4-byte words");
+        const int words = min(a.nlev, kLvShared) * (int)(sizeof(MKLevel<T>) / 4);
+        const int32_t *src = (const int32_t *)a.lv;
+        for (int i = threadIdx.x; i < words; i += blockDim.x) ((int32_t *)slv)[i] = src[i];
+        __syncthreads();
+    }
     int32_t pc = a.begin;
     unsigned int epoch = 0;
     while (pc < a.end) {
@@ -524,7 +532,7 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
             int32_t q = pc;
             if (blockIdx.x == 0) {
                 while (q < a.end && a.prog[q].sb) {
-                    exec_op<T>(a, a.prog[q], 0, 1);
+                    exec_op<T>(a, slv, a.prog[q], 0, 1);
                     __syncthreads();
                     q++;
                 }
@@ -533,7 +541,7 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
             }
             pc = q;
         } else {
-            exec_op<T>(a, op, blockIdx.x, gridDim.x);
+            exec_op<T>(a, slv, op, blockIdx.x, gridDim.x);
             pc++;
         }
         if (!grid_sync(a.bar, a.err, epoch)) return;
@@ -811,6 +819,7 @@ void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s) 
                             (float)mu, h->eng_part.get(), nullptr, h->scratch.get(), h->eng_bar.get(),
                             h->eng_err.get(), h->eng_optime.get()};
         set_graphs(a, h);
+        a.nlev = h->L;
         void *args[] = {&a};
         LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<float>, grid, block, args, kEngSmem, s));
     } else {
@@ -818,6 +827,7 @@ void engine_run(lamg_ctx *h, int kind, int adaptive, double mu, cudaStream_t s) 
                              h->eng_part.get(), nullptr, h->scratch.get(), h->eng_bar.get(), h->eng_err.get(),
                              h->eng_optime.get()};
         set_graphs(a, h);
+        a.nlev = h->L;
         void *args[] = {&a};
         LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<double>, grid, block, args, kEngSmem, s));
     }
@@ -900,6 +910,7 @@ int32_t *engine_run_noalloc(lamg_ctx *h, int adaptive, double mu, cudaStream_t s
                          (const MKLevel<double> *)h->eng_lv64.get(), L0, mu, part, nullptr, h->scratch.get(),
                          bar, err, nullptr};
     set_graphs(a, h);
+    a.nlev = h->L;
     void *args[] = {&a};
     LAMG_CUDA(cudaLaunchCooperativeKernel((void *)k_engine<double>, dim3(h->eng_grid), dim3(kEngThreads), args,
                                           kEngSmem, s));

@@ -294,7 +294,17 @@ struct EngineArgs {
     const int32_t *iperm0;   // natural level-1 id -> permuted row
     const int32_t *gid0;     // graph of each permuted level-1 row
     double *gsum, *gnorm;    // per-graph means, ||r64||^2
+    int32_t nlev;            // levels in lv (the first kLvShared are copied to shared memory)
 };
+
+// Level descriptors kept in each block's shared memory for the whole launch: an op
+// then reads its level's pointers and sizes from shared memory instead of
+// starting with dependent loads from global memory.
+constexpr int kLvShared = 20;
+template <class T>
+__device__ __forceinline__ const MKLevel<T> &lvl(const EngineArgs<T> &a, const MKLevel<T> *s, int l) {
+    return l < kLvShared ? s[l] : a.lv[l];
+}
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;

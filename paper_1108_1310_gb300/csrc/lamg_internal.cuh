@@ -193,6 +193,8 @@ struct BatchState {
     DBuf<int32_t> err;
     DBuf<int32_t> prog[6];         // (FP64 step, FP32-IR step, residual only) x adaptive
     int32_t len[6] = {0, 0, 0, 0, 0, 0};
+    int32_t prof_pending = 0;      // a timed launch whose events are not read yet
+    int64_t prof_bytes = 0;        // its algorithmic bytes
 };
 
 struct Hierarchy;
@@ -266,6 +268,8 @@ bool engine_failed(lamg_ctx *h, cudaStream_t s);
 // op timer table: (level < 128) x (op type < 32) x (grid, single block) x (ns, count)
 constexpr int kOpTimeSlots = 128 * 32 * 2 * 2;
 void engine_op_times(lamg_ctx *h, int mode, std::vector<unsigned long long> &out);
+// algorithmic bytes of one cycle with `cols` right-hand sides (weights of wb bytes)
+int64_t cycle_bytes(lamg_ctx *h, int wb, int cols);
 void build_program(lamg_ctx *h, int kind, int adaptive, std::vector<int32_t> &out, int groups = 0);
 bool engine_noalloc_ready(lamg_ctx *h, int adaptive);
 int32_t barrier_selftest(int32_t hold_one, cudaStream_t s);

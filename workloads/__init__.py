@@ -370,6 +370,8 @@ def config_graph(name: str) -> Graph:
         return grid3d(128, 128, 128, 1.0, 1.0, 0.01)
     if name == "rgg2m":
         return rgg2d(2_000_000, 12.0, seed=4)
+    if name.startswith("grid1024_"):
+        return grid2d_stencil(1024, name.split("_", 1)[1])
     if name == "torus1024":
         return grid2d_periodic(1024)
     raise KeyError(name)
