@@ -42,7 +42,7 @@ WORKLOADS = {
                 "128^3 7-point grid, weights 1/1/0.01 (the profiling case of the 256^3 family); FP32 cycles in "
                 "FP64 IR to 1e-8"),
     "grid64": ("grid64", "fp64", "64x64 5-point grid, unit weights; FP64 to 1e-10"),
-    "grid1024": ("grid1024", "fp32ir", "1024x1024 5-point grid, unit weights (run with --elim); FP32 cycles in FP64 IR to 1e-8"),
+    "grid1024": ("grid1024", "fp32ir", "1024x1024 5-point grid, unit weights; FP32 cycles in FP64 IR to 1e-8"),
     "grid1024_13pt": ("grid1024_13pt", "fp32ir",
                       "1024x1024 13-point 4th-order grid (negative weights, Sec. 5 grid table (b)); FP32 cycles "
                       "in FP64 IR to 1e-8"),

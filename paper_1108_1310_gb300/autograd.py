@@ -25,9 +25,11 @@ class GraphPattern:
     """Sparsity pattern of an undirected graph given by its edge list (u, v),
     u != v, no repeated pair.  Holds the symmetric CSR pattern on the device and,
     for every CSR entry, the index of its edge, so that a weight vector over the
-    edges maps to CSR weights by one gather."""
+    edges maps to CSR weights by one gather.  With ``gptr`` (host int64 node
+    ranges) the graph is a block-diagonal union of independent graphs, set up by
+    lamg_setup_graphs and solved per graph."""
 
-    def __init__(self, n: int, eu: torch.Tensor, ev: torch.Tensor, **opts):
+    def __init__(self, n: int, eu: torch.Tensor, ev: torch.Tensor, gptr=None, **opts):
         if eu.shape != ev.shape or eu.dim() != 1:
             raise ValueError("eu, ev must be 1-D and of equal length")
         dev = eu.device
@@ -46,6 +48,7 @@ class GraphPattern:
         self.entry_edge = eid[order].contiguous()
         self.eu = u.to(torch.int32).contiguous()
         self.ev = v.to(torch.int32).contiguous()
+        self.gptr = gptr
         self.opts = opts
         self._solver = None
         self._key = None
@@ -61,7 +64,7 @@ class GraphPattern:
             wc = w.detach()[self.entry_edge].contiguous()
             if wc.dtype not in (torch.float32, torch.float64):
                 wc = wc.to(torch.float64)
-            self._solver = _L.Solver(self.n, self.row_ptr, self.col, wc, **self.opts)
+            self._solver = _L.Solver(self.n, self.row_ptr, self.col, wc, gptr=self.gptr, **self.opts)
             self._key = (weakref.ref(w), w._version)
         return self._solver
 
