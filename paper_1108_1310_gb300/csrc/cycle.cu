@@ -31,7 +31,7 @@ static_assert((kEngThreads / 32) * kSellStageBytes <= kEngSmem, "sliced-ELL stag
 // ---------------------------------------------------------------------------
 
 template <class T>
-__device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid, int nb) {
+__device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid, int nb, SellPre &pre) {
     const int32_t t1 = L.cb[4 * c + 1], t2 = L.cb[4 * c + 2], t3 = L.cb[4 * c + 3];
     const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
@@ -40,10 +40,10 @@ __device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid
     if constexpr (sizeof(T) == 4) {
         // FP32: the next slice's first pairs are staged in shared memory while this
         // slice's gathers are in flight
-        sell_walk32(L, L.csl[c] + wid, L.csl[c + 1], nwarp, [&](const int4 m, const uint4 *st) {
+        sell_walk32(L, L.csl[c] + wid, L.csl[c + 1], nwarp, pre, [&](const int4 m, const uint4 *st, int nst) {
             float acc = 0.0f, d = 0.0f;
-            sell_row32(L, m, lane, st, L.x, 0.0f, false, acc, d);
-            sell_rest(L, m, lane, L.x, 0.0f, false, acc, d);
+            sell_row32(st, nst, L.x, 0.0f, false, acc, d);
+            sell_rest(L, m, lane, nst, L.x, 0.0f, false, acc, d);
             const int32_t i = m.x + lane;
             if (lane < m.y && d != 0.0f) L.x[i] = (L.b[i] + acc) / d;
         });
@@ -62,7 +62,7 @@ __device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid
 
 template <class T>
 __device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const T *x, T *r, T *xs, T *rs, int bid,
-                                         int nb) {
+                                         int nb, SellPre &pre) {
     const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     const int64_t nwarp = nthr >> 5, wid = tid >> 5;
     const int lane = threadIdx.x & 31;
@@ -70,12 +70,12 @@ __device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const 
     if constexpr (sizeof(T) == 4) {
         // FP32: the next slice's first pairs are staged in shared memory while this
         // slice's gathers are in flight
-        sell_walk32(L, wid, L.nsl, nwarp, [&](const int4 m, const uint4 *st) {
+        sell_walk32(L, wid, L.nsl, nwarp, pre, [&](const int4 m, const uint4 *st, int nst) {
             const int32_t i = m.x + (lane < m.y ? lane : 0);
             const float xi = x[i];
             float acc = 0.0f, dummy = 0.0f;
-            sell_row32(L, m, lane, st, x, xi, true, acc, dummy);
-            sell_rest(L, m, lane, x, xi, true, acc, dummy);
+            sell_row32(st, nst, x, xi, true, acc, dummy);
+            sell_rest(L, m, lane, nst, x, xi, true, acc, dummy);
             if (lane < m.y) {
                 const float ri = b[i] + acc;
                 r[i] = ri;
@@ -169,23 +169,28 @@ __device__ __forceinline__ void tail_pre_row(int32_t i, const MKLevel<T> &L) {
 }
 
 template <class T>
-__device__ void exec_op(const EngineArgs<T> &a, const MKLevel<T> *slv, const Op &op, int bid, int nb) {
+__device__ void exec_op(const EngineArgs<T> &a, const MKLevel<T> *slv, const Op &op, int bid, int nb, SellPre &pre) {
     const int64_t nthr = (int64_t)nb * blockDim.x, tid = spread_tid(bid, nb);
     const MKLevel<T> &L = lvl(a, slv, op.level);
     switch (op.type) {
         case OP_SWEEP:
-            sweep_colour<T>(L, op.a, bid, nb);
+            sweep_colour<T>(L, op.a, bid, nb, pre);
             break;
         case OP_SWEEP_RUN:
             for (int c = op.a; c < op.b; c++) {
-                sweep_colour<T>(L, c, 0, 1);
+                sweep_colour<T>(L, c, 0, 1, pre);
+                if constexpr (sizeof(T) == 4) {
+                    // the next colour's first slices are staged before the block syncs
+                    if (c + 1 < op.b)
+                        sell_prestage(L, L.csl[c + 1] + (threadIdx.x >> 5), L.csl[c + 2], blockDim.x >> 5, pre);
+                }
                 __syncthreads();
             }
             break;
         case OP_RESID: {
             T *xs = op.a == 0 ? L.xs0 : (op.a == 1 ? L.xs1 : nullptr);
             T *rs = op.a == 0 ? L.rs0 : (op.a == 1 ? L.rs1 : nullptr);
-            residual<T>(L, L.b, L.x, L.r, xs, rs, bid, nb);
+            residual<T>(L, L.b, L.x, L.r, xs, rs, bid, nb, pre);
             break;
         }
         case OP_RESTRICT:
@@ -289,7 +294,8 @@ __device__ void exec_op(const EngineArgs<T> &a, const MKLevel<T> *slv, const Op 
             break;
         }
         case OP_RES64: {
-            residual<double>(a.L0, a.L0.b, a.L0.x, a.L0.r, nullptr, nullptr, bid, nb);
+            SellPre none{};
+            residual<double>(a.L0, a.L0.b, a.L0.x, a.L0.r, nullptr, nullptr, bid, nb, none);
             // the residual entries this block wrote are not known here; sum squares after a barrier
             break;
         }
@@ -512,6 +518,23 @@ __device__ void exec_op(const EngineArgs<T> &a, const MKLevel<T> *slv, const Op 
     }
 }
 
+// Stage this warp's first slice of op `nx` (run by nb blocks, this one bid),
+// for the sliced-ELL walks that begin the FP32 sweep and residual ops.
+template <class T>
+__device__ __forceinline__ void prestage_op(const EngineArgs<T> &a, const MKLevel<T> *slv, const Op &nx, int bid,
+                                            int nb, SellPre &pre) {
+    if constexpr (sizeof(T) == 4) {
+        const int64_t nwarp = ((int64_t)nb * blockDim.x) >> 5, wid = spread_tid(bid, nb) >> 5;
+        if (nx.type == OP_SWEEP || (nx.type == OP_SWEEP_RUN && nx.a < nx.b)) {
+            const MKLevel<T> &N = lvl(a, slv, nx.level);
+            sell_prestage(N, N.csl[nx.a] + wid, N.csl[nx.a + 1], nwarp, pre);
+        } else if (nx.type == OP_RESID) {
+            const MKLevel<T> &N = lvl(a, slv, nx.level);
+            sell_prestage(N, wid, N.nsl, nwarp, pre);
+        }
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
     __shared__ MKLevel<T> slv[kLvShared];
@@ -524,6 +547,7 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
     }
     int32_t pc = a.begin;
     unsigned int epoch = 0;
+    SellPre pre{};
     while (pc < a.end) {
         const Op op = a.prog[pc];
         const bool timed = a.optime && blockIdx.x == 0 && threadIdx.x == 0;
@@ -532,7 +556,11 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
             int32_t q = pc;
             if (blockIdx.x == 0) {
                 while (q < a.end && a.prog[q].sb) {
-                    exec_op<T>(a, slv, a.prog[q], 0, 1);
+                    const int32_t t = a.prog[q].type;
+                    exec_op<T>(a, slv, a.prog[q], 0, 1, pre);
+                    // (ops that hold the level in shared memory may still be reading it)
+                    if (q + 1 < a.end && a.prog[q + 1].sb && t != OP_TAIL_RUN && t != OP_SWEEP_SMEM)
+                        prestage_op<T>(a, slv, a.prog[q + 1], 0, 1, pre);
                     __syncthreads();
                     q++;
                 }
@@ -541,10 +569,20 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
             }
             pc = q;
         } else {
-            exec_op<T>(a, slv, op, blockIdx.x, gridDim.x);
+            exec_op<T>(a, slv, op, blockIdx.x, gridDim.x, pre);
             pc++;
         }
-        if (!grid_sync(a.bar, a.err, epoch)) return;
+        grid_arrive(a.bar, epoch);
+        // stage this warp's first slice of the next op while the block waits
+        if (pc < a.end) {
+            const Op nx = a.prog[pc];
+            if (!nx.sb) prestage_op<T>(a, slv, nx, blockIdx.x, gridDim.x, pre);
+            else if (blockIdx.x == 0) prestage_op<T>(a, slv, nx, 0, 1, pre);
+        }
+        if (!grid_wait(a.bar, a.err, epoch)) {
+            cp_async_wait<0>();   // copies staged ahead land before the block leaves
+            return;
+        }
         if (timed) {
             const int key = (op.level * 32 + op.type) * 2 + (op.sb ? 1 : 0);
             a.optime[2 * key] += gtimer() - t0;

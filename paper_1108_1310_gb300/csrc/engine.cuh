@@ -38,11 +38,10 @@ struct MKLevel {
     const double2 *ellw;
 };
 
-// Software-pipelined walk over slices: the first four pairs of the next slice
-// are loaded while the gathers of the current slice are in flight.  fn(m, lane,
-// pairs, xv) receives the current slice's first four pairs and their gathered x
-// values and finishes the slice (further pairs, then the row update).
 constexpr int kSellStage = 6;   // pairs of a slice staged in shared memory (rows of up to 12 entries)
+// A warp with a single slice in an op has both slots to itself and stages up to
+// 2 kSellStage pairs (rows of up to 24 entries: the coarse levels of a 3-D grid).
+constexpr int kSellWide = 2 * kSellStage;
 constexpr int kSellChunk = 3;   // staged pairs moved to registers at a time (a 7-point row has 3)
 // per-warp staging of the FP32 sliced ELL in the engine's dynamic shared memory:
 // two slots of kSellStage pairs x 32 lanes of 16 bytes
@@ -57,52 +56,93 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Stage the first pairs of slice m into slot `slot` of this warp's buffer (each
-// lane copies its own 16-byte pairs; one commit group per call, possibly empty).
-__device__ __forceinline__ void sell_stage(const MKLevel<float> &L, const int4 m, int lane, uint4 *wbuf, int slot) {
-    uint4 *dst = wbuf + slot * kSellStage * 32;
+__device__ __forceinline__ uint4 *sell_warp_buf() {
+    extern __shared__ __align__(16) unsigned char smem[];
+    return (uint4 *)(smem + (size_t)(threadIdx.x >> 5) * kSellStageBytes);
+}
+
+// Stage the first min(m.z, cap) pairs of slice m at slot `slot` of this warp's
+// buffer (each lane copies its own 16-byte pairs; one commit group per call,
+// possibly empty).  cap = kSellWide fills both slots from slot 0.
+__device__ __forceinline__ void sell_stage(const MKLevel<float> &L, const int4 m, int lane, uint4 *wbuf, int slot,
+                                           int cap) {
+    uint4 *dst = wbuf + slot * kSellStage * 32 + lane;
     const uint4 *src = L.ell32 + (size_t)m.w * 32 + lane;
-#pragma unroll
-    for (int q = 0; q < kSellStage; q++)
-        if (q < m.z) cp_async16(dst + q * 32 + lane, src + (size_t)q * 32);
+    const int nq = min(m.z, cap);
+#pragma unroll 1
+    for (int q = 0; q < nq; q++) cp_async16(dst + q * 32, src + (size_t)q * 32);
     cp_async_commit();
 }
 
+// A warp's first slice of an op, staged ahead: while its block waits in the
+// barrier before the op, each warp loads the descriptor of its first slice and
+// stages that slice's pairs (neither depends on x), so that after the barrier
+// only the gathers of x remain on the op's critical path.  The descriptor
+// waits in shared memory (one per warp).
+struct SellPre {
+    bool on;
+};
+__device__ __forceinline__ int4 &sell_pre_desc() {
+    __shared__ int4 desc[kEngThreads / 32];
+    return desc[threadIdx.x >> 5];
+}
+
+// Issue the staging of slice k0 of a walk [k0, k1) with step `step`, as
+// sell_walk32 would at its start; false when the warp has no slice.
+__device__ __forceinline__ bool sell_prestage(const MKLevel<float> &L, int64_t k0, int64_t k1, int64_t step,
+                                              SellPre &pre) {
+    pre.on = false;
+    if (k0 >= k1) return false;
+    const int4 m = L.sl[k0];
+    sell_stage(L, m, threadIdx.x & 31, sell_warp_buf(), 0, k0 + step >= k1 ? kSellWide : kSellStage);
+    if ((threadIdx.x & 31) == 0) sell_pre_desc() = m;
+    __syncwarp();
+    pre.on = true;
+    return true;
+}
+
 // Walk the FP32 slices [k0, k1) with step `step`, the next slice's first pairs
-// staged in shared memory while the current slice is processed.  fn(m, st)
-// gets the slice and this lane's staged pairs (st[q * 32], q < min(m.z,
-// kSellStage)).  Every copy issued is waited for before returning.
+// staged in shared memory while the current slice is processed (a warp with a
+// single slice stages up to kSellWide pairs of it).  fn(m, st, nst) gets the
+// slice, this lane's staged pairs (st[q * 32], q < nst) and their count.  A
+// staged first slice (pre.on, from sell_prestage with the same range) is taken
+// over and pre is cleared.  Every copy issued is waited for before returning.
 template <class F>
-__device__ __forceinline__ void sell_walk32(const MKLevel<float> &L, int64_t k0, int64_t k1, int64_t step, F fn) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void sell_walk32(const MKLevel<float> &L, int64_t k0, int64_t k1, int64_t step,
+                                            SellPre &pre, F fn) {
     const int lane = threadIdx.x & 31;
-    uint4 *wbuf = (uint4 *)(smem + (size_t)(threadIdx.x >> 5) * kSellStageBytes);
-    if (k0 >= k1) return;
-    int4 mc = L.sl[k0];
-    sell_stage(L, mc, lane, wbuf, 0);
+    uint4 *wbuf = sell_warp_buf();
+    const bool single = k0 + step >= k1;
+    int4 mc;
+    if (pre.on) {
+        mc = sell_pre_desc();
+        pre.on = false;
+    } else {
+        if (k0 >= k1) return;
+        mc = L.sl[k0];
+        sell_stage(L, mc, lane, wbuf, 0, single ? kSellWide : kSellStage);
+    }
     int slot = 0;
     for (int64_t k = k0; k < k1; k += step) {
         const bool more = k + step < k1;
         int4 mn = mc;
         if (more) {
             mn = L.sl[k + step];
-            sell_stage(L, mn, lane, wbuf, slot ^ 1);
+            sell_stage(L, mn, lane, wbuf, slot ^ 1, kSellStage);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
-        fn(mc, (const uint4 *)(wbuf + slot * kSellStage * 32 + lane));
+        fn(mc, (const uint4 *)(wbuf + slot * kSellStage * 32 + lane), min(mc.z, single ? kSellWide : kSellStage));
         slot ^= 1;
         mc = mn;
     }
 }
 
 // The dot products of a staged slice row: acc += sum w x[col] (res: w (x[col] - xi)),
-// d += sum w; staged pairs in chunks of kSellChunk, the rest (rows of more than
-// 2 kSellStage entries) from global memory.
-__device__ __forceinline__ void sell_row32(const MKLevel<float> &L, const int4 m, int lane, const uint4 *st,
-                                           const float *__restrict__ x, float xi, bool res, float &acc, float &d) {
-    const int nst = min(m.z, kSellStage);
+// d += sum w over its nst staged pairs, in pair order, kSellChunk pairs at a time.
+__device__ __forceinline__ void sell_row32(const uint4 *st, int nst, const float *__restrict__ x, float xi, bool res,
+                                           float &acc, float &d) {
     for (int q0 = 0; q0 < nst; q0 += kSellChunk) {
         uint4 v[kSellChunk];
 #pragma unroll
@@ -173,14 +213,14 @@ __device__ __forceinline__ void sell_dot(const MKLevel<double> &L, const int4 m,
         }
     }
 }
-// pairs kSellStage.. of a slice (rows of more than 2 kSellStage entries)
+// pairs nst.. of a slice (the pairs that were not staged)
 template <class T>
-__device__ __forceinline__ void sell_rest(const MKLevel<T> &L, int4 m, int lane, const T *__restrict__ x, T xi,
-                                          bool res, T &acc, T &d) {
-    if (m.z <= kSellStage) return;
+__device__ __forceinline__ void sell_rest(const MKLevel<T> &L, int4 m, int lane, int nst, const T *__restrict__ x,
+                                          T xi, bool res, T &acc, T &d) {
+    if (m.z <= nst) return;
     int4 m2 = m;
-    m2.w += kSellStage;
-    m2.z -= kSellStage;
+    m2.w += nst;
+    m2.z -= nst;
     if (res) sell_res(L, m2, lane, x, xi, acc);
     else sell_dot(L, m2, lane, x, acc, d);
 }
@@ -337,14 +377,26 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
 // and barrier suffices; thread 0 polls with acquire loads.  The spin is
 // bounded: after kMaxSpins polls (or when another block has given up) it sets
 // the error word and every block returns.
-__device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err, unsigned int &epoch) {
-    __shared__ int bad;
+//
+// The barrier comes in two halves, so that a block can issue work that does not
+// depend on the other blocks (loads of the next op's constant data) between
+// its arrival and its wait.  grid_arrive: all of this block's writes are made
+// visible, then thread 0 counts the block in.
+__device__ __forceinline__ void grid_arrive(unsigned int *bar, unsigned int &epoch) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        bad = 0;
-        const unsigned int target = (++epoch) * gridDim.x;
+        ++epoch;
         __threadfence();
         atomicAdd(bar, 1u);
+    }
+}
+// grid_wait: thread 0 polls until every block of barrier `epoch` has arrived
+// (bounded), then the block proceeds; false when the wait gave up.
+__device__ __forceinline__ bool grid_wait(unsigned int *bar, int32_t *err, unsigned int epoch) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) {
+        bad = 0;
+        const unsigned int target = epoch * gridDim.x;
         long long spins = 0;
         while (ld_acquire_gpu(bar) < target) {
             if ((++spins & 255) == 0) {
@@ -356,6 +408,10 @@ __device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err, unsig
     }
     __syncthreads();
     return bad == 0;
+}
+__device__ __forceinline__ bool grid_sync(unsigned int *bar, int32_t *err, unsigned int &epoch) {
+    grid_arrive(bar, epoch);
+    return grid_wait(bar, err, epoch);
 }
 
 // Block sums of N values of type A, result in every thread.  The cross-warp
