@@ -548,8 +548,10 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
     int32_t pc = a.begin;
     unsigned int epoch = 0;
     SellPre pre{};
+    // the next op is read while the block waits in the barrier and carried over,
+    // so that no op starts with a load of its own descriptor
+    Op op = pc < a.end ? a.prog[pc] : Op{};
     while (pc < a.end) {
-        const Op op = a.prog[pc];
         const bool timed = a.optime && blockIdx.x == 0 && threadIdx.x == 0;
         const unsigned long long t0 = timed ? gtimer() : 0ull;
         if (op.sb) {
@@ -574,8 +576,9 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
         }
         grid_arrive(a.bar, epoch);
         // stage this warp's first slice of the next op while the block waits
+        Op nx{};
         if (pc < a.end) {
-            const Op nx = a.prog[pc];
+            nx = a.prog[pc];
             if (!nx.sb) prestage_op<T>(a, slv, nx, blockIdx.x, gridDim.x, pre);
             else if (blockIdx.x == 0) prestage_op<T>(a, slv, nx, 0, 1, pre);
         }
@@ -588,6 +591,7 @@ __global__ void __launch_bounds__(kEngThreads) k_engine(EngineArgs<T> a) {
             a.optime[2 * key] += gtimer() - t0;
             a.optime[2 * key + 1] += 1;
         }
+        op = nx;
     }
 }
 

@@ -374,24 +374,30 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
 // launch and must be zero when the launch starts (the host clears it before
 // each launch).  Barrier number e (1, 2, ...) completes when bar[0] reaches
 // e * gridDim.x, so no block resets anything and a single atomic per block
-// and barrier suffices; thread 0 polls with acquire loads.  The spin is
-// bounded: after kMaxSpins polls (or when another block has given up) it sets
-// the error word and every block returns.
-//
-// The barrier comes in two halves, so that a block can issue work that does not
-// depend on the other blocks (loads of the next op's constant data) between
-// its arrival and its wait.  grid_arrive: all of this block's writes are made
-// visible, then thread 0 counts the block in.
+// and barrier suffices.  Ordering: the block's __syncthreads puts its threads'
+// writes before thread 0's arrival, a release reduction (cumulative at GPU
+// scope); thread 0 polls with acquire loads, and the closing __syncthreads
+// puts that acquire before every thread's next access.  On GB300 this pair
+// costs about a microsecond less per barrier inside the engine than full
+// fences around a relaxed atomic.  The spin is bounded: after kMaxSpins polls
+// (or when another block has given up) it sets the error word and every block
+// returns.
+
+__device__ __forceinline__ void red_release_gpu(unsigned int *p) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+
+// The barrier comes in two halves, so that a block can issue work that does
+// not depend on the other blocks (loads of the next op's constant data)
+// between its arrival and its wait.
 __device__ __forceinline__ void grid_arrive(unsigned int *bar, unsigned int &epoch) {
     __syncthreads();
     if (threadIdx.x == 0) {
         ++epoch;
-        __threadfence();
-        atomicAdd(bar, 1u);
+        red_release_gpu(bar);
     }
 }
-// grid_wait: thread 0 polls until every block of barrier `epoch` has arrived
-// (bounded), then the block proceeds; false when the wait gave up.
+// grid_wait: false when the wait gave up
 __device__ __forceinline__ bool grid_wait(unsigned int *bar, int32_t *err, unsigned int epoch) {
     __shared__ int bad;
     if (threadIdx.x == 0) {
@@ -404,7 +410,6 @@ __device__ __forceinline__ bool grid_wait(unsigned int *bar, int32_t *err, unsig
                 if (spins > kMaxSpins) { atomicExch(err, 1); bad = 1; break; }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return bad == 0;
@@ -461,13 +466,21 @@ __device__ __forceinline__ void sum_partials_n(const double *part, int nb, int k
     __shared__ double res[N];
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
+        // all N sums in one pass over the partials, so that their loads are in
+        // flight together; each sum still adds its partials in block order
         const int lane = threadIdx.x & 31;
+        double t[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) t[k] = 0.0;
+#pragma unroll 4
+        for (int b = lane; b < nb; b += 32) {
+#pragma unroll
+            for (int k = 0; k < N; k++) t[k] += part[(int64_t)b * 8 + k0 + k];
+        }
 #pragma unroll
         for (int k = 0; k < N; k++) {
-            double t = 0.0;
-            for (int b = lane; b < nb; b += 32) t += part[(int64_t)b * 8 + k0 + k];
-            t = warp_allsum(t);
-            if (lane == 0) res[k] = t;
+            const double v = warp_allsum(t[k]);
+            if (lane == 0) res[k] = v;
         }
     }
     __syncthreads();

@@ -591,16 +591,17 @@ constexpr long long kCoopMaxSpins = 1ll << 21;  // one to two seconds of polling
 
 // Counting grid barrier of the cooperative setup kernels: bar[0] counts the
 // arrivals of the whole launch (zeroed before it); barrier e completes at
-// e * gridDim.x.  Bounded spin: on expiry (or when another block gave up) the
-// error word is set and every block returns.
+// e * gridDim.x.  Thread 0 arrives with a release reduction after the block's
+// __syncthreads and polls with acquire loads; the closing __syncthreads passes
+// the acquire on to the block.  Bounded spin: on expiry (or when another block
+// gave up) the error word is set and every block returns.
 __device__ __forceinline__ bool coop_sync(unsigned int *bar, int32_t *err, unsigned int &epoch) {
     __shared__ int bad;
     __syncthreads();
     if (threadIdx.x == 0) {
         bad = 0;
         const unsigned int target = (++epoch) * gridDim.x;
-        __threadfence();
-        atomicAdd(bar, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         long long spins = 0;
         while (true) {
             unsigned int v;
@@ -611,7 +612,6 @@ __device__ __forceinline__ bool coop_sync(unsigned int *bar, int32_t *err, unsig
                 if (spins > kCoopMaxSpins) { atomicExch(err, 1); bad = 1; break; }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return bad == 0;
