@@ -121,8 +121,9 @@ CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), 
 #   counts as the printed 2 at a tenth of the colour phases on the 3-D grids;
 # - elimination (Sec. 3.2) on the power-law graph, where its degree-1..4 nodes
 #   are many (on 3-D grids no node qualifies);
-# - on the 1024^2 grid the printed cap 2 with mu_adaptive 1.2: with mu 1 the
-#   adaptive cycle stalls there, with cap 1 too;
+# - on the 1024^2 grids the printed cap 2 with mu_adaptive 1.2: with mu 1 the
+#   adaptive cycle stalls there (5-point: with cap 1 too; 13-point: 0.997 per
+#   cycle, against 16 cycles at 0.31 with mu 1.2, the oracle on the same grid);
 # - the other workloads run the library's defaults (cap 1 slows RGGs, 11 -> 18
 #   cycles on a 200k-node one, and can stall them).
 WORKLOAD_OPTS = {
@@ -130,7 +131,7 @@ WORKLOAD_OPTS = {
     "grid128": {"gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
     "chung_lu1m": {"gamma_coarse_max": 1.0, "elim": 1},
     "grid1024": {"gamma_coarse_max": 2.0, "mu_adaptive": 1.2},
-    "grid1024_13pt": {"negative_weights": 1},
+    "grid1024_13pt": {"negative_weights": 1, "mu_adaptive": 1.2},
     "grid1024_rot_c": {"negative_weights": 1, "recomb_finest": 0},
 }
 
