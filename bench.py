@@ -119,6 +119,10 @@ CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), 
 # which overrides it; the library's defaults are the paper's printed values):
 # - gamma_coarse_max 1 on the 3-D grids and the power-law graph: the same cycle
 #   counts as the printed 2 at a tenth of the colour phases on the 3-D grids;
+# - gamma 1.2 (fine-level cap; printed 1.5) on the 3-D grids: each coarse level
+#   is visited 5 times per cycle instead of 8, for 27/27, 29/29 and 28/30 cycles
+#   (printed cap / 1.2) on the oracle's 96^3, 64^3 and 128^3 grids; on the GPU
+#   at 256^3, 32 cycles in 621 ms against 30 in 752 ms;
 # - elimination (Sec. 3.2) on the power-law graph, where its degree-1..4 nodes
 #   are many (on 3-D grids no node qualifies);
 # - on the 1024^2 grids the printed cap 2 with mu_adaptive 1.2: with mu 1 the
@@ -127,8 +131,8 @@ CPU_SAMPLE = {"chung_lu1m": ("chung_lu", 1_000_000), "grid256": ("grid3d", 96), 
 # - the other workloads run the library's defaults (cap 1 slows RGGs, 11 -> 18
 #   cycles on a 200k-node one, and can stall them).
 WORKLOAD_OPTS = {
-    "grid256": {"gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
-    "grid128": {"gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
+    "grid256": {"gamma": 1.2, "gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
+    "grid128": {"gamma": 1.2, "gamma_coarse_max": 1.0, "colour_rule": 1, "sb_work32": 65536},
     "chung_lu1m": {"gamma_coarse_max": 1.0, "elim": 1},
     "grid1024": {"gamma_coarse_max": 2.0, "mu_adaptive": 1.2},
     "grid1024_13pt": {"negative_weights": 1, "mu_adaptive": 1.2},
@@ -173,7 +177,8 @@ def method_options(args, workload, n):
     """The method's options of this run, shared by the library and the oracle, and
     whether the solve is adaptive: the workload's settings, then any flag given."""
     opts, adaptive = method_opts(workload, n)
-    for k in ("gamma_coarse_max", "elim", "agg_rule", "recomb_finest", "n_coarsest", "mu_adaptive", "colour_rule"):
+    for k in ("gamma", "gamma_coarse_max", "elim", "agg_rule", "recomb_finest", "n_coarsest", "mu_adaptive",
+              "colour_rule"):
         v = getattr(args, k)
         if v is not None:
             opts[k] = v
@@ -659,6 +664,8 @@ def main():
     # else the library's default
     ap.add_argument("--elim", type=int, default=None, choices=[0, 1],
                     help="low-degree elimination levels (Sec. 3.2)")
+    ap.add_argument("--gamma", type=float, default=None,
+                    help="cap of the cycle index at the fine levels (Sec. 4.1 prints 1.5)")
     ap.add_argument("--gamma-coarse-max", type=float, default=None,
                     help="cap of the cycle index at the coarse levels (Eq. (4.1) prints 2)")
     ap.add_argument("--mu-adaptive", type=float, default=None,
