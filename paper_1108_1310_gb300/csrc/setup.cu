@@ -666,19 +666,82 @@ __global__ void k_jp_ready(const int32_t *__restrict__ rp, int64_t n, int tier, 
 }
 
 // decrement the counts of the neighbours that u beats; append those that reach zero
+// Append the ready lanes' nodes v to the next frontier, list row_tier(deg[v]),
+// with one atomic per warp and tier: a round releases tens of thousands of
+// nodes on the finest levels of a grid, and one atomic per node on the three
+// list counters serialised there.  All 32 lanes of the warp call it together.
+// The order inside a list changes no decision (a frontier's nodes are
+// pairwise non-adjacent, and each one's colour depends on earlier rounds only).
+__device__ __forceinline__ void jp_append_warp(bool ready, int32_t v, int t, int32_t *nlst, int64_t cap,
+                                               int32_t *nxt) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int tier = 0; tier < 3; tier++) {
+        const bool mine = ready && t == tier;
+        const unsigned m = __ballot_sync(0xffffffffu, mine);
+        if (m == 0u) continue;
+        const int leader = __ffs(m) - 1;
+        int32_t base = 0;
+        if (lane == leader) base = atomicAdd(&nxt[tier], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (mine) nlst[(int64_t)tier * cap + base + __popc(m & below)] = v;
+    }
+}
+
+// Release neighbour col[i] of u (its wait count drops by one when u beats it);
+// true when that made it ready, with its list tier.
+__device__ __forceinline__ bool jp_release_one(int32_t u, int32_t du, uint64_t pu, int32_t i,
+                                               const int32_t *__restrict__ col, const int32_t *__restrict__ deg,
+                                               const uint64_t *__restrict__ hsh, int32_t *__restrict__ wait,
+                                               int32_t &v, int &t) {
+    v = col[i];
+    if (!beats(du, pu, u, deg[v], hsh[v], v)) return false;
+    if (atomicSub(&wait[v], 1) != 1) return false;
+    t = row_tier(deg[v]);
+    return true;
+}
+
+// Thread tier: lane l releases the neighbours of u (u < 0: no row).  Called by
+// all 32 lanes of a warp; the loop runs to the warp's longest row.
+__device__ __forceinline__ void jp_release_thr(int32_t u, const int32_t *__restrict__ rp,
+                                               const int32_t *__restrict__ col, const int32_t *__restrict__ deg,
+                                               const uint64_t *__restrict__ hsh, int32_t *__restrict__ wait,
+                                               int32_t *nlst, int64_t cap, int32_t *nxt) {
+    int32_t s = 0, len = 0, du = 0;
+    uint64_t pu = 0;
+    if (u >= 0) {
+        s = rp[u];
+        len = rp[u + 1] - s;
+        du = deg[u];
+        pu = hsh[u];
+    }
+    const int32_t mlen = __reduce_max_sync(0xffffffffu, len);
+    for (int32_t k = 0; k < mlen; k++) {
+        int32_t v = 0;
+        int t = 0;
+        const bool ready = k < len && jp_release_one(u, du, pu, s + k, col, deg, hsh, wait, v, t);
+        jp_append_warp(ready, v, t, nlst, cap, nxt);
+    }
+}
+
+// Warp or block tier: the row's entries in strides of 32 (warp) or kBlk
+// (block) lanes; every warp of the row loops the same number of times.
 template <int M>
 __device__ __forceinline__ void jp_release(int32_t u, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                            const int32_t *__restrict__ deg, const uint64_t *__restrict__ hsh,
                                            int32_t *__restrict__ wait, int32_t *nlst, int64_t cap, int32_t *nxt) {
+    static_assert(M != M_THR, "thread-tier rows go through jp_release_thr");
     const int32_t du = deg[u];
     const uint64_t pu = hsh[u];
-    for (int32_t i = rp[u] + tlane<M>(); i < rp[u + 1]; i += tstride<M>()) {
-        const int32_t v = col[i];
-        if (!beats(du, pu, u, deg[v], hsh[v], v)) continue;
-        if (atomicSub(&wait[v], 1) == 1) {
-            const int t = row_tier(deg[v]);
-            nlst[(int64_t)t * cap + atomicAdd(&nxt[t], 1)] = v;
-        }
+    const int32_t s = rp[u], e = rp[u + 1];
+    const int32_t w0 = M == M_WARP ? 0 : (int32_t)(threadIdx.x & ~31u);
+    for (int32_t i0 = s + w0; i0 < e; i0 += tstride<M>()) {
+        const int32_t i = i0 + (int32_t)(threadIdx.x & 31);
+        int32_t v = 0;
+        int t = 0;
+        const bool ready = i < e && jp_release_one(u, du, pu, i, col, deg, hsh, wait, v, t);
+        jp_append_warp(ready, v, t, nlst, cap, nxt);
     }
 }
 
@@ -781,7 +844,10 @@ __global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp,
         if (blockIdx.x == 0 && threadIdx.x == 0) { nxt[0] = 0; nxt[1] = 0; nxt[2] = 0; }
         if (!coop_sync(bar, err, epoch)) return;
         // release the neighbours they beat
-        for (int64_t i = tid; i < c0; i += nthr) jp_release<M_THR>(L0[i], rp, col, deg, hsh, wait, N, cap, nxt);
+        for (int64_t i0 = tid - lane; i0 < c0; i0 += nthr) {   // warp-uniform loop
+            const int64_t i = i0 + lane;
+            jp_release_thr(i < c0 ? L0[i] : -1, rp, col, deg, hsh, wait, N, cap, nxt);
+        }
         for (int64_t i = wid; i < c1; i += nwarp) jp_release<M_WARP>(L1[i], rp, col, deg, hsh, wait, N, cap, nxt);
         if (spread) {
             if (c2 > 0) {
@@ -804,13 +870,10 @@ __global__ void __launch_bounds__(kBlk) k_jp_dag(const int32_t *__restrict__ rp,
                     int j;
                     int32_t u, e;
                     hub_piece(hp, p, c2, rp, j, u, e);
-                    if (e < rp[u + 1]) {
-                        const int32_t v = col[e];
-                        if (beats(deg[u], hsh[u], u, deg[v], hsh[v], v) && atomicSub(&wait[v], 1) == 1) {
-                            const int t = row_tier(deg[v]);
-                            N[(int64_t)t * cap + atomicAdd(&nxt[t], 1)] = v;
-                        }
-                    }
+                    int32_t v = 0;
+                    int t = 0;
+                    const bool ready = e < rp[u + 1] && jp_release_one(u, deg[u], hsh[u], e, col, deg, hsh, wait, v, t);
+                    jp_append_warp(ready, v, t, N, cap, nxt);
                 }
             }
         } else {
@@ -1200,13 +1263,42 @@ __global__ void k_scores(int64_t nnz, const int32_t *__restrict__ erow, const in
     const double num = dot * dot, den = XX[u] * XX[v];
     const double a = den > 0.0 ? num / den : 0.0;
     const double half_a = 0.5 * diag[u];
+    // q = max_k E_s,k / Emin,k, each quotient correctly rounded.  FP64 division is
+    // a long instruction sequence on a GPU whose FP64 rate is 1/64 of FP32, and
+    // rounding is monotone, so the largest rounded quotient is the rounded
+    // quotient of the largest exact ratio: FP32 estimates (relative error below
+    // 2^-20) pick the candidates within 2^-14 of the largest estimate, and only
+    // those are divided in FP64.  Values outside FP32's comfortable range, and
+    // Emin <= 0, take the exact path at once.  The result is the plain maximum's.
     double qq = 0.0;
-    for (int k = 0; k < K; k++) {
-        const double d = xv[k] - ystar[(int64_t)u * K + k];
-        const double em = emin[(int64_t)u * K + k];
-        const double es = em + half_a * (d * d);
-        const double r = em > 0.0 ? es / em : (es == 0.0 ? 1.0 : INFINITY);
-        if (r > qq) qq = r;
+    float est[16];
+    float emax = -1.0f;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        est[k] = -1.0f;
+        if (k < K) {
+            const double d = xv[k] - ystar[(int64_t)u * K + k];
+            const double em = emin[(int64_t)u * K + k];
+            const double es = em + half_a * (d * d);
+            if (em > 0.0 && em >= 1e-30 && em <= 1e30 && es <= 1e30) {
+                est[k] = __fdividef((float)es, (float)em);
+                emax = fmaxf(emax, est[k]);
+            } else {
+                const double r = em > 0.0 ? es / em : (es == 0.0 ? 1.0 : INFINITY);
+                if (r > qq) qq = r;
+            }
+        }
+    }
+    const float cut = emax * (1.0f - 6.103515625e-05f);   // 1 - 2^-14
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        if (k < K && est[k] >= 0.0f && est[k] >= cut) {
+            const double d = xv[k] - ystar[(int64_t)u * K + k];
+            const double em = emin[(int64_t)u * K + k];
+            const double es = em + half_a * (d * d);
+            const double r = es / em;
+            if (r > qq) qq = r;
+        }
     }
     const double mw = fmax(maxw[u], maxw[v]);
     const bool strong = fabs(w[j]) >= weak_tol * mw;
