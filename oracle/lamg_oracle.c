@@ -135,6 +135,35 @@ double orc_canon_sum(const double *t, int64_t len) {
     return tree32(q);
 }
 
+/* Canonical sum of products a_i b_i (the terms of Eq. (3.5), (3.12) and the
+ * TV relaxation): the order above, with each running lane sum advanced by a
+ * fused multiply-add, p = fma(a_i, b_i, p), one rounding per term.  The GPU
+ * kernels advance their lane sums the same way. */
+static double dot_left_to_right(const double *a, const double *b, int64_t len) {
+    double s = 0.0;
+    for (int64_t i = 0; i < len; i++) s = fma(a[i], b[i], s);
+    return s;
+}
+
+double orc_canon_dot(const double *a, const double *b, int64_t len) {
+    if (g_plain_sums || len <= 32) return dot_left_to_right(a, b, len);
+    if (len <= 512) {
+        double p[32];
+        for (int j = 0; j < 32; j++) {
+            p[j] = 0.0;
+            for (int64_t i = j; i < len; i += 32) p[j] = fma(a[i], b[i], p[j]);
+        }
+        return tree32(p);
+    }
+    double p[1024], q[32];
+    for (int j = 0; j < 1024; j++) {
+        p[j] = 0.0;
+        for (int64_t i = j; i < len; i += 1024) p[j] = fma(a[i], b[i], p[j]);
+    }
+    for (int g = 0; g < 32; g++) q[g] = tree32(p + 32 * g);
+    return tree32(q);
+}
+
 /* Long vectors: chunks of 512 terms, each summed canonically; the chunk sums
  * are summed the same way, recursively. */
 double orc_canon_sum_global(const double *t, int64_t len) {
@@ -387,6 +416,7 @@ void orc_edge_scores(int64_t n, const int64_t *rp, const int32_t *col, const dou
     int64_t maxdeg = 0;
     for (int64_t u = 0; u < n; u++) if (rp[u + 1] - rp[u] > maxdeg) maxdeg = rp[u + 1] - rp[u];
     double *t = (double *)malloc(sizeof(double) * (size_t)(maxdeg + 1));
+    double *aw = (double *)malloc(sizeof(double) * (size_t)(maxdeg + 1));
     /* the nodal energies use |w_uv| (reading R22): identical for positive weights,
      * and with negative weights min_y E_u stays non-negative, so the ratio keeps
      * its meaning of an energy inflation */
@@ -396,22 +426,23 @@ void orc_edge_scores(int64_t n, const int64_t *rp, const int32_t *col, const dou
     }
     for (int64_t u = 0; u < n; u++) {
         double s = 0.0;
-        for (int k = 0; k < K; k++) s = s + X[u * K + k] * X[u * K + k];
+        for (int k = 0; k < K; k++) s = fma(X[u * K + k], X[u * K + k], s);
         XX[u] = s;
         double m = 0.0;
         for (int64_t e = rp[u]; e < rp[u + 1]; e++) if (fabs(w[e]) > m) m = fabs(w[e]);
         maxw[u] = m;
         int64_t deg = rp[u + 1] - rp[u];
+        for (int64_t e = rp[u]; e < rp[u + 1]; e++) aw[e - rp[u]] = fabs(w[e]);
         for (int k = 0; k < K; k++) {
-            for (int64_t e = rp[u]; e < rp[u + 1]; e++) t[e - rp[u]] = fabs(w[e]) * X[(int64_t)col[e] * K + k];
-            double B = orc_canon_sum(t, deg);
+            for (int64_t e = rp[u]; e < rp[u + 1]; e++) t[e - rp[u]] = X[(int64_t)col[e] * K + k];
+            double B = orc_canon_dot(aw, t, deg);
             double y = B / diag[u];
             for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
                 double d = y - X[(int64_t)col[e] * K + k];
-                t[e - rp[u]] = fabs(w[e]) * (d * d);
+                t[e - rp[u]] = d * d;
             }
             ystar[u * K + k] = y;
-            emin[u * K + k] = 0.5 * orc_canon_sum(t, deg);
+            emin[u * K + k] = 0.5 * orc_canon_dot(aw, t, deg);
         }
     }
     for (int64_t u = 0; u < n; u++) {
@@ -419,7 +450,7 @@ void orc_edge_scores(int64_t n, const int64_t *rp, const int32_t *col, const dou
         for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
             int64_t v = col[e];
             double dot = 0.0;
-            for (int k = 0; k < K; k++) dot = dot + X[u * K + k] * X[v * K + k];
+            for (int k = 0; k < K; k++) dot = fma(X[u * K + k], X[v * K + k], dot);
             double num = dot * dot, den = XX[u] * XX[v];
             double a = den > 0.0 ? num / den : 0.0;
             double qq = 0.0;
@@ -437,7 +468,7 @@ void orc_edge_scores(int64_t n, const int64_t *rp, const int32_t *col, const dou
             if (score) score[e] = (strong && qq <= q_max) ? a : -1.0;
         }
     }
-    free(diag); free(XX); free(maxw); free(ystar); free(emin); free(t);
+    free(diag); free(XX); free(maxw); free(ystar); free(emin); free(t); free(aw);
 }
 
 /* Hub test, Sec. 3.4.1 footnote: |E_u| >= 8 sum_v |w_uv||E_v| / sum_v |w_uv|,
@@ -590,8 +621,8 @@ static double relax_tvs(orc_level *L, const orc_opts *o, int32_t level) {
                 if (deg == 0) continue;   /* isolated node: its TVs keep their random values */
                 for (int k = 0; k < K; k++) {
                     for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++)
-                        t[e - L->rp[u]] = L->w[e] * L->X[(int64_t)L->col[e] * K + k];
-                    L->X[u * K + k] = orc_canon_sum(t, deg) / L->diag[u];
+                        t[e - L->rp[u]] = L->X[(int64_t)L->col[e] * K + k];
+                    L->X[u * K + k] = orc_canon_dot(L->w + L->rp[u], t, deg) / L->diag[u];
                 }
             }
         if (o->relax_fast_ratio > 0.0 && sw >= o->nu_tv - 1) {
@@ -600,9 +631,9 @@ static double relax_tvs(orc_level *L, const orc_opts *o, int32_t level) {
                     int64_t deg = L->rp[u + 1] - L->rp[u];
                     for (int64_t e = L->rp[u]; e < L->rp[u + 1]; e++) {
                         double d = L->X[u * K + k] - L->X[(int64_t)L->col[e] * K + k];
-                        t[e - L->rp[u]] = L->w[e] * (d * d);
+                        t[e - L->rp[u]] = d * d;
                     }
-                    eu[u] = 0.5 * orc_canon_sum(t, deg);
+                    eu[u] = 0.5 * orc_canon_dot(L->w + L->rp[u], t, deg);
                 }
                 double E = orc_canon_sum_global(eu, n);
                 if (sw == o->nu_tv - 1) eprev[k] = E; else ecur[k] = E;

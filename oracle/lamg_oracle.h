@@ -95,6 +95,7 @@ void     orc_default_opts(orc_opts *o);
 /* ---- building blocks, exported so the tests can pin each one ---- */
 uint64_t orc_splitmix64(uint64_t key);
 double   orc_canon_sum(const double *t, int64_t len);
+double   orc_canon_dot(const double *a, const double *b, int64_t len);
 double   orc_canon_sum_global(const double *t, int64_t len);
 int32_t  orc_validate(int64_t n, const int64_t *rp, const int32_t *col, const double *w);
 /* the same for signed weights: nonzero and finite, every row's sum positive */

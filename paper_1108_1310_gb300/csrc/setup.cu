@@ -940,7 +940,8 @@ __global__ void k_tv_init(double *__restrict__ X, int64_t count, uint64_t key) {
 }
 
 // x_uk = (canonical sum of w_uv x_vk) / a_uu for every TV k (b = 0); one pass
-// over the row with K accumulators, each summed in its canonical order.
+// over the row with K accumulators, each summed in its canonical order; each
+// lane's running sum advances by a fused multiply-add, as in the oracle.
 template <int M>
 __device__ __forceinline__ void tv_update(int32_t u, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                           const double *__restrict__ w, const double *__restrict__ diag, int32_t K,
@@ -963,8 +964,8 @@ __device__ __forceinline__ void tv_update(int32_t u, const int32_t *__restrict__
         for (int k = 0; k < 16; k++)
             if (k < K) {
                 const double a = x0[k], b = x1[k];
-                acc[k] = acc[k] + w0 * a;
-                acc[k] = acc[k] + w1 * b;
+                acc[k] = fma(w0, a, acc[k]);
+                acc[k] = fma(w1, b, acc[k]);
             }
     }
     if (j < e) {
@@ -972,7 +973,7 @@ __device__ __forceinline__ void tv_update(int32_t u, const int32_t *__restrict__
         const double *xv = X + (int64_t)col[j] * K;
 #pragma unroll
         for (int k = 0; k < 16; k++)
-            if (k < K) acc[k] = acc[k] + wj * xv[k];
+            if (k < K) acc[k] = fma(wj, xv[k], acc[k]);
     }
     const double du = diag[u];
 #pragma unroll
@@ -1072,8 +1073,8 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const 
                             for (int k = 0; k < 16; k++)
                                 if (k < K) {
                                     const double a = x0[k], b = x1[k];
-                                    acc[k] = acc[k] + w0 * a;
-                                    acc[k] = acc[k] + w1 * b;
+                                    acc[k] = fma(w0, a, acc[k]);
+                                    acc[k] = fma(w1, b, acc[k]);
                                 }
                         }
                         if (j < je) {
@@ -1081,7 +1082,7 @@ __global__ void __launch_bounds__(kBlk) k_tv_sweeps_coop(int32_t nsweeps, const 
                             const double *xv = X + (int64_t)col[j] * K;
 #pragma unroll
                             for (int k = 0; k < 16; k++)
-                                if (k < K) acc[k] = acc[k] + wj * xv[k];
+                                if (k < K) acc[k] = fma(wj, xv[k], acc[k]);
                         }
 #pragma unroll
                         for (int k = 0; k < 16; k++) {
@@ -1126,7 +1127,7 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_tv_energy(int32_t n
     double acc = 0.0;
     for (int32_t j = s + tlane<M>(); j < e; j += tstride<M>()) {
         const double d = xu - X[(int64_t)col[j] * K + k];
-        acc = acc + w[j] * (d * d);
+        acc = fma(w[j], d * d, acc);
     }
     acc = canon_reduce<M>(acc);
     if (tlane<M>() == 0) eu[u] = 0.5 * acc;
@@ -1194,7 +1195,7 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_pre(int32_t n,
         double xx = 0.0;
         for (int k = 0; k < K; k++) {
             const double x = X[(int64_t)u * K + k];
-            xx = xx + x * x;
+            xx = fma(x, x, xx);
         }
         XX[u] = xx;
     }
@@ -1207,7 +1208,7 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_pre(int32_t n,
         const double *xv = X + (int64_t)col[j] * K;
 #pragma unroll
         for (int k = 0; k < 16; k++)
-            if (k < K) acc[k] = acc[k] + wj * xv[k];
+            if (k < K) acc[k] = fma(wj, xv[k], acc[k]);
     }
 #pragma unroll
     for (int k = 0; k < 16; k++) {
@@ -1222,7 +1223,7 @@ __global__ void __launch_bounds__(M == M_BLK ? kBlk : 256) k_node_pre(int32_t n,
         for (int k = 0; k < 16; k++)
             if (k < K) {
                 const double d = y[k] - xv[k];
-                acc[k] = acc[k] + wj * (d * d);
+                acc[k] = fma(wj, d * d, acc[k]);
             }
     }
 #pragma unroll
@@ -1259,7 +1260,7 @@ __global__ void k_scores(int64_t nnz, const int32_t *__restrict__ erow, const in
     const int32_t u = erow[j], v = col[j];
     const double *xu = X + (int64_t)u * K, *xv = X + (int64_t)v * K;
     double dot = 0.0;
-    for (int k = 0; k < K; k++) dot = dot + xu[k] * xv[k];
+    for (int k = 0; k < K; k++) dot = fma(xu[k], xv[k], dot);
     const double num = dot * dot, den = XX[u] * XX[v];
     const double a = den > 0.0 ? num / den : 0.0;
     const double half_a = 0.5 * diag[u];
