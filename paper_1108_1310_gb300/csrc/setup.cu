@@ -1264,42 +1264,13 @@ __global__ void k_scores(int64_t nnz, const int32_t *__restrict__ erow, const in
     const double num = dot * dot, den = XX[u] * XX[v];
     const double a = den > 0.0 ? num / den : 0.0;
     const double half_a = 0.5 * diag[u];
-    // q = max_k E_s,k / Emin,k, each quotient correctly rounded.  FP64 division is
-    // a long instruction sequence on a GPU whose FP64 rate is 1/64 of FP32, and
-    // rounding is monotone, so the largest rounded quotient is the rounded
-    // quotient of the largest exact ratio: FP32 estimates (relative error below
-    // 2^-20) pick the candidates within 2^-14 of the largest estimate, and only
-    // those are divided in FP64.  Values outside FP32's comfortable range, and
-    // Emin <= 0, take the exact path at once.  The result is the plain maximum's.
     double qq = 0.0;
-    float est[16];
-    float emax = -1.0f;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-        est[k] = -1.0f;
-        if (k < K) {
-            const double d = xv[k] - ystar[(int64_t)u * K + k];
-            const double em = emin[(int64_t)u * K + k];
-            const double es = em + half_a * (d * d);
-            if (em > 0.0 && em >= 1e-30 && em <= 1e30 && es <= 1e30) {
-                est[k] = __fdividef((float)es, (float)em);
-                emax = fmaxf(emax, est[k]);
-            } else {
-                const double r = em > 0.0 ? es / em : (es == 0.0 ? 1.0 : INFINITY);
-                if (r > qq) qq = r;
-            }
-        }
-    }
-    const float cut = emax * (1.0f - 6.103515625e-05f);   // 1 - 2^-14
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-        if (k < K && est[k] >= 0.0f && est[k] >= cut) {
-            const double d = xv[k] - ystar[(int64_t)u * K + k];
-            const double em = emin[(int64_t)u * K + k];
-            const double es = em + half_a * (d * d);
-            const double r = es / em;
-            if (r > qq) qq = r;
-        }
+    for (int k = 0; k < K; k++) {
+        const double d = xv[k] - ystar[(int64_t)u * K + k];
+        const double em = emin[(int64_t)u * K + k];
+        const double es = em + half_a * (d * d);
+        const double r = em > 0.0 ? es / em : (es == 0.0 ? 1.0 : INFINITY);
+        if (r > qq) qq = r;
     }
     const double mw = fmax(maxw[u], maxw[v]);
     const bool strong = fabs(w[j]) >= weak_tol * mw;

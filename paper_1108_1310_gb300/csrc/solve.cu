@@ -70,31 +70,6 @@ __global__ void k_perm_keys(const int32_t *__restrict__ rp, const int32_t *__res
     val[u] = u;
 }
 
-// Thread-tier rows are sorted by length, longest first, inside windows of
-// kSellSigma consecutive rows of their colour (stable: id order among equal
-// lengths).  A slice of the sliced ELL is as wide as its longest row, so rows of
-// like length share slices: on the coarse levels of a 3-D grid the stored pairs
-// drop from 1.4-1.75 to 1.02-1.05 times the entries' pairs, while a window of
-// 1024 rows keeps the gathers of x local.  Rows of one colour are independent
-// and each row's entries keep their order, so no result depends on this order.
-constexpr int32_t kSellSigma = 1024;
-
-// key2 = (window << 6) | (32 - length) for the rows at sorted positions p
-// (bin = colour * 3 + tier, boff = first position of each bin, woff = first
-// window of each bin); the rows of the warp and block tiers keep their order.
-__global__ void k_window_keys(int32_t n, const uint32_t *__restrict__ bin, const int32_t *__restrict__ boff,
-                              const int32_t *__restrict__ woff, const int32_t *__restrict__ perm,
-                              const int32_t *__restrict__ rp, uint32_t *__restrict__ key2) {
-    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint32_t b = bin[p];
-    const uint32_t w = (uint32_t)woff[b] + (uint32_t)((p - boff[b]) / kSellSigma);
-    const int32_t u = perm[p];
-    const int32_t len = rp[u + 1] - rp[u];
-    const uint32_t lk = (b % 3u == 0u && len <= kLongRow) ? (uint32_t)(kLongRow - len) : 0u;
-    key2[p] = (w << 6) | lk;
-}
-
 __global__ void k_invert(const int32_t *__restrict__ perm, int32_t n, int32_t *__restrict__ iperm) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) iperm[perm[i]] = i;
@@ -397,6 +372,8 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         int nb = 0;
         while ((1ll << nb) < nbins) nb++;
         radix_sort_pairs<uint32_t, int32_t>(key.get(), V.perm.get(), ktmp.get(), vtmp.get(), n, nb, s);
+        k_invert<<<ceil_div(n, 256), 256, 0, s>>>(V.perm.get(), n, iperm[l].get());
+        LAMG_CHECK_LAUNCH();
         LAMG_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (nbins + 1), s));
         k_key_hist<<<ceil_div(n, 256), 256, 0, s>>>(key.get(), n, cnt.get());
         LAMG_CHECK_LAUNCH();
@@ -404,23 +381,6 @@ void build_solve_layout(lamg_ctx *h, cudaStream_t s) {
         std::vector<int32_t> hoff(nbins + 1);
         LAMG_CUDA(cudaMemcpyAsync(hoff.data(), off.get(), sizeof(int32_t) * (nbins + 1), cudaMemcpyDeviceToHost, s));
         LAMG_CUDA(cudaStreamSynchronize(s));
-        {   // thread-tier rows by length inside windows of their colour (kSellSigma)
-            std::vector<int32_t> hwoff(nbins + 1, 0);
-            for (int b = 0; b < nbins; b++)
-                hwoff[b + 1] = hwoff[b] + (hoff[b + 1] - hoff[b] + kSellSigma - 1) / kSellSigma;
-            int wb = 6;
-            while ((1ll << wb) < ((int64_t)hwoff[nbins] << 6)) wb++;
-            LAMG_REQUIRE(wb <= 32, LAMG_ERR_ARG, "solve layout: too many row windows");
-            Tmp<int32_t> dwoff(nbins + 1, s);
-            LAMG_CUDA(cudaMemcpyAsync(dwoff.get(), hwoff.data(), sizeof(int32_t) * (nbins + 1), cudaMemcpyHostToDevice, s));
-            Tmp<uint32_t> key2(n, s);
-            k_window_keys<<<ceil_div(n, 256), 256, 0, s>>>(n, key.get(), off.get(), dwoff.get(), V.perm.get(),
-                                                             S.rp.get(), key2.get());
-            LAMG_CHECK_LAUNCH();
-            radix_sort_pairs<uint32_t, int32_t>(key2.get(), V.perm.get(), ktmp.get(), vtmp.get(), n, wb, s);
-        }
-        k_invert<<<ceil_div(n, 256), 256, 0, s>>>(V.perm.get(), n, iperm[l].get());
-        LAMG_CHECK_LAUNCH();
         V.cb.assign(4 * S.ncolours, 0);
         for (int c = 0; c < S.ncolours; c++)
             for (int t = 0; t < 4; t++) V.cb[4 * c + t] = hoff[3 * c + t];
