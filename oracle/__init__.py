@@ -65,6 +65,7 @@ def lib():
                 "orc_splitmix64": (_U64, [_U64]),
                 "orc_canon_sum": (_D, [_P, _I64]),
                 "orc_canon_sum_global": (_D, [_P, _I64]),
+                "orc_canon_dot": (_D, [_P, _P, _I64]),
                 "orc_validate": (_I32, [_I64, _P, _P, _P]),
                 "orc_validate_signed": (_I32, [_I64, _P, _P, _P]),
                 "orc_validate_graphs": (_I32, [_I64, _P, _P, _P, _I32, _P]),
@@ -126,6 +127,14 @@ def splitmix64(key: int) -> int:
 def canon_sum(t) -> float:
     t = np.ascontiguousarray(t, dtype=np.float64)
     return float(lib().orc_canon_sum(_p(t), t.size))
+
+
+def canon_dot(a, b) -> float:
+    """Canonical sum of the products a_i b_i, each lane advanced by a fused multiply-add."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert a.size == b.size
+    return float(lib().orc_canon_dot(_p(a), _p(b), a.size))
 
 
 def canon_sum_global(t) -> float:

@@ -120,6 +120,35 @@ def test_canon_sum_definition():
     assert err <= 1e5 * np.finfo(float).eps * np.abs(t).sum()
 
 
+def test_canon_dot_definition():
+    """Sums of products: the canonical order with every lane advanced by a fused
+    multiply-add, p = round(a b + p), one rounding per term."""
+    from fractions import Fraction
+    rng = np.random.default_rng(1)
+    # len <= 32: a left-to-right chain of exactly rounded a b + p (Fraction
+    # arithmetic is exact and float(Fraction) rounds to nearest, ties to even)
+    for n in (0, 1, 2, 7, 32):
+        a, b = rng.normal(size=n), rng.normal(size=n)
+        p = 0.0
+        for x, y in zip(a, b):
+            p = float(Fraction(float(x)) * Fraction(float(y)) + Fraction(p))
+        assert oracle.canon_dot(a, b) == p
+    # fused, not multiply-then-add: (1 + 2^-30)(1 - 2^-30) = 1 - 2^-60 rounds to 1
+    # as a product, so -1 + that product is 0 with two roundings and -2^-60 fused
+    u = 1.0 + 2.0 ** -30
+    assert oracle.canon_dot([-1.0, u], [1.0, 2.0 - u]) == -(2.0 ** -60)
+    # len > 32: lanes then the halving tree, as for canon_sum; with exact products
+    # (small integers) the result is the sum's
+    for n in (33, 512, 513, 5000):
+        a = rng.integers(-50, 50, n).astype(np.float64)
+        b = rng.integers(-50, 50, n).astype(np.float64)
+        assert oracle.canon_dot(a, b) == oracle.canon_sum(a * b) == float((a * b).sum())
+    # error bound of any order: |s - exact| <= n eps sum |a_i b_i|
+    a, b = rng.normal(size=4000), rng.normal(size=4000)
+    exact = float(sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b)))
+    assert abs(oracle.canon_dot(a, b) - exact) <= 4000 * np.finfo(float).eps * np.abs(a * b).sum()
+
+
 # --------------------------------------------------------------------------- #
 # Gauss-Seidel (Eq. (2.3))
 # --------------------------------------------------------------------------- #
