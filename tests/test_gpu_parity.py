@@ -70,6 +70,9 @@ RULES = {
     "mu12": {"mu_adaptive": 1.2},
     # the colouring's priority without the hash: greedy in (degree, index) order
     "colour_greedy": {"colour_rule": 1},
+    # the options of the 3-D grid benchmark: fine-level cycle-index cap 1.2 with
+    # the coarse cap 1 (Eq. (4.1)) and the greedy colouring
+    "grid_bench": {"gamma": 1.2, "gamma_coarse_max": 1.0, "colour_rule": 1},
 }
 
 
