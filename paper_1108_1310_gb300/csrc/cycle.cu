@@ -41,11 +41,13 @@ __device__ __forceinline__ void sweep_colour(const MKLevel<T> &L, int c, int bid
         // FP32: the next slice's first pairs are staged in shared memory while this
         // slice's gathers are in flight
         sell_walk32(L, L.csl[c] + wid, L.csl[c + 1], nwarp, pre, [&](const int4 m, const uint4 *st, int nst) {
+            // b does not depend on x: its load goes out before the gathers
+            const int32_t i = m.x + (lane < m.y ? lane : 0);
+            const float bi = L.b[i];
             float acc = 0.0f, d = 0.0f;
             sell_row32(st, nst, L.x, 0.0f, false, acc, d);
             sell_rest(L, m, lane, nst, L.x, 0.0f, false, acc, d);
-            const int32_t i = m.x + lane;
-            if (lane < m.y && d != 0.0f) L.x[i] = (L.b[i] + acc) / d;
+            if (lane < m.y && d != 0.0f) L.x[i] = (bi + acc) / d;
         });
     } else {
         for (int64_t k = L.csl[c] + wid; k < L.csl[c + 1]; k += nwarp) {
@@ -72,12 +74,12 @@ __device__ __forceinline__ void residual(const MKLevel<T> &L, const T *b, const 
         // slice's gathers are in flight
         sell_walk32(L, wid, L.nsl, nwarp, pre, [&](const int4 m, const uint4 *st, int nst) {
             const int32_t i = m.x + (lane < m.y ? lane : 0);
-            const float xi = x[i];
+            const float xi = x[i], bi = b[i];
             float acc = 0.0f, dummy = 0.0f;
             sell_row32(st, nst, x, xi, true, acc, dummy);
             sell_rest(L, m, lane, nst, x, xi, true, acc, dummy);
             if (lane < m.y) {
-                const float ri = b[i] + acc;
+                const float ri = bi + acc;
                 r[i] = ri;
                 if (xs) { xs[i] = xi; rs[i] = ri; }
             }
