@@ -711,6 +711,61 @@ def test_coarse_cycle_index_cap():
     assert hist[-1] <= 1e-10 * hist[0]
 
 
+def _iterations_per_cycle(h):
+    """Sub-cycle iterations of each level in one cycle under the per-cycle rule of
+    the fractional index (reading R14): the k-th coarse correction of level l, k
+    counted from 0 within the cycle, runs ceil((k+1) g) - ceil(k g) iterations."""
+    L = h.num_levels
+    its, k = [0] * L, [0] * L
+
+    def visit(l, theta):
+        its[l] += theta
+        if l + 1 >= L - 1:
+            return
+        g = h.info(l)["gamma"]
+        for _ in range(theta):
+            kk = k[l]
+            k[l] += 1
+            visit(l + 1, min(2, max(1, math.ceil((kk + 1) * g) - math.ceil(kk * g))))
+
+    visit(0, 1)
+    return its
+
+
+def test_fine_cycle_index_cap():
+    # Eq. (4.1) with the reading R13: gamma^l = min{cap, max{1, .7 |E^l| / |E^{l+1}|}},
+    # cap = gamma (printed 1.5) where |E^l| > .1 |E|, else gamma_coarse_max.  The cap
+    # changes the cycle only: the same hierarchy, fewer coarse iterations per cycle,
+    # and on the 1/1/0.01 grid about the same number of cycles
+    g = W.grid3d(32, 32, 32, 1.0, 1.0, 0.01)
+    b = W.zero_sum_rhs(g.n, 3)
+    kw = dict(gamma_coarse_max=1.0, colour_rule=1)
+    h15 = oracle.Hierarchy(g.n, g.rp, g.col, g.w, **kw)
+    h12 = oracle.Hierarchy(g.n, g.rp, g.col, g.w, gamma=1.2, **kw)
+    assert oracle.default_opts().gamma == 1.5
+    assert h12.num_levels == h15.num_levels
+    m1 = h15.info(0)["nnz"] / 2.0
+    fine = 0
+    for l in range(h15.num_levels - 1):
+        for k in range(3):
+            assert np.array_equal(h12.csr(l)[k], h15.csr(l)[k])
+        ml, mn = h15.info(l)["nnz"] / 2.0, h15.info(l + 1)["nnz"] / 2.0
+        r = 0.7 * ml / mn
+        if ml > 0.1 * m1:
+            fine += 1
+            assert h15.info(l)["gamma"] == min(1.5, max(1.0, r))
+            assert h12.info(l)["gamma"] == min(1.2, max(1.0, r))
+        else:
+            assert h15.info(l)["gamma"] == h12.info(l)["gamma"] == 1.0
+    assert fine >= 2
+    it15, it12 = _iterations_per_cycle(h15), _iterations_per_cycle(h12)
+    assert it12[0] == it15[0] == 1
+    assert all(a <= b for a, b in zip(it12, it15)) and sum(it12) < sum(it15)
+    _, hist15 = h15.solve(b, tol=1e-8)
+    _, hist12 = h12.solve(b, tol=1e-8)
+    assert hist12[-1] <= 1e-8 * hist12[0] and abs(len(hist12) - len(hist15)) <= 3
+
+
 @pytest.mark.parametrize("gname", ["grid64", "chung_lu", "rgg", "grid3d", "er"])
 @pytest.mark.parametrize("elim", [0, 1])
 def test_cycle_work_is_about_ten_relaxations(gname, elim):
